@@ -1,0 +1,415 @@
+"""FP64 CPU oracle of the PSM lattice Boltzmann step (arXiv 2502.20049).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow, obviously-correct restatement of the
+method that the CUDA library is checked against.  Only the test suite, the
+smoke check of ``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` may
+import it.  It shares no code with the CUDA library; the C++ source is
+``psm_oracle.cpp`` next to this file and is compiled with
+``-ffp-contract=off`` so that every float/double operation rounds on its own.
+
+What each function follows (sections and equations of the paper):
+
+* :func:`lattice` -- D3Q19 / D3Q27 velocity sets (Sec. 2.2 names them).
+* :func:`feq` -- Eq. 3, read with ``-u.u/(2 c_s^2)`` (the printed ``+`` is a
+  typo: with it the zeroth moment is not rho).
+* :func:`weighting` -- Eq. 5 (``mode=0``) and Eq. 6 (``mode=1``).
+* :class:`Sim` -- one step = remap (Sec. 3) -> Eq. 4 with Eq. 2 / TRT and the
+  solid collision Eq. 7 / 8 / 9 -> force and torque Eq. 10 / 11 -> streaming
+  Eq. 1.
+* :func:`voxelize`, :func:`remap` -- the super-sampled geometry field and its
+  per-step interpolation onto the lattice (Sec. 3).
+* :class:`TangentSim` -- the same code on dual numbers: exact directional
+  derivatives of the force/torque series (the reference the adjoint is
+  checked against).
+
+Parity status: every function above is pinned by the tests in
+``tests/test_oracle_*.py`` (closed forms, invariants, brute force).  The torque
+magnitude of the synthetic rotor has no pin beyond those invariants
+(parity unpinned for that value).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "psm_oracle.cpp")
+_SO = os.path.join(_HERE, "liboracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+KIND_SPHERE, KIND_ELLIPSOID, KIND_BOX, KIND_ROTOR = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (g++, FP contraction off)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-o", tmp, _SRC]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P = ctypes.POINTER
+            d, i, l, vp = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
+            dp, ip, u8p = P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_uint8)
+            sig = {
+                "or_lattice": (i, [i, ip, dp, ip]),
+                "or_feq": (d, [i, i, d, dp]),
+                "or_weighting": (d, [i, d, d]),
+                "or_shape_box": (i, [i, dp, ip, dp]),
+                "or_voxelize": (i, [i, dp, i, u8p]),
+                "or_inside": (i, [i, dp, d, d, d]),
+                "or_remap": (i, [u8p, i, i, i, i, dp, dp, dp, dp, dp, l, i, i, i, dp]),
+                "or_pose": (i, [dp, dp, dp, dp, l, dp, dp]),
+                "or_create": (vp, [vp]),
+                "or_destroy": (None, [vp]),
+                "or_set_threads": (i, [vp, i]),
+                "or_get_threads": (i, [vp]),
+                "or_add_body": (i, [vp, u8p, i, i, i, i, dp, dp, dp, dp, dp]),
+                "or_init_eq": (i, [vp, d, dp]),
+                "or_set_body_us_omega": (i, [vp, i, dp]),
+                "or_set_f": (i, [vp, dp]),
+                "or_get_f": (i, [vp, dp]),
+                "or_set_delta": (i, [vp, dp]),
+                "or_step": (i, [vp, i]),
+                "or_step_count": (l, [vp]),
+                "or_ft": (i, [vp, dp]),
+                "or_eps": (i, [vp, l, dp, ip]),
+                "or_macroscopic": (i, [vp, dp, dp]),
+                "ort_create": (vp, [vp, dp]),
+                "ort_destroy": (None, [vp]),
+                "ort_set_threads": (i, [vp, i]),
+                "ort_add_body": (i, [vp, u8p, i, i, i, i, dp, dp, dp, dp, dp, dp]),
+                "ort_init_eq": (i, [vp, d, dp, dp]),
+                "ort_set_delta": (i, [vp, dp, dp]),
+                "ort_step": (i, [vp, i]),
+                "ort_ft": (i, [vp, dp, dp]),
+                "ort_get_f": (i, [vp, dp, dp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _d3(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [
+        ("Q", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("bc_z", ctypes.c_int), ("walls_y", ctypes.c_int),
+        ("wall_u_lo", ctypes.c_double * 3), ("wall_u_hi", ctypes.c_double * 3),
+        ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("u_in", ctypes.c_double * 3),
+        ("fluid", ctypes.c_int), ("tau", ctypes.c_double), ("trt_lambda", ctypes.c_double),
+        ("solid", ctypes.c_int), ("weighting", ctypes.c_int),
+    ]
+
+
+@dataclass
+class Config:
+    """Oracle configuration (mirrors ``or_config`` in psm_oracle.cpp).
+
+    ``bc_z``: 0 periodic, 1 equilibrium ghost planes f^eq(rho0, u_in) at z=-1 and
+    z=nz.  ``fluid``: 0 BGK (Eq. 2), 1 TRT.  ``solid``: 1/2/3 = Eq. 7/8/9.
+    ``weighting``: 0 Eq. 5, 1 Eq. 6.  ``walls_y`` and ``force`` are oracle-only
+    (half-way bounce-back walls and a Guo body force, used by the pins).
+    """
+
+    nx: int
+    ny: int
+    nz: int
+    Q: int = 19
+    bc_z: int = 1
+    rho0: float = 1.0
+    u_in: tuple = (0.0, 0.0, 0.0)
+    fluid: int = 0
+    tau: float = 0.8
+    trt_lambda: float = 3.0 / 16.0
+    solid: int = 1
+    weighting: int = 1
+    walls_y: int = 0
+    wall_u_lo: tuple = (0.0, 0.0, 0.0)
+    wall_u_hi: tuple = (0.0, 0.0, 0.0)
+    force: tuple = (0.0, 0.0, 0.0)
+
+    def _c(self):
+        c = _Cfg()
+        c.Q, c.nx, c.ny, c.nz = self.Q, self.nx, self.ny, self.nz
+        c.bc_z, c.walls_y = self.bc_z, self.walls_y
+        for k in range(3):
+            c.wall_u_lo[k] = self.wall_u_lo[k]
+            c.wall_u_hi[k] = self.wall_u_hi[k]
+            c.force[k] = self.force[k]
+            c.u_in[k] = self.u_in[k]
+        c.rho0, c.fluid, c.tau, c.trt_lambda = self.rho0, self.fluid, self.tau, self.trt_lambda
+        c.solid, c.weighting = self.solid, self.weighting
+        return c
+
+
+def lattice(Q: int):
+    """(c[Q,3] int, w[Q], opp[Q]) in the oracle's own direction order."""
+    c = np.zeros((Q, 3), dtype=np.int32)
+    w = np.zeros(Q)
+    opp = np.zeros(Q, dtype=np.int32)
+    rc = _lib().or_lattice(Q, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w),
+                           opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if rc != 0:
+        raise ValueError(f"unsupported stencil Q={Q}")
+    return c.astype(np.int64), w, opp.astype(np.int64)
+
+
+def feq(Q: int, i: int, rho: float, u) -> float:
+    """Eq. 3 (sign-corrected) for direction i of the oracle's order."""
+    u = _d3(u)
+    return _lib().or_feq(Q, i, rho, _dp(u))
+
+
+def weighting(mode: int, eps: float, tau: float) -> float:
+    """B(eps): Eq. 5 (mode 0) or Eq. 6 (mode 1)."""
+    return _lib().or_weighting(mode, eps, tau)
+
+
+def shape_box(kind: int, params):
+    """Coarse-cell dims and body-frame origin of an analytic shape's geometry box."""
+    p = _d3(params)
+    dims = np.zeros(3, dtype=np.int32)
+    lo = np.zeros(3)
+    _lib().or_shape_box(kind, _dp(p), dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(lo))
+    return tuple(int(v) for v in dims), lo
+
+
+def voxelize(kind: int, params, s: int):
+    """Binary super-sampled geometry field of an analytic shape (Sec. 3).
+
+    Returns (sub[nsz, nsy, nsx] uint8, lo[3]); sub-cell size 2^-s, bit = sub-cell
+    centre inside the shape.
+    """
+    p = _d3(params)
+    dims, lo = shape_box(kind, p)
+    n = 1 << s
+    sub = np.zeros((dims[2] * n, dims[1] * n, dims[0] * n), dtype=np.uint8)
+    _lib().or_voxelize(kind, _dp(p), s, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return sub, lo
+
+
+def inside(kind: int, params, x: float, y: float, z: float) -> bool:
+    p = _d3(params)
+    return bool(_lib().or_inside(kind, _dp(p), x, y, z))
+
+
+def pose(Q0, R0, omega, v, n: int):
+    """Rotation Q_n (world <- body, 3x3) and reference point R_n at step n."""
+    Qo = np.zeros(9)
+    Ro = np.zeros(3)
+    _lib().or_pose(_dp(_d3(Q0)), _dp(_d3(R0)), _dp(_d3(omega)), _dp(_d3(v)), int(n), _dp(Qo), _dp(Ro))
+    return Qo.reshape(3, 3), Ro
+
+
+def remap(sub, s, lo, Q0, R0, omega, v, n, shape):
+    """eps[nz, ny, nx] of one body at the pose of step n (Sec. 3)."""
+    sub = np.ascontiguousarray(sub, dtype=np.uint8)
+    nsz, nsy, nsx = sub.shape
+    nx, ny, nz = shape
+    eps = np.zeros((nz, ny, nx))
+    _lib().or_remap(sub.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nsx, nsy, nsz, s, _dp(_d3(lo)),
+                    _dp(_d3(Q0)), _dp(_d3(R0)), _dp(_d3(omega)), _dp(_d3(v)), int(n), nx, ny, nz, _dp(eps))
+    return eps
+
+
+IDENTITY = np.eye(3).reshape(-1)
+
+
+@dataclass
+class BodySpec:
+    """A rigid body for the oracle: geometry field + motion (Sec. 3)."""
+
+    sub: np.ndarray
+    s: int
+    lo: np.ndarray
+    R0: tuple
+    Q0: np.ndarray = field(default_factory=lambda: IDENTITY.copy())
+    omega: tuple = (0.0, 0.0, 0.0)
+    v: tuple = (0.0, 0.0, 0.0)
+
+
+class Sim:
+    """FP64 oracle simulation (two-grid, natural pre-collision state f[Q,nz,ny,nx])."""
+
+    def __init__(self, cfg: Config, threads: int | None = None):
+        self.cfg = cfg
+        self._h = _lib().or_create(ctypes.byref(cfg._c()))
+        if not self._h:
+            raise ValueError("invalid oracle configuration")
+        if threads is not None:
+            _lib().or_set_threads(self._h, int(threads))
+        self.nbodies = 0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib().or_destroy(h)
+            self._h = None
+
+    @property
+    def threads(self) -> int:
+        return _lib().or_get_threads(self._h)
+
+    @property
+    def shape(self):
+        c = self.cfg
+        return (c.Q, c.nz, c.ny, c.nx)
+
+    def add_body(self, b: BodySpec) -> int:
+        sub = np.ascontiguousarray(b.sub, dtype=np.uint8)
+        nsz, nsy, nsx = sub.shape
+        self.nbodies += 1
+        return _lib().or_add_body(self._h, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nsx, nsy, nsz,
+                                  b.s, _dp(_d3(b.lo)), _dp(_d3(b.Q0)), _dp(_d3(b.R0)), _dp(_d3(b.omega)),
+                                  _dp(_d3(b.v)))
+
+    def init_eq(self, rho: float = 1.0, u=(0.0, 0.0, 0.0)):
+        _lib().or_init_eq(self._h, rho, _dp(_d3(u)))
+
+    def set_us_omega(self, body: int, omega):
+        """Angular velocity used in u_s only (the geometry keeps its pose sequence)."""
+        if _lib().or_set_body_us_omega(self._h, int(body), _dp(_d3(omega))) != 0:
+            raise IndexError(body)
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.shape)
+        _lib().or_set_f(self._h, _dp(f))
+
+    def get_f(self):
+        f = np.zeros(self.shape)
+        _lib().or_get_f(self._h, _dp(f))
+        return f
+
+    def set_delta(self, d):
+        if d is None:
+            _lib().or_set_delta(self._h, None)
+            return
+        d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1)
+        _lib().or_set_delta(self._h, _dp(d))
+
+    def step(self, n: int = 1):
+        _lib().or_step(self._h, int(n))
+
+    @property
+    def step_count(self) -> int:
+        return _lib().or_step_count(self._h)
+
+    def force_torque(self):
+        """[steps, nbodies, 6] force and torque ON each body (-S of Eq. 10/11)."""
+        nb = max(self.nbodies, 1)
+        out = np.zeros(max(self.step_count * nb * 6, 1))
+        _lib().or_ft(self._h, _dp(out))
+        return out[: self.step_count * self.nbodies * 6].reshape(self.step_count, self.nbodies, 6)
+
+    def eps(self, n: int | None = None):
+        """(eps[nz,ny,nx], owner[nz,ny,nx]) at the pose of step n (default: current)."""
+        n = self.step_count if n is None else n
+        c = self.cfg
+        e = np.zeros((c.nz, c.ny, c.nx))
+        o = np.zeros((c.nz, c.ny, c.nx), dtype=np.int32)
+        _lib().or_eps(self._h, int(n), _dp(e), o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return e, o
+
+    def macroscopic(self):
+        """(rho[nz,ny,nx], u[nz,ny,nx,3]) with u = j / rho."""
+        c = self.cfg
+        rho = np.zeros((c.nz, c.ny, c.nx))
+        u = np.zeros((c.nz, c.ny, c.nx, 3))
+        _lib().or_macroscopic(self._h, _dp(rho), _dp(u))
+        return rho, u
+
+
+class TangentSim:
+    """Tangent-linear oracle: the same step on dual numbers.
+
+    Seeds are set at construction (``d_u_in``), per body (``d_omega``) and per
+    cell (``set_delta(delta, d_delta)``); :meth:`force_torque` returns values
+    and exact directional derivatives of the force/torque series.  The eps
+    sequence is taken at the nominal angular velocity (frozen geometry).
+    """
+
+    def __init__(self, cfg: Config, d_u_in=(0.0, 0.0, 0.0), threads: int | None = None):
+        self.cfg = cfg
+        self._h = _lib().ort_create(ctypes.byref(cfg._c()), _dp(_d3(d_u_in)))
+        if not self._h:
+            raise ValueError("invalid oracle configuration")
+        if threads is not None:
+            _lib().ort_set_threads(self._h, int(threads))
+        self.nbodies = 0
+        self.steps = 0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib().ort_destroy(h)
+            self._h = None
+
+    @property
+    def shape(self):
+        c = self.cfg
+        return (c.Q, c.nz, c.ny, c.nx)
+
+    def add_body(self, b: BodySpec, d_omega=(0.0, 0.0, 0.0)) -> int:
+        sub = np.ascontiguousarray(b.sub, dtype=np.uint8)
+        nsz, nsy, nsx = sub.shape
+        self.nbodies += 1
+        return _lib().ort_add_body(self._h, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nsx, nsy, nsz,
+                                   b.s, _dp(_d3(b.lo)), _dp(_d3(b.Q0)), _dp(_d3(b.R0)), _dp(_d3(b.omega)),
+                                   _dp(_d3(d_omega)), _dp(_d3(b.v)))
+
+    def init_eq(self, rho: float = 1.0, u=(0.0, 0.0, 0.0), du=(0.0, 0.0, 0.0)):
+        _lib().ort_init_eq(self._h, rho, _dp(_d3(u)), _dp(_d3(du)))
+
+    def set_delta(self, d=None, dd=None):
+        c = self.cfg
+        n = c.nx * c.ny * c.nz
+        d = np.zeros(n) if d is None else np.ascontiguousarray(d, dtype=np.float64).reshape(-1)
+        dd = np.zeros(n) if dd is None else np.ascontiguousarray(dd, dtype=np.float64).reshape(-1)
+        _lib().ort_set_delta(self._h, _dp(d), _dp(dd))
+
+    def step(self, n: int = 1):
+        _lib().ort_step(self._h, int(n))
+        self.steps += n
+
+    def force_torque(self):
+        """(values, tangents), each [steps, nbodies, 6]."""
+        m = self.steps * self.nbodies * 6
+        v = np.zeros(max(m, 1))
+        t = np.zeros(max(m, 1))
+        _lib().ort_ft(self._h, _dp(v), _dp(t))
+        shp = (self.steps, self.nbodies, 6)
+        return v[:m].reshape(shp), t[:m].reshape(shp)
+
+    def get_f(self):
+        v = np.zeros(self.shape)
+        t = np.zeros(self.shape)
+        _lib().ort_get_f(self._h, _dp(v), _dp(t))
+        return v, t
