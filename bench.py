@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Throughput of the PSM-LBM step (arXiv 2502.20049) on GB300: MLUPS and the
+fraction of the HBM roofline, with the CPU oracle timed beside it.
+
+One "step" is one pass of the whole hot path on one batch of cells: body poses,
+remap of the geometry field onto eps, PSM collision (Eq. 4), streaming, and the
+FP64 force/torque reduction -- one fused kernel launch (libpsm, psm_step).
+
+Default workload: D3Q19 TRT, FP32 PDFs, 256^3 lattice, uniform inflow 0.05,
+tau 0.55, an ellipsoid (semi-axes 40/20/8) rotating at 2e-4 rad/step about z
+and remapped every step (synthetic data shaped like the paper's 256^3 GPU
+block).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank runs its own replica of
+the workload (weak scaling, no data-path collective); the time is the maximum
+over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PSM-LBM MLUPS on 1×GB300 and % of HBM roofline; adjoint/forward step cost"
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per cell update of the step kernel, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum over one launch / cells) for the
+# workload and access pattern named in the key; None until captured for the
+# kernel as it is now.
+NCU_BYTES_PER_CELL = {}
+
+
+def workload(name: str, streaming: str):
+    from paper_2502_20049_gb300 import workloads as W
+
+    if name == "c2":
+        case = W.c2_ellipsoid()
+        desc = ("D3Q19 TRT FP32 256^3, inflow 0.05, tau 0.55, ellipsoid 40/20/8 rotating 2e-4 rad/step about z, "
+                "remap every step")
+    elif name == "c5":
+        case = W.c5_large()
+        desc = "D3Q19 BGK FP16-shifted 1024x1024x960, counter-rotating rotor x2, remap every step"
+    elif name == "c3_fp32":
+        case = W.c3_rotor("fp32")
+        desc = "D3Q27 BGK FP32 512x512x640, counter-rotating rotor, remap every step"
+    elif name == "c3_fp16":
+        case = W.c3_rotor("fp16")
+        desc = "D3Q27 BGK FP16-shifted 512x512x640, counter-rotating rotor, remap every step"
+    elif name == "c3_bf16":
+        case = W.c3_rotor("bf16")
+        desc = "D3Q27 BGK BF16-shifted 512x512x640, counter-rotating rotor, remap every step"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    case = case.with_(streaming=streaming)
+    return case, desc
+
+
+def reference_sample(name: str):
+    """The bounded sample the CPU oracle runs per step: the same workload on a
+    48^3 lattice with the body scaled by 48/n (about 0.1 MLUP per step)."""
+    from paper_2502_20049_gb300 import workloads as W
+
+    if name == "c2":
+        return W.c2_ellipsoid(scale=48 / 256, n=48, steps=1)
+    if name == "c5":
+        return W.c5_large(dims=(48, 48, 48), steps=1)
+    storage = name.split("_")[1]
+    return W.c3_rotor(storage, scale=48 / 512, dims=(48, 48, 60), steps=1)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in loaded for k, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(name: str, steps: int = 3):
+    """The oracle as it stands on this host's cores: `steps` steps of the full workload."""
+    from oracle.cases import sim_from_case as oracle_sim
+
+    case, _ = workload(name, "twogrid")
+    case = case.with_(storage="fp64")
+    sim = oracle_sim(case)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    mlups = case.cells * steps / dt / 1e6
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": sim.threads, "kind": "oracle",
+            "sample": f"{steps} steps of the full {case.nx}x{case.ny}x{case.nz} workload, FP64 two-grid, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.cases import sim_from_case as oracle_sim
+
+    case = reference_sample(args.workload)
+    sim = oracle_sim(case)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = case.cells * args.steps / dt / 1e6
+    _, desc = workload(args.workload, args.streaming)
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample_cells": case.cells},
+            "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": sim.threads, "kind": "oracle",
+                             "sample": f"each step one oracle step of the workload on a "
+                                       f"{case.nx}x{case.ny}x{case.nz} lattice (body scaled to fit)"},
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as G
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    G.build()
+    from paper_2502_20049_gb300 import psm
+
+    case, desc = workload(args.workload, args.streaming)
+    stream = torch.cuda.current_stream()
+    sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
+    cells = case.cells
+    sol.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        sol.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t = ev0.elapsed_time(ev1) / 1e3
+    t_max = t
+    if dist:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = cells * args.steps * world / t_max / 1e6
+    ms = t_max / args.steps * 1e3
+
+    # roofline of the step kernel (the only kernel in the step): algorithmic
+    # bytes per launch = 2 Q b per cell (one read, one write of every PDF)
+    bpc = sol.bytes_per_cell_update()
+    achieved = bpc * cells / (t / args.steps) / 1e9
+    peak, peak_kind = peaks()
+    key = f"{args.workload}/{args.streaming}"
+    traffic = NCU_BYTES_PER_CELL.get(key)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": f"hbm_gbs of {peak_kind}",
+                "traffic": None if traffic is None else round(traffic * cells),
+                "algorithmic_bytes_per_cell": bpc}
+
+    # end to end through the public API: every step one psm_step call (the
+    # pose rides in the launch parameters) and a synchronous read of that
+    # step's force/torque into pinned host memory
+    nb = len(case.bodies)
+    out = torch.empty((1, 6), dtype=torch.float64, pin_memory=True)
+    sol.synchronize()
+    e2e_steps = args.steps
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sol.step(1)
+        for b in range(nb):
+            sol.force_torque(b, sol.step_count - 1, 1, out=out)
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": round(cells * e2e_steps * world / t_e2e / 1e6, 1), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": 48 * nb,
+           "note": "per step: psm_step(h, 1) with the body poses as launch parameters, then psm_force_torque "
+                   "into pinned host memory (synchronising)"}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64"}.get(case.storage, "f32"), "data": "synthetic",
+            "config": {"workload": desc, "cells": cells, "streaming": args.streaming, "storage": case.storage,
+                       "stencil": f"D3Q{case.Q}", "parallelism": f"replicas x{world}",
+                       "l2": f"PDF working set {cells * case.Q * psm.STORAGE_BYTES[case.storage] / 1e9:.2f} GB "
+                             f"> 129 MB L2, no flush"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps}
+    ck = clk.summary()
+    if ck:
+        line["clocks"] = ck
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5", "c3_fp32", "c3_fp16", "c3_bf16"])
+    ap.add_argument("--streaming", default="aa", choices=["aa", "twogrid"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

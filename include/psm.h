@@ -1,0 +1,248 @@
+/*
+ * psm.h -- C ABI of libpsm: the Partially Saturated Cells Method (PSM)
+ * lattice Boltzmann hot path on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2502.20049.  One time step n of a solver handle is
+ *   1. the pose of every body at step n (Sec. 3: rotation of the cell centre
+ *      into the body frame, plus a translation),
+ *   2. the remap of the super-sampled binary geometry field onto the per-cell
+ *      solid fraction eps (Sec. 3),
+ *   3. the per-cell PSM collision f* = f + (1 - B) Omega^F + B Omega^S
+ *      (Eq. 4) with Omega^F = BGK (Eq. 2) or TRT, Omega^S = SC1/SC2/SC3
+ *      (Eq. 7/8/9), B = B(eps) (Eq. 5 or Eq. 6), f^eq of Eq. 3 (read with
+ *      -u.u/(2 c_s^2)),
+ *   4. streaming f_i(x + c_i, t + 1) = f*_i(x) (Eq. 1): AA pattern in place, or
+ *      two grids,
+ *   5. the force and torque on every body (Eq. 10 and Eq. 11), reduced in FP64.
+ * It runs fused in one kernel launch per step.
+ *
+ * Conventions:
+ *   - lattice units dx = dt = 1; cell (x, y, z) has its centre at
+ *     (x + 1/2, y + 1/2, z + 1/2);
+ *   - PDF arrays are [Q][nz][ny][nx] (x fastest), in the direction order that
+ *     psm_lattice_velocities() returns;
+ *   - x and y are periodic; z is periodic or bounded by two equilibrium ghost
+ *     planes holding f^eq(rho0, u_in) (populations entering from a ghost plane
+ *     take the ghost value at every step; populations leaving are dropped);
+ *   - PDFs are stored shifted, f_i - w_i rho0, in the storage precision;
+ *     collision arithmetic is FP64 for PSM_FP64 storage and FP32 otherwise;
+ *     force/torque sums are FP64;
+ *   - the force/torque returned is the one ON THE BODY: minus the sums
+ *     S_F = sum B sum_i Omega^S_i c_i and S_T = sum B (x - R) x sum_i Omega^S_i c_i
+ *     of Eq. 10/11 (which are the momentum the solid gives the fluid).
+ *
+ * Pointers: every array argument may be a host pointer (pageable or pinned)
+ * or a device pointer of the current device; the library copies with
+ * cudaMemcpyDefault.  The library owns all device memory it allocates and
+ * frees it in psm_destroy.  Calls on one handle are not thread safe.
+ *
+ * Errors: every function returns PSM_OK (0) or a negative PSM_ERR_* code and
+ * records a message readable with psm_last_error() (thread local).  No C++
+ * exception crosses the ABI and no kernel traps.
+ */
+#ifndef PSM_H_
+#define PSM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSM_OK 0
+#define PSM_ERR_ARG (-1)         /* invalid argument or configuration */
+#define PSM_ERR_CUDA (-2)        /* a CUDA runtime call or a launch failed */
+#define PSM_ERR_OOM (-3)         /* device or host allocation failed */
+#define PSM_ERR_NONFINITE (-4)   /* a reduced result is NaN or infinite */
+#define PSM_ERR_STATE (-5)       /* call out of order (e.g. backward before a recorded forward) */
+#define PSM_ERR_UNSUPPORTED (-6) /* valid but not implemented combination */
+
+#define PSM_MAX_BODIES 4
+
+/* psm_lattice.stencil */
+#define PSM_D3Q19 19
+#define PSM_D3Q27 27
+/* psm_lattice.streaming */
+#define PSM_STREAM_AA 0       /* in place, one PDF copy (AA pattern, Sec. 2.2) */
+#define PSM_STREAM_TWO_GRID 1 /* two PDF copies, push from the own cell */
+/* psm_lattice.storage: PDF storage precision (values stored as f_i - w_i rho0) */
+#define PSM_FP64 0
+#define PSM_FP32 1
+#define PSM_FP16_SHIFTED 2
+#define PSM_BF16_SHIFTED 3
+/* psm_collision.fluid */
+#define PSM_BGK 0 /* single relaxation time, Eq. 2 */
+#define PSM_TRT 1 /* two relaxation times: omega+ = 1/tau, Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) */
+/* psm_collision.solid: SC1 (Eq. 7), SC2 (Eq. 8 as printed: u_s in both brackets), SC3 (Eq. 9) */
+#define PSM_SC1 1
+#define PSM_SC2 2
+#define PSM_SC3 3
+/* psm_collision.weighting */
+#define PSM_B_DIRECT 0        /* B = eps, Eq. 5 */
+#define PSM_B_TAU_WEIGHTED 1  /* B = eps (tau - 1/2) / ((1 - eps) + (tau - 1/2)), Eq. 6 */
+/* psm_grid.bc_z */
+#define PSM_BC_PERIODIC 0
+#define PSM_BC_EQ_INLET_OUTLET 1
+
+typedef struct psm_solver* psm_handle;
+
+/* Grid: nx*ny*nz cells (each >= 1, nx*ny*nz < 2^32), rho0 > 0, |u_in| < 0.3. */
+typedef struct {
+  int64_t nx, ny, nz;
+  int bc_z;          /* PSM_BC_PERIODIC or PSM_BC_EQ_INLET_OUTLET */
+  double rho0;       /* reference density: storage shift and ghost-plane density */
+  double u_in[3];    /* ghost-plane velocity */
+} psm_grid;
+
+typedef struct {
+  int stencil;   /* PSM_D3Q19 or PSM_D3Q27 */
+  int streaming; /* PSM_STREAM_AA or PSM_STREAM_TWO_GRID */
+  int storage;   /* PSM_FP64, PSM_FP32, PSM_FP16_SHIFTED, PSM_BF16_SHIFTED */
+} psm_lattice;
+
+typedef struct {
+  int fluid;          /* PSM_BGK or PSM_TRT */
+  double tau;         /* relaxation time, > 1/2 (TRT: 1/omega+) */
+  double trt_lambda;  /* TRT Lambda (> 0); ignored for BGK.  3/16 is the usual choice */
+  int solid;          /* PSM_SC1, PSM_SC2 or PSM_SC3 */
+  int weighting;      /* PSM_B_DIRECT or PSM_B_TAU_WEIGHTED */
+} psm_collision;
+
+/*
+ * Super-sampled binary geometry field of one body (Sec. 3), in the body frame.
+ * The body-frame box [lo, lo + (gx, gy, gz)) is split into gx*gy*gz coarse
+ * cells of size 1, each into (2^s)^3 sub-cells of size 2^-s (0 <= s <= 3).
+ * A bit is 1 iff the sub-cell centre is inside the body.  Bits are packed per
+ * coarse cell ("brick") into words_per_brick = max(1, 8^s / 64) 64-bit words:
+ * bit b = (sz * 2^s + sy) * 2^s + sx of the brick, word b / 64, bit b % 64,
+ * with (sx, sy, sz) the sub-cell offsets inside the coarse cell.  Bricks are
+ * ordered [gz][gy][gx] (gx fastest).  bricks holds gx*gy*gz*words_per_brick
+ * words.
+ */
+typedef struct {
+  const uint64_t* bricks;
+  int64_t gx, gy, gz;
+  int s;
+  double lo[3];
+} psm_geom_field;
+
+/* Synthetic rotor (hub cylinder plus twisted thin elliptic blades), body frame
+ * with the hub axis along z:
+ *   hub: sqrt(x^2 + y^2) <= r_hub and |z| <= hub_len / 2;
+ *   blade k (0 <= k < n_blades) at azimuth phase + 2 pi k / n_blades, for
+ *   r_hub <= r <= r_hub + span: with t = r * wrap(phi - azimuth) (wrap into
+ *   [-pi, pi)), beta = hand * (pitch_root_deg - twist_deg (r - r_hub) / span)
+ *   in radians, xi = t cos(beta) + z sin(beta), eta = -t sin(beta) + z cos(beta),
+ *   inside iff (xi / (chord/2))^2 + (eta / (thickness/2))^2 <= 1. */
+typedef struct {
+  double r_hub, hub_len, span, chord, thickness, pitch_root_deg, twist_deg, phase;
+  int n_blades;
+  int hand; /* +1 or -1 */
+} psm_rotor;
+
+/* ------------------------------------------------------------------------ */
+/* Library information                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next call on this thread. */
+const char* psm_last_error(void);
+
+/* Lattice velocities (c_out: stencil*3 ints, may be NULL), weights (w_out:
+ * stencil doubles, may be NULL) and opposite indices (opp_out, may be NULL)
+ * in the library's direction order.  Host only; no GPU needed. */
+int psm_lattice_velocities(int stencil, int* c_out, double* w_out, int* opp_out);
+
+/* ------------------------------------------------------------------------ */
+/* Geometry fields of analytic bodies (host helpers, no GPU needed)          */
+/* ------------------------------------------------------------------------ */
+/* Each voxeliser fills *out with a newly allocated host field (free it with
+ * psm_geom_free).  Box rule: per axis, with e the body's half extent,
+ * m = floor(e) + 2, lo = -m and 2m coarse cells, so sub-cell boundaries fall
+ * on integers of the body frame.  Bits are set iff the sub-cell centre
+ * satisfies the body's inside test (a point on the surface is inside). */
+
+/* Sphere x^2 + y^2 + z^2 <= r^2. */
+int psm_geom_voxelize_sphere(double r, int s, psm_geom_field* out);
+/* Ellipsoid (x/a)^2 + (y/b)^2 + (z/c)^2 <= 1. */
+int psm_geom_voxelize_ellipsoid(double a, double b, double c, int s, psm_geom_field* out);
+/* Box |x| <= hx, |y| <= hy, |z| <= hz. */
+int psm_geom_voxelize_box(double hx, double hy, double hz, int s, psm_geom_field* out);
+/* Synthetic rotor (see psm_rotor). */
+int psm_geom_voxelize_rotor(const psm_rotor* rotor, int s, psm_geom_field* out);
+/* Release a field returned by a voxeliser (bricks set to NULL). */
+int psm_geom_free(psm_geom_field* field);
+
+/* ------------------------------------------------------------------------ */
+/* Solver                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a solver on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * the legacy default stream) on which every kernel of this handle runs.
+ * Validates tau > 1/2, |u_in| < 0.3, rho0 > 0, trt_lambda > 0, the grid size
+ * and the enum values (PSM_ERR_ARG), allocates the PDF buffer(s) and the
+ * reduction scratch (PSM_ERR_OOM).  The PDFs are initialised to the
+ * equilibrium f^eq(rho0, u_in).  The step counter starts at 0. */
+int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision, void* stream,
+               psm_handle* out);
+
+/* Free everything the handle owns.  NULL is accepted. */
+int psm_destroy(psm_handle h);
+
+/* Set every cell to f^eq(rho, u) (Eq. 3), keeping the step counter; populations
+ * entering from a z ghost plane take the ghost value. */
+int psm_init_equilibrium(psm_handle h, double rho, const double u[3]);
+
+/* Import / export the full PDF state, natural layout, FP64, unshifted f,
+ * [Q][nz][ny][nx] in the library's direction order (Q*nx*ny*nz doubles).
+ * Import rounds to the storage precision.  Export of a state in the AA
+ * "swapped" layout (after an odd number of AA steps) undoes the swap. */
+int psm_set_state(psm_handle h, const double* f);
+int psm_get_state(psm_handle h, double* f);
+
+/* Density and velocity u = j / rho per cell: rho[nz][ny][nx], u[nz][ny][nx][3] (FP64). */
+int psm_get_macroscopic(psm_handle h, double* rho, double* u);
+
+/* Solid fraction eps (Sec. 3, all bodies combined: min(1, sum_b eps_b)) at the
+ * pose of the current step counter: eps[nz][ny][nx] (float; exact multiples
+ * of 2^-3s). */
+int psm_get_eps(psm_handle h, float* eps);
+
+/* Attach body `body` (0 <= body < PSM_MAX_BODIES; bodies are used in id order
+ * and must be set contiguously from 0).  The field is copied to the device
+ * once.  Motion: pose at step n is Q_n = Rot(omega/|omega|, |omega| n) Q0
+ * (Rodrigues), R_n = R0 + v n; Q0 is row-major world <- body; R0 is the
+ * reference point (centre of rotation, torque reference).  Solid velocity
+ * u_s(x) = omega x (x - R_n) + v.  Replacing a body is allowed. */
+int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const double Q0[9], const double R0[3],
+                     const double omega[3], const double v[3]);
+
+/* Number of bodies attached. */
+int psm_num_bodies(psm_handle h, int* out);
+
+/* Run n >= 0 time steps asynchronously on the handle's stream (one fused
+ * kernel launch per step; no host synchronisation). */
+int psm_step(psm_handle h, int n);
+
+/* Step counter (steps taken since creation). */
+int psm_step_count(psm_handle h, int64_t* out);
+
+/* Force (3) and torque (3) on body `body` for steps [step_from, step_from +
+ * count): out[count][6] (FP64).  Synchronises the stream.  Only the last
+ * psm_series_capacity() steps are kept (PSM_ERR_ARG for older steps).
+ * PSM_ERR_NONFINITE if any returned value is NaN or infinite. */
+int psm_force_torque(psm_handle h, int body, int64_t step_from, int64_t count, double* out);
+int psm_series_capacity(psm_handle h, int64_t* out);
+
+/* Total mass sum_x sum_i f_i (FP64, deterministic order).  Synchronises.
+ * PSM_ERR_NONFINITE if it is not finite. */
+int psm_mass(psm_handle h, double* out);
+
+/* Wait for all work of the handle. */
+int psm_synchronize(psm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSM_H_ */

@@ -1,0 +1,685 @@
+// Host side of the libpsm C ABI (include/psm.h): handle, validation, device
+// memory, per-step body poses (Sec. 3), kernel dispatch and the diagnostics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "psm_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a non-sticky error
+  return fail(e == cudaErrorMemoryAllocation ? PSM_ERR_OOM : PSM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PSM_CUDA(call, what)                      \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+size_t storage_bytes(int st) {
+  switch (st) {
+    case PSM_FP64: return 8;
+    case PSM_FP32: return 4;
+    default: return 2;
+  }
+}
+
+struct HostBody {
+  unsigned long long* d_bricks = nullptr;
+  int64_t gx = 0, gy = 0, gz = 0;
+  int s = 0, wpb = 1;
+  double lo[3] = {0, 0, 0};
+  double Q0[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double R0[3] = {0, 0, 0};
+  double omega[3] = {0, 0, 0};
+  double v[3] = {0, 0, 0};
+};
+
+// Pose at step n: Q_n = Rot(k, th) Q0 with k = omega/|omega|, th = |omega| n
+// (Rodrigues: cos(th) I + sin(th) [k]x + (1 - cos(th)) k k^T), R_n = R0 + v n.
+void body_pose(const HostBody& b, int64_t n, double Q[9], double R[3]) {
+  const double wn = std::sqrt(b.omega[0] * b.omega[0] + b.omega[1] * b.omega[1] + b.omega[2] * b.omega[2]);
+  double Rt[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (wn > 0.0) {
+    const double k0 = b.omega[0] / wn, k1 = b.omega[1] / wn, k2 = b.omega[2] / wn;
+    const double th = wn * double(n);
+    const double c = std::cos(th), s = std::sin(th), oc = 1.0 - c;
+    Rt[0] = c + oc * k0 * k0;
+    Rt[1] = oc * k0 * k1 - s * k2;
+    Rt[2] = oc * k0 * k2 + s * k1;
+    Rt[3] = oc * k1 * k0 + s * k2;
+    Rt[4] = c + oc * k1 * k1;
+    Rt[5] = oc * k1 * k2 - s * k0;
+    Rt[6] = oc * k2 * k0 - s * k1;
+    Rt[7] = oc * k2 * k1 + s * k0;
+    Rt[8] = c + oc * k2 * k2;
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      Q[3 * r + c] = (Rt[3 * r + 0] * b.Q0[0 + c] + Rt[3 * r + 1] * b.Q0[3 + c]) + Rt[3 * r + 2] * b.Q0[6 + c];
+  for (int k = 0; k < 3; ++k) R[k] = b.R0[k] + b.v[k] * double(n);
+}
+
+}  // namespace
+
+struct psm_solver {
+  psm_grid grid;
+  psm_lattice lat;
+  psm_collision col;
+  psm::Grid3 g;
+  psm::Tiling tiling;
+  cudaStream_t stream = nullptr;
+  int Q = 19;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  int64_t step = 0;
+  int nbodies = 0;
+  HostBody body[PSM_MAX_BODIES];
+  double ghost[27];
+  int max_blocks = 0;
+  double* d_partials = nullptr;
+  unsigned int* d_ticket = nullptr;
+  double* d_series = nullptr;
+  int64_t cap = 0;
+  double* d_sum = nullptr;
+  float* d_delta = nullptr;
+};
+
+namespace psm {
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+Tiling make_tiling(int nx, int ny, int nz) {
+  Tiling t;
+  int tx = ((nx + 31) / 32) * 32;
+  if (tx > PSM_THREADS) tx = PSM_THREADS;
+  t.tx = tx;
+  t.ty = PSM_THREADS / tx;
+  t.ntx = (nx + t.tx - 1) / t.tx;
+  t.nty = (ny + t.ty - 1) / t.ty;
+  t.ntiles = (long long)t.ntx * t.nty * nz;
+  return t;
+}
+
+cudaError_t launch_step(int storage, int Q, int mode, const StepParams& p, cudaStream_t st) {
+  switch (storage) {
+    case PSM_FP64: return launch_step_fp64(Q, mode, p.trt, p, st);
+    case PSM_FP32: return launch_step_fp32(Q, mode, p.trt, p, st);
+    case PSM_FP16_SHIFTED: return launch_step_fp16(Q, mode, p.trt, p, st);
+    default: return launch_step_bf16(Q, mode, p.trt, p, st);
+  }
+}
+int step_grid_blocks(int storage, int Q, int mode, int trt) {
+  switch (storage) {
+    case PSM_FP64: return step_grid_blocks_fp64(Q, mode, trt);
+    case PSM_FP32: return step_grid_blocks_fp32(Q, mode, trt);
+    case PSM_FP16_SHIFTED: return step_grid_blocks_fp16(Q, mode, trt);
+    default: return step_grid_blocks_bf16(Q, mode, trt);
+  }
+}
+#define PSM_IO_DISPATCH(FN)                                                    \
+  cudaError_t launch_##FN(int storage, int Q, const IoParams& p, cudaStream_t st) { \
+    switch (storage) {                                                         \
+      case PSM_FP64: return launch_##FN##_fp64(Q, p, st);                      \
+      case PSM_FP32: return launch_##FN##_fp32(Q, p, st);                      \
+      case PSM_FP16_SHIFTED: return launch_##FN##_fp16(Q, p, st);              \
+      default: return launch_##FN##_bf16(Q, p, st);                            \
+    }                                                                          \
+  }
+PSM_IO_DISPATCH(import)
+PSM_IO_DISPATCH(export)
+PSM_IO_DISPATCH(macro)
+cudaError_t launch_mass(int storage, int Q, const IoParams& p, int blocks, cudaStream_t st) {
+  switch (storage) {
+    case PSM_FP64: return launch_mass_fp64(Q, p, blocks, st);
+    case PSM_FP32: return launch_mass_fp32(Q, p, blocks, st);
+    case PSM_FP16_SHIFTED: return launch_mass_fp16(Q, p, blocks, st);
+    default: return launch_mass_bf16(Q, p, blocks, st);
+  }
+}
+
+__global__ void k_remap(const __grid_constant__ RemapParams p) {
+  const long long plane = (long long)p.g.nx * p.g.ny;
+  const long long n = plane * (p.z_end - p.z_begin);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int z = p.z_begin + (int)(idx / plane);
+    const long long r = idx % plane;
+    const int y = (int)(r / p.g.nx), x = (int)(r % p.g.nx);
+    int owner;
+    p.eps_out[idx] = cell_eps(p.body, p.nbodies, x, y, z, owner);
+  }
+}
+
+cudaError_t launch_remap(const RemapParams& p, cudaStream_t st) {
+  long long cells = (long long)p.g.nx * p.g.ny * (p.z_end - p.z_begin);
+  long long b = (cells + PSM_THREADS - 1) / PSM_THREADS;
+  if (b > 4096) b = 4096;
+  k_remap<<<(int)(b < 1 ? 1 : b), PSM_THREADS, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace psm
+
+namespace {
+
+using psm::DevBody;
+using psm::IoParams;
+using psm::StepParams;
+
+void fill_ghost(psm_solver* h) {
+  const double* u = h->grid.u_in;
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int i = 0; i < 27; ++i) h->ghost[i] = 0.0;
+  for (int i = 0; i < h->Q; ++i) {
+    const double w = h->Q == 19 ? psm::lat_w<19>(i) : psm::lat_w<27>(i);
+    const double cu = psm::lat_cx(i) * u[0] + psm::lat_cy(i) * u[1] + psm::lat_cz(i) * u[2];
+    const double fe = w * h->grid.rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    h->ghost[i] = fe - w * h->grid.rho0;
+  }
+}
+
+// Device view of body b at step n, including the world box of cells whose
+// eps can be non-zero: the axis-aligned hull of the rotated geometry box,
+// widened by 2.5 cells (a cell's sub-cell block reaches at most
+// sqrt(3) (1/2 + 2^-s / 2) < 1.75 from its centre).
+DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
+  const HostBody& b = h->body[bi];
+  DevBody d;
+  std::memset(&d, 0, sizeof d);
+  double Q[9], R[3];
+  body_pose(b, n, Q, R);
+  d.bricks = b.d_bricks;
+  d.gx = (int)b.gx;
+  d.gy = (int)b.gy;
+  d.gz = (int)b.gz;
+  d.s = b.s;
+  d.wpb = b.wpb;
+  for (int k = 0; k < 9; ++k) d.Qf[k] = (float)Q[k];
+  for (int k = 0; k < 3; ++k) {
+    d.Rf[k] = (float)R[k];
+    d.Cf[k] = (float)(b.lo[k] + 0.5);
+    d.R[k] = R[k];
+    d.omega[k] = b.omega[k];
+    d.v[k] = b.v[k];
+  }
+  double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+  const double ext[3] = {(double)b.gx, (double)b.gy, (double)b.gz};
+  for (int c = 0; c < 8; ++c) {
+    double pb[3];
+    for (int k = 0; k < 3; ++k) pb[k] = b.lo[k] + (((c >> k) & 1) ? ext[k] : 0.0);
+    for (int r = 0; r < 3; ++r) {
+      const double w = Q[3 * r + 0] * pb[0] + Q[3 * r + 1] * pb[1] + Q[3 * r + 2] * pb[2] + R[r];
+      mn[r] = std::fmin(mn[r], w);
+      mx[r] = std::fmax(mx[r], w);
+    }
+  }
+  const int64_t dims[3] = {h->grid.nx, h->grid.ny, h->grid.nz};
+  int lo_[3], hi_[3];
+  for (int k = 0; k < 3; ++k) {
+    double a = std::floor(mn[k] - 2.5), e = std::ceil(mx[k] + 2.5) + 1.0;
+    if (a < 0) a = 0;
+    if (e > (double)dims[k]) e = (double)dims[k];
+    if (e < a) e = a;
+    lo_[k] = (int)a;
+    hi_[k] = (int)e;
+  }
+  d.x0 = lo_[0];
+  d.x1 = hi_[0];
+  d.y0 = lo_[1];
+  d.y1 = hi_[1];
+  d.z0 = lo_[2];
+  d.z1 = hi_[2];
+  return d;
+}
+
+int layout_of(const psm_solver* h) {
+  if (h->lat.streaming == PSM_STREAM_TWO_GRID) return psm::LAYOUT_NATURAL;
+  return (h->step & 1) ? psm::LAYOUT_SWAPPED : psm::LAYOUT_NATURAL;
+}
+
+void io_base(const psm_solver* h, IoParams& p) {
+  std::memset(&p, 0, sizeof p);
+  p.g = h->g;
+  p.t = h->tiling;
+  p.f = h->buf[h->cur];
+  p.layout = layout_of(h);
+  for (int i = 0; i < 27; ++i) p.ghost[i] = h->ghost[i];
+  p.rho0 = h->grid.rho0;
+}
+
+// planes per chunk so that one chunk of `per_cell` bytes stays near 64 MiB
+int chunk_planes(const psm_solver* h, size_t per_cell) {
+  const size_t plane = (size_t)h->grid.nx * h->grid.ny * per_cell;
+  size_t p = (64u << 20) / (plane ? plane : 1);
+  if (p < 1) p = 1;
+  if (p > (size_t)h->grid.nz) p = (size_t)h->grid.nz;
+  return (int)p;
+}
+
+int import_uniform(psm_solver* h, double rho, const double u[3]) {
+  IoParams p;
+  io_base(h, p);
+  p.uniform = 1;
+  p.rho = rho;
+  for (int k = 0; k < 3; ++k) p.u[k] = u[k];
+  p.z_begin = 0;
+  p.z_end = (int)h->grid.nz;
+  PSM_CUDA(psm::launch_import(h->lat.storage, h->Q, p, h->stream), "import kernel");
+  return PSM_OK;
+}
+
+bool valid_handle(psm_handle h) { return h != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char* psm_last_error(void) { return g_err.c_str(); }
+
+int psm_lattice_velocities(int stencil, int* c_out, double* w_out, int* opp_out) {
+  if (stencil != PSM_D3Q19 && stencil != PSM_D3Q27) return fail(PSM_ERR_ARG, "stencil must be 19 or 27");
+  for (int i = 0; i < stencil; ++i) {
+    if (c_out) {
+      c_out[3 * i + 0] = psm::lat_cx(i);
+      c_out[3 * i + 1] = psm::lat_cy(i);
+      c_out[3 * i + 2] = psm::lat_cz(i);
+    }
+    if (w_out) w_out[i] = stencil == 19 ? psm::lat_w<19>(i) : psm::lat_w<27>(i);
+    if (opp_out) opp_out[i] = psm::lat_opp(i);
+  }
+  return PSM_OK;
+}
+
+int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision, void* stream,
+               psm_handle* out) {
+  if (!grid || !lattice || !collision || !out) return fail(PSM_ERR_ARG, "psm_create: NULL argument");
+  *out = nullptr;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(PSM_ERR_ARG, "grid sizes must be >= 1");
+  if (grid->nx > (1 << 30) || grid->ny > (1 << 30) || grid->nz > (1 << 30))
+    return fail(PSM_ERR_ARG, "grid size per axis must be < 2^30");
+  const double ncell = (double)grid->nx * (double)grid->ny * (double)grid->nz;
+  if (ncell >= 4294967296.0) return fail(PSM_ERR_ARG, "nx*ny*nz must be < 2^32");
+  if (grid->bc_z != PSM_BC_PERIODIC && grid->bc_z != PSM_BC_EQ_INLET_OUTLET) return fail(PSM_ERR_ARG, "bad bc_z");
+  if (!(grid->rho0 > 0.0) || !std::isfinite(grid->rho0)) return fail(PSM_ERR_ARG, "rho0 must be > 0");
+  const double un = std::sqrt(grid->u_in[0] * grid->u_in[0] + grid->u_in[1] * grid->u_in[1] +
+                              grid->u_in[2] * grid->u_in[2]);
+  if (!(un < 0.3)) return fail(PSM_ERR_ARG, "|u_in| must be < 0.3 (lattice units)");
+  if (lattice->stencil != PSM_D3Q19 && lattice->stencil != PSM_D3Q27) return fail(PSM_ERR_ARG, "bad stencil");
+  if (lattice->streaming != PSM_STREAM_AA && lattice->streaming != PSM_STREAM_TWO_GRID)
+    return fail(PSM_ERR_ARG, "bad streaming");
+  if (lattice->storage < PSM_FP64 || lattice->storage > PSM_BF16_SHIFTED) return fail(PSM_ERR_ARG, "bad storage");
+  if (collision->fluid != PSM_BGK && collision->fluid != PSM_TRT) return fail(PSM_ERR_ARG, "bad fluid collision");
+  if (!(collision->tau > 0.5) || !std::isfinite(collision->tau)) return fail(PSM_ERR_ARG, "tau must be > 1/2");
+  if (collision->fluid == PSM_TRT && !(collision->trt_lambda > 0.0)) return fail(PSM_ERR_ARG, "trt_lambda must be > 0");
+  if (collision->solid < PSM_SC1 || collision->solid > PSM_SC3) return fail(PSM_ERR_ARG, "bad solid collision");
+  if (collision->weighting != PSM_B_DIRECT && collision->weighting != PSM_B_TAU_WEIGHTED)
+    return fail(PSM_ERR_ARG, "bad weighting");
+
+  psm_solver* h = new (std::nothrow) psm_solver();
+  if (!h) return fail(PSM_ERR_OOM, "host allocation failed");
+  h->grid = *grid;
+  h->lat = *lattice;
+  h->col = *collision;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->Q = lattice->stencil;
+  h->g.nx = (int)grid->nx;
+  h->g.ny = (int)grid->ny;
+  h->g.nz = (int)grid->nz;
+  h->g.ncell = (long long)grid->nx * grid->ny * grid->nz;
+  h->g.bc_z = grid->bc_z;
+  h->tiling = psm::make_tiling(h->g.nx, h->g.ny, h->g.nz);
+  fill_ghost(h);
+
+  auto cleanup = [&](int rc) {
+    psm_destroy(h);
+    return rc;
+  };
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "no CUDA device"));
+  h->max_blocks = sms * (2048 / psm::PSM_THREADS);
+  const size_t bytes = (size_t)h->Q * (size_t)h->g.ncell * storage_bytes(lattice->storage);
+  const int nbuf = lattice->streaming == PSM_STREAM_TWO_GRID ? 2 : 1;
+  for (int b = 0; b < nbuf; ++b) {
+    e = cudaMalloc(&h->buf[b], bytes);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "PDF buffer allocation"));
+  }
+  e = cudaMalloc(&h->d_partials, sizeof(double) * (size_t)h->max_blocks * PSM_MAX_BODIES * 6);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_ticket, sizeof(unsigned int));
+  h->cap = 1 << 16;
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_series, sizeof(double) * (size_t)h->cap * PSM_MAX_BODIES * 6);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_sum, sizeof(double) * 8);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch allocation"));
+  e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->d_series, 0, sizeof(double) * (size_t)h->cap * PSM_MAX_BODIES * 6, h->stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch initialisation"));
+  int rc = import_uniform(h, grid->rho0, grid->u_in);
+  if (rc != PSM_OK) return cleanup(rc);
+  *out = h;
+  return PSM_OK;
+}
+
+int psm_destroy(psm_handle h) {
+  if (!h) return PSM_OK;
+  if (h->stream || h->buf[0]) cudaStreamSynchronize(h->stream);
+  for (int b = 0; b < 2; ++b) cudaFree(h->buf[b]);
+  for (int b = 0; b < PSM_MAX_BODIES; ++b) cudaFree(h->body[b].d_bricks);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_ticket);
+  cudaFree(h->d_series);
+  cudaFree(h->d_sum);
+  cudaFree(h->d_delta);
+  delete h;
+  return PSM_OK;
+}
+
+int psm_init_equilibrium(psm_handle h, double rho, const double u[3]) {
+  if (!valid_handle(h) || !u) return fail(PSM_ERR_ARG, "psm_init_equilibrium: NULL argument");
+  if (!(rho > 0.0)) return fail(PSM_ERR_ARG, "rho must be > 0");
+  return import_uniform(h, rho, u);
+}
+
+int psm_set_state(psm_handle h, const double* f) {
+  if (!valid_handle(h) || !f) return fail(PSM_ERR_ARG, "psm_set_state: NULL argument");
+  const int planes = chunk_planes(h, sizeof(double) * h->Q);
+  const size_t plane = (size_t)h->grid.nx * h->grid.ny;
+  double* tmp = nullptr;
+  PSM_CUDA(cudaMalloc(&tmp, sizeof(double) * h->Q * plane * planes), "state staging allocation");
+  int rc = PSM_OK;
+  for (int z0 = 0; z0 < h->grid.nz && rc == PSM_OK; z0 += planes) {
+    const int z1 = (int)std::min<int64_t>(h->grid.nz, z0 + planes);
+    const size_t nchunk = plane * (z1 - z0);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < h->Q && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(tmp + (size_t)i * nchunk, f + (size_t)i * h->g.ncell + (size_t)z0 * plane,
+                          sizeof(double) * nchunk, cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "state upload");
+      break;
+    }
+    IoParams p;
+    io_base(h, p);
+    p.z_begin = z0;
+    p.z_end = z1;
+    p.f_in = tmp;
+    e = psm::launch_import(h->lat.storage, h->Q, p, h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "import kernel");
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  return rc;
+}
+
+int psm_get_state(psm_handle h, double* f) {
+  if (!valid_handle(h) || !f) return fail(PSM_ERR_ARG, "psm_get_state: NULL argument");
+  const int planes = chunk_planes(h, sizeof(double) * h->Q);
+  const size_t plane = (size_t)h->grid.nx * h->grid.ny;
+  double* tmp = nullptr;
+  PSM_CUDA(cudaMalloc(&tmp, sizeof(double) * h->Q * plane * planes), "state staging allocation");
+  int rc = PSM_OK;
+  for (int z0 = 0; z0 < h->grid.nz && rc == PSM_OK; z0 += planes) {
+    const int z1 = (int)std::min<int64_t>(h->grid.nz, z0 + planes);
+    const size_t nchunk = plane * (z1 - z0);
+    IoParams p;
+    io_base(h, p);
+    p.z_begin = z0;
+    p.z_end = z1;
+    p.f_out = tmp;
+    cudaError_t e = psm::launch_export(h->lat.storage, h->Q, p, h->stream);
+    for (int i = 0; i < h->Q && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(f + (size_t)i * h->g.ncell + (size_t)z0 * plane, tmp + (size_t)i * nchunk,
+                          sizeof(double) * nchunk, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "state export");
+  }
+  cudaFree(tmp);
+  return rc;
+}
+
+int psm_get_macroscopic(psm_handle h, double* rho, double* u) {
+  if (!valid_handle(h) || !rho || !u) return fail(PSM_ERR_ARG, "psm_get_macroscopic: NULL argument");
+  const int planes = chunk_planes(h, sizeof(double) * 4);
+  const size_t plane = (size_t)h->grid.nx * h->grid.ny;
+  double* tmp = nullptr;
+  PSM_CUDA(cudaMalloc(&tmp, sizeof(double) * 4 * plane * planes), "macroscopic staging allocation");
+  int rc = PSM_OK;
+  for (int z0 = 0; z0 < h->grid.nz && rc == PSM_OK; z0 += planes) {
+    const int z1 = (int)std::min<int64_t>(h->grid.nz, z0 + planes);
+    const size_t nchunk = plane * (z1 - z0);
+    IoParams p;
+    io_base(h, p);
+    p.z_begin = z0;
+    p.z_end = z1;
+    p.rho_out = tmp;
+    p.u_out = tmp + nchunk;
+    cudaError_t e = psm::launch_macro(h->lat.storage, h->Q, p, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rho + (size_t)z0 * plane, tmp, sizeof(double) * nchunk, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(u + 3 * (size_t)z0 * plane, tmp + nchunk, sizeof(double) * 3 * nchunk, cudaMemcpyDefault,
+                          h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "macroscopic export");
+  }
+  cudaFree(tmp);
+  return rc;
+}
+
+int psm_get_eps(psm_handle h, float* eps) {
+  if (!valid_handle(h) || !eps) return fail(PSM_ERR_ARG, "psm_get_eps: NULL argument");
+  const int planes = chunk_planes(h, sizeof(float));
+  const size_t plane = (size_t)h->grid.nx * h->grid.ny;
+  float* tmp = nullptr;
+  PSM_CUDA(cudaMalloc(&tmp, sizeof(float) * plane * planes), "eps staging allocation");
+  int rc = PSM_OK;
+  for (int z0 = 0; z0 < h->grid.nz && rc == PSM_OK; z0 += planes) {
+    const int z1 = (int)std::min<int64_t>(h->grid.nz, z0 + planes);
+    psm::RemapParams p;
+    std::memset(&p, 0, sizeof p);
+    p.g = h->g;
+    p.t = h->tiling;
+    p.nbodies = h->nbodies;
+    for (int b = 0; b < h->nbodies; ++b) p.body[b] = dev_body(h, b, h->step);
+    p.z_begin = z0;
+    p.z_end = z1;
+    p.eps_out = tmp;
+    cudaError_t e = psm::launch_remap(p, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(eps + (size_t)z0 * plane, tmp, sizeof(float) * plane * (z1 - z0), cudaMemcpyDefault,
+                          h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "eps export");
+  }
+  cudaFree(tmp);
+  return rc;
+}
+
+int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const double Q0[9], const double R0[3],
+                     const double omega[3], const double v[3]) {
+  if (!valid_handle(h) || !field || !Q0 || !R0 || !omega || !v)
+    return fail(PSM_ERR_ARG, "psm_set_geometry: NULL argument");
+  if (body < 0 || body >= PSM_MAX_BODIES || body > h->nbodies)
+    return fail(PSM_ERR_ARG, "body id %d: bodies are numbered contiguously from 0 (max %d)", body, PSM_MAX_BODIES);
+  if (field->s < 0 || field->s > 3) return fail(PSM_ERR_ARG, "super-sampling depth s must be 0..3");
+  if (field->gx < 1 || field->gy < 1 || field->gz < 1 || field->gx > (1 << 20) || field->gy > (1 << 20) ||
+      field->gz > (1 << 20))
+    return fail(PSM_ERR_ARG, "geometry field dims must be in 1..2^20");
+  if (!field->bricks) return fail(PSM_ERR_ARG, "geometry field has no bricks");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(field->lo[k]) || !std::isfinite(R0[k]) || !std::isfinite(omega[k]) || !std::isfinite(v[k]))
+      return fail(PSM_ERR_ARG, "non-finite body parameter");
+  const int wpb = field->s == 3 ? 8 : 1;
+  const size_t words = (size_t)field->gx * field->gy * field->gz * wpb;
+  HostBody& b = h->body[body];
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronise before geometry upload");
+  cudaFree(b.d_bricks);
+  b.d_bricks = nullptr;
+  PSM_CUDA(cudaMalloc(&b.d_bricks, words * sizeof(unsigned long long)), "geometry field allocation");
+  PSM_CUDA(cudaMemcpy(b.d_bricks, field->bricks, words * sizeof(unsigned long long), cudaMemcpyDefault),
+           "geometry field upload");
+  b.gx = field->gx;
+  b.gy = field->gy;
+  b.gz = field->gz;
+  b.s = field->s;
+  b.wpb = wpb;
+  for (int k = 0; k < 3; ++k) {
+    b.lo[k] = field->lo[k];
+    b.R0[k] = R0[k];
+    b.omega[k] = omega[k];
+    b.v[k] = v[k];
+  }
+  for (int k = 0; k < 9; ++k) b.Q0[k] = Q0[k];
+  if (body == h->nbodies) h->nbodies++;
+  return PSM_OK;
+}
+
+int psm_num_bodies(psm_handle h, int* out) {
+  if (!valid_handle(h) || !out) return fail(PSM_ERR_ARG, "psm_num_bodies: NULL argument");
+  *out = h->nbodies;
+  return PSM_OK;
+}
+
+int psm_step(psm_handle h, int n) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_step: NULL handle");
+  if (n < 0) return fail(PSM_ERR_ARG, "psm_step: n must be >= 0");
+  StepParams p;
+  std::memset(&p, 0, sizeof p);
+  p.g = h->g;
+  p.t = h->tiling;
+  for (int i = 0; i < 27; ++i) p.ghost[i] = h->ghost[i];
+  p.rho0 = h->grid.rho0;
+  p.tau = h->col.tau;
+  if (h->col.fluid == PSM_TRT) {
+    const double wp = 1.0 / h->col.tau;
+    const double wm = 1.0 / (h->col.trt_lambda / (h->col.tau - 0.5) + 0.5);
+    p.om_a = 0.5 * (wp + wm);
+    p.om_b = 0.5 * (wp - wm);
+    p.trt = 1;
+  } else {
+    p.om_a = 1.0 / h->col.tau;
+    p.om_b = 0.0;
+    p.trt = 0;
+  }
+  p.solid = h->col.solid;
+  p.weighting = h->col.weighting;
+  p.nbodies = h->nbodies;
+  p.delta = h->d_delta;
+  p.partials = h->d_partials;
+  p.ticket = h->d_ticket;
+  for (int k = 0; k < n; ++k) {
+    for (int b = 0; b < h->nbodies; ++b) p.body[b] = dev_body(h, b, h->step);
+    p.ft_out = h->d_series + (size_t)(h->step % h->cap) * PSM_MAX_BODIES * 6;
+    int mode;
+    if (h->lat.streaming == PSM_STREAM_TWO_GRID) {
+      mode = psm::MODE_TG;
+      p.f = h->buf[h->cur];
+      p.f_dst = h->buf[h->cur ^ 1];
+    } else {
+      mode = (h->step & 1) ? psm::MODE_AA_ODD : psm::MODE_AA_EVEN;
+      p.f = h->buf[0];
+      p.f_dst = nullptr;
+    }
+    cudaError_t e = psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    if (h->lat.streaming == PSM_STREAM_TWO_GRID) h->cur ^= 1;
+    h->step++;
+  }
+  return PSM_OK;
+}
+
+int psm_step_count(psm_handle h, int64_t* out) {
+  if (!valid_handle(h) || !out) return fail(PSM_ERR_ARG, "psm_step_count: NULL argument");
+  *out = h->step;
+  return PSM_OK;
+}
+
+int psm_series_capacity(psm_handle h, int64_t* out) {
+  if (!valid_handle(h) || !out) return fail(PSM_ERR_ARG, "psm_series_capacity: NULL argument");
+  *out = h->cap;
+  return PSM_OK;
+}
+
+int psm_force_torque(psm_handle h, int body, int64_t step_from, int64_t count, double* out) {
+  if (!valid_handle(h) || (!out && count > 0)) return fail(PSM_ERR_ARG, "psm_force_torque: NULL argument");
+  if (body < 0 || body >= h->nbodies) return fail(PSM_ERR_ARG, "no body %d", body);
+  if (count < 0 || step_from < 0 || step_from + count > h->step)
+    return fail(PSM_ERR_ARG, "steps [%lld, %lld) not yet computed (step count %lld)", (long long)step_from,
+                (long long)(step_from + count), (long long)h->step);
+  if (step_from < h->step - h->cap)
+    return fail(PSM_ERR_ARG, "step %lld is older than the kept series (%lld steps)", (long long)step_from,
+                (long long)h->cap);
+  PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  const size_t row = PSM_MAX_BODIES * 6;
+  std::vector<double> tmp(row);
+  bool finite = true;
+  // copy in at most two contiguous runs of the ring buffer
+  int64_t done = 0;
+  std::vector<double> rows;
+  while (done < count) {
+    const int64_t s = step_from + done;
+    const int64_t slot = s % h->cap;
+    int64_t run = std::min<int64_t>(count - done, h->cap - slot);
+    rows.resize((size_t)run * row);
+    PSM_CUDA(cudaMemcpy(rows.data(), h->d_series + (size_t)slot * row, sizeof(double) * row * run,
+                        cudaMemcpyDeviceToHost),
+             "force/torque download");
+    for (int64_t r = 0; r < run; ++r)
+      for (int k = 0; k < 6; ++k) {
+        const double v = rows[(size_t)r * row + body * 6 + k];
+        out[(done + r) * 6 + k] = v;
+        finite = finite && std::isfinite(v);
+      }
+    done += run;
+  }
+  if (!finite) return fail(PSM_ERR_NONFINITE, "force/torque series holds NaN or Inf");
+  return PSM_OK;
+}
+
+int psm_mass(psm_handle h, double* out) {
+  if (!valid_handle(h) || !out) return fail(PSM_ERR_ARG, "psm_mass: NULL argument");
+  IoParams p;
+  io_base(h, p);
+  p.z_begin = 0;
+  p.z_end = (int)h->grid.nz;
+  p.partials = h->d_partials;
+  p.ticket = h->d_ticket;
+  p.sum_out = h->d_sum;
+  const long long cells = h->g.ncell;
+  long long blocks = (cells + psm::PSM_THREADS - 1) / psm::PSM_THREADS;
+  if (blocks > h->max_blocks) blocks = h->max_blocks;
+  PSM_CUDA(psm::launch_mass(h->lat.storage, h->Q, p, (int)blocks, h->stream), "mass kernel");
+  PSM_CUDA(cudaMemcpyAsync(out, h->d_sum, sizeof(double), cudaMemcpyDefault, h->stream), "mass download");
+  PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  if (!std::isfinite(*out)) return fail(PSM_ERR_NONFINITE, "mass is NaN or Inf");
+  return PSM_OK;
+}
+
+int psm_synchronize(psm_handle h) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_synchronize: NULL handle");
+  PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  return PSM_OK;
+}
+
+}  // extern "C"

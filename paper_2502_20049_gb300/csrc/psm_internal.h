@@ -1,0 +1,137 @@
+// Internal declarations shared by the host API (psm_api.cu) and the kernel
+// translation units (psm_kern_*.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/psm.h"
+
+namespace psm {
+
+enum Storage { ST_FP64 = PSM_FP64, ST_FP32 = PSM_FP32, ST_FP16 = PSM_FP16_SHIFTED, ST_BF16 = PSM_BF16_SHIFTED };
+
+// Access pattern of one step kernel.
+//   MODE_TG      : read own cell slot i (natural), write slot i of x + c_i in
+//                  the second buffer (two grids, push);
+//   MODE_AA_EVEN : read own slot i (natural), write own slot opp(i) (swapped);
+//   MODE_AA_ODD  : read slot opp(i) of x - c_i (swapped), write slot i of
+//                  x + c_i (natural).
+enum Mode { MODE_TG = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
+
+// Layout a state is stored in, for import / export kernels.
+enum Layout { LAYOUT_NATURAL = 0, LAYOUT_SWAPPED = 1 };
+
+// One body as the kernels see it at one step.
+struct DevBody {
+  const unsigned long long* bricks;  // [gz][gy][gx][wpb] words
+  int gx, gy, gz;
+  int s;    // super-sampling depth
+  int wpb;  // 64-bit words per brick
+  // pose of this step, rounded to float: the remap decides sub-cell indices in float
+  float Qf[9];  // world <- body, row-major
+  float Rf[3];  // reference point R_n
+  float Cf[3];  // lo + 1/2
+  // kinematics in double (converted to the compute precision in the kernel)
+  double R[3];
+  double omega[3];
+  double v[3];
+  // cells tested for this body: [x0, x1) x [y0, y1) x [z0, z1)
+  int x0, x1, y0, y1, z0, z1;
+};
+
+struct Grid3 {
+  int nx, ny, nz;
+  long long ncell;
+  int bc_z;  // PSM_BC_PERIODIC / PSM_BC_EQ_INLET_OUTLET
+};
+
+struct Tiling {
+  int tx, ty;    // threads per block along x, y (tx * ty = PSM_THREADS)
+  int ntx, nty;  // tiles along x, y
+  long long ntiles;
+};
+
+struct StepParams {
+  Grid3 g;
+  Tiling t;
+  void* f;      // AA: the buffer; TG: source
+  void* f_dst;  // TG: destination
+  double ghost[27];  // shifted ghost-plane populations f^eq_i(rho0, u_in) - w_i rho0
+  double rho0;
+  double tau;
+  double om_a, om_b;  // TRT as Omega^F_i = -om_a n_i - om_b n_opp(i); BGK: om_a = 1/tau, om_b = 0
+  int trt;
+  int solid;      // 1, 2, 3
+  int weighting;  // 0 direct, 1 tau-weighted
+  int nbodies;
+  DevBody body[PSM_MAX_BODIES];
+  const float* delta;  // optional additive eps perturbation per cell (nullptr: none)
+  // force/torque reduction
+  double* partials;      // [gridDim.x][nbodies * 6]
+  unsigned int* ticket;  // zero between launches
+  double* ft_out;        // [nbodies * 6] of this step (body convention)
+};
+
+// Parameters of the import / export / reduction kernels.
+struct IoParams {
+  Grid3 g;
+  Tiling t;
+  void* f;
+  int layout;  // Layout
+  double ghost[27];
+  double rho0;
+  int z_begin, z_end;  // z-planes handled by this launch
+  // import: from a natural FP64 state chunk (f_in, planes z_begin..z_end) or uniform (rho, u)
+  const double* f_in;
+  int uniform;
+  double rho, u[3];
+  // export
+  double* f_out;    // natural, unshifted, planes z_begin..z_end
+  double* rho_out;  // macroscopic
+  double* u_out;
+  // reduction
+  double* partials;
+  unsigned int* ticket;
+  double* sum_out;
+};
+
+// Parameters of the stand-alone remap kernel (psm_get_eps).
+struct RemapParams {
+  Grid3 g;
+  Tiling t;
+  int nbodies;
+  DevBody body[PSM_MAX_BODIES];
+  int z_begin, z_end;
+  float* eps_out;
+};
+
+constexpr int PSM_THREADS = 256;
+
+Tiling make_tiling(int nx, int ny, int nz);
+
+// Launchers (one set per storage precision, in psm_kern_<storage>.cu).  Each
+// returns cudaSuccess or the launch error.  `grid_out` reports the number of
+// blocks the step kernel uses (so the host sizes the partials array).
+cudaError_t launch_step(int storage, int Q, int mode, const StepParams& p, cudaStream_t st);
+int step_grid_blocks(int storage, int Q, int mode, int trt);
+cudaError_t launch_import(int storage, int Q, const IoParams& p, cudaStream_t st);
+cudaError_t launch_export(int storage, int Q, const IoParams& p, cudaStream_t st);
+cudaError_t launch_macro(int storage, int Q, const IoParams& p, cudaStream_t st);
+cudaError_t launch_mass(int storage, int Q, const IoParams& p, int blocks, cudaStream_t st);
+cudaError_t launch_remap(const RemapParams& p, cudaStream_t st);
+
+#define PSM_DECLARE_STORAGE(NAME)                                                          \
+  cudaError_t launch_step_##NAME(int Q, int mode, int trt, const StepParams& p, cudaStream_t st); \
+  int step_grid_blocks_##NAME(int Q, int mode, int trt);                                  \
+  cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
+  cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
+  cudaError_t launch_macro_##NAME(int Q, const IoParams& p, cudaStream_t st);             \
+  cudaError_t launch_mass_##NAME(int Q, const IoParams& p, int blocks, cudaStream_t st);
+
+PSM_DECLARE_STORAGE(fp64)
+PSM_DECLARE_STORAGE(fp32)
+PSM_DECLARE_STORAGE(fp16)
+PSM_DECLARE_STORAGE(bf16)
+
+}  // namespace psm

@@ -1,0 +1,4 @@
+// Step, import, export, macroscopic and mass kernels for bf16 PDF storage.
+#include "psm_kernels.cuh"
+
+PSM_DEFINE_STORAGE(bf16, __nv_bfloat16)

@@ -1,0 +1,4 @@
+// Step, import, export, macroscopic and mass kernels for fp16 PDF storage.
+#include "psm_kernels.cuh"
+
+PSM_DEFINE_STORAGE(fp16, __half)

@@ -1,0 +1,380 @@
+"""Python binding of libpsm (include/psm.h): argument marshalling only.
+
+Every step of the PSM path runs in the CUDA library; this module converts
+Python / numpy / torch arguments to the C ABI and back.  It raises
+:class:`PSMError` for a non-zero status.  If ``libpsm.so`` has not been built,
+loading fails loudly: there is no CPU fallback.
+
+PyTorch supplies the CUDA stream (``torch.cuda.current_stream()``) and, where a
+caller passes a torch CUDA tensor as an output, the device memory it is written
+to.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpsm.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+PSM_OK = 0
+ERRORS = {-1: "PSM_ERR_ARG", -2: "PSM_ERR_CUDA", -3: "PSM_ERR_OOM", -4: "PSM_ERR_NONFINITE", -5: "PSM_ERR_STATE",
+          -6: "PSM_ERR_UNSUPPORTED"}
+PSM_MAX_BODIES = 4
+STORAGE = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+STREAMING = {"aa": 0, "twogrid": 1}
+FLUID = {"bgk": 0, "trt": 1}
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+
+class PSMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("bc_z", ctypes.c_int),
+                ("rho0", ctypes.c_double), ("u_in", ctypes.c_double * 3)]
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("stencil", ctypes.c_int), ("streaming", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
+class Collision(ctypes.Structure):
+    _fields_ = [("fluid", ctypes.c_int), ("tau", ctypes.c_double), ("trt_lambda", ctypes.c_double),
+                ("solid", ctypes.c_int), ("weighting", ctypes.c_int)]
+
+
+class GeomField(ctypes.Structure):
+    _fields_ = [("bricks", ctypes.POINTER(ctypes.c_uint64)), ("gx", ctypes.c_int64), ("gy", ctypes.c_int64),
+                ("gz", ctypes.c_int64), ("s", ctypes.c_int), ("lo", ctypes.c_double * 3)]
+
+
+class RotorParams(ctypes.Structure):
+    _fields_ = [("r_hub", ctypes.c_double), ("hub_len", ctypes.c_double), ("span", ctypes.c_double),
+                ("chord", ctypes.c_double), ("thickness", ctypes.c_double), ("pitch_root_deg", ctypes.c_double),
+                ("twist_deg", ctypes.c_double), ("phase", ctypes.c_double), ("n_blades", ctypes.c_int),
+                ("hand", ctypes.c_int)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpsm.so (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                                  f"g.build()'` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            i, d, vp, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
+            H = vp
+            sig = {
+                "psm_last_error": (ctypes.c_char_p, []),
+                "psm_lattice_velocities": (i, [i, P(i), P(d), P(i)]),
+                "psm_geom_voxelize_sphere": (i, [d, i, P(GeomField)]),
+                "psm_geom_voxelize_ellipsoid": (i, [d, d, d, i, P(GeomField)]),
+                "psm_geom_voxelize_box": (i, [d, d, d, i, P(GeomField)]),
+                "psm_geom_voxelize_rotor": (i, [P(RotorParams), i, P(GeomField)]),
+                "psm_geom_free": (i, [P(GeomField)]),
+                "psm_create": (i, [P(Grid), P(Lattice), P(Collision), vp, P(H)]),
+                "psm_destroy": (i, [H]),
+                "psm_init_equilibrium": (i, [H, d, P(d)]),
+                "psm_set_state": (i, [H, vp]),
+                "psm_get_state": (i, [H, vp]),
+                "psm_get_macroscopic": (i, [H, vp, vp]),
+                "psm_get_eps": (i, [H, vp]),
+                "psm_set_geometry": (i, [H, i, P(GeomField), P(d), P(d), P(d), P(d)]),
+                "psm_num_bodies": (i, [H, P(i)]),
+                "psm_step": (i, [H, i]),
+                "psm_step_count": (i, [H, P(i64)]),
+                "psm_force_torque": (i, [H, i, i64, i64, vp]),
+                "psm_series_capacity": (i, [H, P(i64)]),
+                "psm_mass": (i, [H, P(d)]),
+                "psm_synchronize": (i, [H]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def check(rc: int):
+    if rc != PSM_OK:
+        msg = lib().psm_last_error()
+        raise PSMError(rc, msg.decode() if msg else "")
+
+
+def _d(arr, n):
+    a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr(out, dtype, count):
+    """(pointer, keepalive) for an output/input array: numpy host array or torch tensor."""
+    if hasattr(out, "data_ptr"):  # torch tensor, host or device
+        if out.numel() != count:
+            raise ValueError(f"expected {count} elements, got {out.numel()}")
+        return ctypes.c_void_p(out.data_ptr()), out
+    if not isinstance(out, np.ndarray) or out.dtype != dtype or out.size != count or not out.flags.c_contiguous:
+        raise ValueError(f"expected a C-contiguous {dtype} array of {count} elements")
+    return ctypes.c_void_p(out.ctypes.data), out
+
+
+def current_stream() -> int:
+    """cudaStream_t of torch's current stream (0 when torch has no CUDA)."""
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+def lattice_velocities(Q: int):
+    """(c[Q,3], w[Q], opp[Q]) in the library's direction order."""
+    c = np.zeros((Q, 3), dtype=np.int32)
+    w = np.zeros(Q)
+    opp = np.zeros(Q, dtype=np.int32)
+    check(lib().psm_lattice_velocities(Q, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                       w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return c.astype(np.int64), w, opp.astype(np.int64)
+
+
+class Geometry:
+    """A host geometry field returned by a library voxeliser (freed on delete)."""
+
+    def __init__(self):
+        self.field = GeomField()
+
+    def __del__(self):
+        if getattr(self, "field", None) is not None and self.field.bricks:
+            lib().psm_geom_free(ctypes.byref(self.field))
+
+    @property
+    def dims(self):
+        return (self.field.gx, self.field.gy, self.field.gz)
+
+    @property
+    def s(self) -> int:
+        return self.field.s
+
+    @property
+    def lo(self):
+        return np.array(self.field.lo[:])
+
+    def words(self) -> np.ndarray:
+        wpb = 8 if self.field.s == 3 else 1
+        n = self.field.gx * self.field.gy * self.field.gz * wpb
+        return np.ctypeslib.as_array(self.field.bricks, shape=(n,)).copy()
+
+    def subcells(self) -> np.ndarray:
+        """Unpack to one byte per sub-cell, [gz*n, gy*n, gx*n] (x fastest)."""
+        s = self.field.s
+        n = 1 << s
+        gx, gy, gz = self.dims
+        wpb = 8 if s == 3 else 1
+        words = self.words().reshape(gz, gy, gx, wpb)
+        bits = np.unpackbits(words.view(np.uint8).reshape(gz, gy, gx, wpb * 8), axis=-1, bitorder="little")
+        bits = bits[..., : n * n * n].reshape(gz, gy, gx, n, n, n)  # [.., sz, sy, sx]
+        return np.ascontiguousarray(bits.transpose(0, 3, 1, 4, 2, 5).reshape(gz * n, gy * n, gx * n))
+
+
+def voxelize(kind: int, params, s: int) -> Geometry:
+    """Library voxeliser for an analytic shape kind of :mod:`workloads`."""
+    g = Geometry()
+    p = list(params)
+    if kind == W.SPHERE:
+        rc = lib().psm_geom_voxelize_sphere(p[0], s, ctypes.byref(g.field))
+    elif kind == W.ELLIPSOID:
+        rc = lib().psm_geom_voxelize_ellipsoid(p[0], p[1], p[2], s, ctypes.byref(g.field))
+    elif kind == W.BOX:
+        rc = lib().psm_geom_voxelize_box(p[0], p[1], p[2], s, ctypes.byref(g.field))
+    elif kind == W.ROTOR:
+        r = RotorParams(p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], int(p[8]), int(p[9]))
+        rc = lib().psm_geom_voxelize_rotor(ctypes.byref(r), s, ctypes.byref(g.field))
+    else:
+        raise ValueError(f"unknown shape kind {kind}")
+    check(rc)
+    return g
+
+
+@dataclass
+class SolverConfig:
+    nx: int
+    ny: int
+    nz: int
+    Q: int = 19
+    streaming: str = "aa"
+    storage: str = "fp32"
+    fluid: str = "bgk"
+    tau: float = 0.8
+    trt_lambda: float = 3.0 / 16.0
+    solid: int = 1
+    weighting: int = 1
+    bc_z: int = 1
+    rho0: float = 1.0
+    u_in: tuple = (0.0, 0.0, 0.0)
+
+
+class Solver:
+    """One libpsm handle (psm_create ... psm_destroy)."""
+
+    def __init__(self, cfg: SolverConfig, stream: int | None = None):
+        self.cfg = cfg
+        grid = Grid(cfg.nx, cfg.ny, cfg.nz, cfg.bc_z, cfg.rho0, (ctypes.c_double * 3)(*cfg.u_in))
+        lat = Lattice(cfg.Q, STREAMING[cfg.streaming], STORAGE[cfg.storage])
+        col = Collision(FLUID[cfg.fluid], cfg.tau, cfg.trt_lambda, cfg.solid, cfg.weighting)
+        self._h = ctypes.c_void_p()
+        self.stream = current_stream() if stream is None else stream
+        check(lib().psm_create(ctypes.byref(grid), ctypes.byref(lat), ctypes.byref(col),
+                               ctypes.c_void_p(self.stream), ctypes.byref(self._h)))
+        self._geoms = []
+
+    @classmethod
+    def from_case(cls, case: "W.Case", stream: int | None = None, init: bool = True) -> "Solver":
+        cfg = SolverConfig(case.nx, case.ny, case.nz, Q=case.Q, streaming=case.streaming, storage=case.storage,
+                           fluid=case.fluid, tau=case.tau, trt_lambda=case.trt_lambda, solid=case.solid,
+                           weighting=case.weighting, bc_z=case.bc_z, rho0=case.rho0, u_in=tuple(case.u_in))
+        s = cls(cfg, stream=stream)
+        for bi, b in enumerate(case.bodies):
+            g = voxelize(b.kind, b.params, b.s)
+            s.set_geometry(bi, g, b.Q0, b.R0, b.omega, b.v)
+        if init:
+            s.init_equilibrium(case.rho0, case.u_in)
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def shape(self):
+        c = self.cfg
+        return (c.Q, c.nz, c.ny, c.nx)
+
+    @property
+    def ncell(self) -> int:
+        c = self.cfg
+        return c.nx * c.ny * c.nz
+
+    def init_equilibrium(self, rho: float, u):
+        _, up = _d(u, 3)
+        check(lib().psm_init_equilibrium(self._h, rho, up))
+
+    def set_geometry(self, body: int, geom: Geometry, Q0, R0, omega, v):
+        a, Qp = _d(Q0, 9)
+        b, Rp = _d(R0, 3)
+        c, wp = _d(omega, 3)
+        e, vp = _d(v, 3)
+        check(lib().psm_set_geometry(self._h, body, ctypes.byref(geom.field), Qp, Rp, wp, vp))
+        self._geoms.append(geom)
+
+    def set_geometry_bits(self, body: int, sub: np.ndarray, s: int, lo, Q0, R0, omega, v):
+        """Attach a field given as one byte per sub-cell [nsz, nsy, nsx] (packed here)."""
+        n = 1 << s
+        nsz, nsy, nsx = sub.shape
+        gx, gy, gz = nsx // n, nsy // n, nsz // n
+        b = sub.reshape(gz, n, gy, n, gx, n).transpose(0, 2, 4, 1, 3, 5).reshape(gz, gy, gx, n * n * n)
+        wpb = 8 if s == 3 else 1
+        padded = np.zeros((gz, gy, gx, wpb * 64), dtype=np.uint8)
+        padded[..., : n * n * n] = b
+        words = np.packbits(padded, axis=-1, bitorder="little").view(np.uint64).reshape(-1).copy()
+        g = Geometry()
+        g._words = words
+        g.field.bricks = words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        g.field.gx, g.field.gy, g.field.gz, g.field.s = gx, gy, gz, s
+        for k in range(3):
+            g.field.lo[k] = float(lo[k])
+        try:
+            self.set_geometry(body, g, Q0, R0, omega, v)
+        finally:
+            g.field.bricks = ctypes.POINTER(ctypes.c_uint64)()  # numpy owns the words
+        self._geoms.pop()
+
+    @property
+    def num_bodies(self) -> int:
+        n = ctypes.c_int()
+        check(lib().psm_num_bodies(self._h, ctypes.byref(n)))
+        return n.value
+
+    def step(self, n: int = 1):
+        check(lib().psm_step(self._h, int(n)))
+
+    @property
+    def step_count(self) -> int:
+        n = ctypes.c_int64()
+        check(lib().psm_step_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def force_torque(self, body: int = 0, step_from: int = 0, count: int | None = None, out=None):
+        """[count, 6] force and torque on the body (FP64, host unless out is given)."""
+        if count is None:
+            count = self.step_count - step_from
+        if out is None:
+            out = np.zeros((count, 6))
+        p, keep = _ptr(out, np.float64, count * 6)
+        check(lib().psm_force_torque(self._h, body, step_from, count, p))
+        return out
+
+    def mass(self) -> float:
+        m = ctypes.c_double()
+        check(lib().psm_mass(self._h, ctypes.byref(m)))
+        return m.value
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros(self.shape)
+        p, keep = _ptr(out, np.float64, int(np.prod(self.shape)))
+        check(lib().psm_get_state(self._h, p))
+        return out
+
+    def set_state(self, f):
+        if hasattr(f, "data_ptr"):
+            p, keep = _ptr(f, np.float64, int(np.prod(self.shape)))
+        else:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            p, keep = _ptr(f, np.float64, int(np.prod(self.shape)))
+        check(lib().psm_set_state(self._h, p))
+
+    def macroscopic(self):
+        c = self.cfg
+        rho = np.zeros((c.nz, c.ny, c.nx))
+        u = np.zeros((c.nz, c.ny, c.nx, 3))
+        check(lib().psm_get_macroscopic(self._h, ctypes.c_void_p(rho.ctypes.data), ctypes.c_void_p(u.ctypes.data)))
+        return rho, u
+
+    def eps(self):
+        c = self.cfg
+        e = np.zeros((c.nz, c.ny, c.nx), dtype=np.float32)
+        check(lib().psm_get_eps(self._h, ctypes.c_void_p(e.ctypes.data)))
+        return e
+
+    def synchronize(self):
+        check(lib().psm_synchronize(self._h))
+
+    def bytes_per_cell_update(self) -> int:
+        """Algorithmic bytes per cell update: one read and one write of every PDF."""
+        return 2 * self.cfg.Q * STORAGE_BYTES[self.cfg.storage]

@@ -1,0 +1,159 @@
+"""GPU parity of the fused PSM step (libpsm, through the C ABI) against the FP64
+CPU oracle on the same seeded synthetic inputs.
+
+Tolerances (velocity: max |u_gpu - u_oracle| / |u_in|):
+  FP64 storage + FP64 arithmetic  <= 1e-12,
+  FP32                            <= 2e-5   (force/torque <= 1e-4 relative),
+  FP16 shifted storage            <= 2e-3,
+  BF16 shifted storage            reported (no bar), must stay finite.
+eps (Sec. 3) is compared bit for bit: both sides take the sub-cell decision in
+the same float arithmetic.
+"""
+
+import numpy as np
+import pytest
+
+from helpers import ft_err, perm_lib_to_oracle, run_gpu, run_oracle, u_err
+from paper_2502_20049_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+
+    g.build()
+
+
+def c2_reduced(storage="fp32", streaming="aa", steps=200, omega=0.01):
+    """The rotating-ellipsoid case at 64^3, body x0.25, faster rotation so eps changes every few steps."""
+    c = W.c2_ellipsoid(scale=0.25, n=64, steps=steps, omega_z=omega)
+    return c.with_(storage=storage, streaming=streaming)
+
+
+@pytest.mark.parametrize("streaming", ["aa", "twogrid"])
+def test_c1_fp64_full(streaming):
+    case = W.c1_sphere().with_(streaming=streaming)
+    g, o = run_gpu(case), run_oracle(case)
+    perm = perm_lib_to_oracle(19)
+    assert u_err(g, o, case) <= 1e-12
+    assert np.abs(g["f"] - o["f"][perm]).max() <= 1e-13
+    assert ft_err(g, o) <= 1e-10
+    # drag on the sphere points downstream (body convention)
+    assert np.all(g["ft"][:, 0, 2] > 0)
+
+
+def test_c1_fp32():
+    case = W.c1_sphere().with_(storage="fp32")
+    g, o = run_gpu(case), run_oracle(case)
+    assert u_err(g, o, case) <= 2e-5
+    assert ft_err(g, o) <= 1e-4
+
+
+@pytest.mark.parametrize("streaming", ["aa", "twogrid"])
+def test_c2_reduced_fp32_trt_rotating(streaming):
+    case = c2_reduced("fp32", streaming)
+    g, o = run_gpu(case), run_oracle(case)
+    assert u_err(g, o, case) <= 2e-5
+    assert ft_err(g, o) <= 1e-4
+    assert np.abs(o["ft"][:, 0, 5]).max() > 0
+
+
+def test_c2_reduced_fp16():
+    case = c2_reduced("fp16")
+    g, o = run_gpu(case), run_oracle(case)
+    err = u_err(g, o, case)
+    print(f"fp16 shifted storage: velocity L_inf / |u_in| = {err:.3e}")
+    assert err <= 2e-3
+
+
+def test_c2_reduced_bf16_reported():
+    case = c2_reduced("bf16")
+    g, o = run_gpu(case), run_oracle(case)
+    err = u_err(g, o, case)
+    print(f"bf16 shifted storage: velocity L_inf / |u_in| = {err:.3e} (no bar)")
+    assert np.isfinite(err) and err < 0.5
+
+
+def test_eps_bitwise_every_step():
+    from paper_2502_20049_gb300 import psm
+
+    case = c2_reduced("fp32", steps=0, omega=0.05)
+    sol = psm.Solver.from_case(case)
+    from helpers import oracle_sim
+
+    sim = oracle_sim(case)
+    for n in range(0, 40):
+        e_gpu = sol.eps()
+        e_or, _ = sim.eps(n)
+        assert np.array_equal(e_gpu.astype(np.float64), e_or), n
+        sol.step(1)
+    assert e_or.sum() > 10
+
+
+def test_aa_equals_twogrid_bitwise():
+    a = run_gpu(c2_reduced("fp32", "aa", steps=60))
+    b = run_gpu(c2_reduced("fp32", "twogrid", steps=60))
+    assert np.array_equal(a["f"], b["f"])
+    assert np.array_equal(a["ft"], b["ft"])
+
+
+RAGGED = [
+    # ragged sizes, SC2 / SC3, direct weighting, periodic z, two translating + rotating bodies
+    dict(nx=37, ny=23, nz=19, solid=2, weighting=0, bc_z=1),
+    dict(nx=37, ny=23, nz=19, solid=3, weighting=1, bc_z=0),
+    dict(nx=33, ny=5, nz=7, solid=1, weighting=1, bc_z=1),
+]
+
+
+@pytest.mark.parametrize("kw", RAGGED)
+@pytest.mark.parametrize("streaming", ["aa", "twogrid"])
+def test_ragged_two_bodies_fp64(kw, streaming):
+    nx, ny, nz = kw["nx"], kw["ny"], kw["nz"]
+    bodies = [W.BodyCase(W.ELLIPSOID, (3.5, 2.0, 1.5), 2, (nx * 0.3, ny * 0.5, nz * 0.5), omega=(0.01, 0.02, 0.03),
+                         v=(0.01, 0.0, -0.005)),
+              W.BodyCase(W.BOX, (1.5, 1.5, 1.0), 1, (nx * 0.75, ny * 0.4, nz * 0.45), omega=(0.0, 0.0, -0.04))]
+    case = W.Case("ragged", nx, ny, nz, Q=19, storage="fp64", streaming=streaming, fluid="trt", tau=0.7,
+                  solid=kw["solid"], weighting=kw["weighting"], bc_z=kw["bc_z"], u_in=(0.01, -0.005, 0.02), steps=31,
+                  bodies=bodies)
+    g, o = run_gpu(case), run_oracle(case)
+    perm = perm_lib_to_oracle(19)
+    assert np.abs(g["f"] - o["f"][perm]).max() <= 1e-13
+    assert ft_err(g, o) <= 1e-10
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_d3q27_rotor_proxy(storage, tol):
+    case = W.c3_rotor(storage=storage, scale=0.12, dims=(48, 48, 60), steps=60)
+    case = case.with_(bodies=[b for b in case.bodies])
+    g, o = run_gpu(case), run_oracle(case)
+    assert u_err(g, o, case) <= tol
+    assert ft_err(g, o) <= (1e-10 if storage == "fp64" else 1e-4)
+    assert len(case.bodies) == 2 and np.abs(o["ft"][:, 1, 5]).max() > 0
+
+
+def test_mass_conserved_periodic_fp64():
+    from paper_2502_20049_gb300 import psm
+
+    case = c2_reduced("fp64", steps=0).with_(bc_z=0, nx=32, ny=32, nz=32)
+    case.bodies[0].R0 = (16.0, 16.0, 16.0)
+    sol = psm.Solver.from_case(case)
+    m0 = sol.mass()
+    sol.step(100)
+    assert abs(sol.mass() - m0) / m0 <= 1e-13
+
+
+def test_empty_domain_and_single_cell():
+    """No bodies (pure LBM) and a 1x1x1 periodic grid (every population streams
+    back into its own cell)."""
+    case = W.Case("nobody", 20, 9, 11, Q=19, storage="fp64", fluid="bgk", tau=0.9, u_in=(0.0, 0.02, 0.03),
+                  steps=17)
+    g, o = run_gpu(case), run_oracle(case)
+    perm = perm_lib_to_oracle(19)
+    assert np.abs(g["f"] - o["f"][perm]).max() <= 1e-13
+    one = W.Case("one", 1, 1, 1, Q=27, storage="fp64", fluid="trt", tau=0.6, bc_z=0, u_in=(0.01, 0.0, 0.0),
+                 steps=5, bodies=[W.BodyCase(W.BOX, (3.0, 3.0, 3.0), 0, (0.5, 0.5, 0.5), v=(0.0, 0.01, 0.0))])
+    g, o = run_gpu(one), run_oracle(one)
+    assert np.abs(g["f"] - o["f"][perm_lib_to_oracle(27)]).max() <= 1e-14
+    assert ft_err(g, o) <= 1e-12
