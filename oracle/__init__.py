@@ -92,6 +92,7 @@ def _lib():
                 "or_ft": (i, [vp, dp]),
                 "or_eps": (i, [vp, l, dp, ip]),
                 "or_macroscopic": (i, [vp, dp, dp]),
+                "or_update_cells": (i, [vp, P(ctypes.c_long), l, dp]),
                 "ort_create": (vp, [vp, dp]),
                 "ort_destroy": (None, [vp]),
                 "ort_set_threads": (i, [vp, i]),
@@ -337,6 +338,17 @@ class Sim:
         o = np.zeros((c.nz, c.ny, c.nx), dtype=np.int32)
         _lib().or_eps(self._h, int(n), _dp(e), o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         return e, o
+
+    def update_cells(self, cells):
+        """f_i(x, n+1) [len(cells), Q] at flat cell indices, from the current state
+        (no step is taken); oracle direction order."""
+        cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+        out = np.zeros((cells.size, self.cfg.Q))
+        rc = _lib().or_update_cells(self._h, cells.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), cells.size,
+                                    _dp(out))
+        if rc != 0:
+            raise IndexError("cell index out of range")
+        return out
 
     def macroscopic(self):
         """(rho[nz,ny,nx], u[nz,ny,nx,3]) with u = j / rho."""

@@ -292,19 +292,159 @@ struct Sim {
     for (long c = 0; c < ncell; ++c) eps[c] = std::min(1.0, eps[c]);
   }
 
+  // TRT rates: omega+ = 1/tau, Lambda = (1/omega+ - 1/2)(1/omega- - 1/2).
+  double omega_plus() const { return 1.0 / cfg.tau; }
+  double omega_minus() const { return 1.0 / (cfg.trt_lambda / (cfg.tau - 0.5) + 0.5); }
+
+  std::vector<Pose> poses_at(long n) const {
+    std::vector<Pose> poses;
+    for (auto& B : bodies) poses.push_back(pose_at(B.Q0, B.R0, B.omega_pose, B.v, n));
+    return poses;
+  }
+
+  // eps and owner of one cell at the pose of step n (same rule as remap_all)
+  void remap_one(const std::vector<Pose>& poses, int x, int y, int z, double& eps_c, int& owner_c) const {
+    double sum = 0.0, best = 0.0;
+    owner_c = -1;
+    for (size_t b = 0; b < bodies.size(); ++b) {
+      const Body<T>& B = bodies[b];
+      double e = remap_cell(B.sub.data(), B.nsx, B.nsy, B.nsz, B.s, B.lo, poses[b], x, y, z);
+      sum += e;
+      if (e > best) { best = e; owner_c = (int)b; }
+    }
+    eps_c = std::min(1.0, sum);
+  }
+
+  // One cell's collision (Eq. 4 with Eq. 2 / TRT, Eq. 5 / 6, Eq. 7 / 8 / 9) from
+  // the pre-collision state f: post-collision PDFs post[Q] and the cell's
+  // force density g = B sum_i Omega^S_i c_i.
+  void collide_cell(int x, int y, int z, double eps_c, int owner_c, const std::vector<Pose>& poses, T* post,
+                    T* g) const {
+    const int Q = L.Q;
+    const double tau = cfg.tau;
+    const double cs2 = 1.0 / 3.0;
+    const double om_p = omega_plus(), om_m = omega_minus();
+    const long c = cell(x, y, z);
+    T fl[27], E[27], G[27], OF[27], OS[27];
+    for (int i = 0; i < Q; ++i) fl[i] = f[i * ncell + c];
+    // moments of the pre-collision PDFs
+    T rho(0.0), j[3] = {T(0.0), T(0.0), T(0.0)};
+    for (int i = 0; i < Q; ++i) {
+      rho += fl[i];
+      for (int k = 0; k < 3; ++k) j[k] += fl[i] * double(L.c[i][k]);
+    }
+    T u[3];
+    T Fb[3] = {T(cfg.force[0]), T(cfg.force[1]), T(cfg.force[2])};
+    // Guo forcing (oracle-only, for the Poiseuille pin): u = (j + F/2)/rho
+    for (int k = 0; k < 3; ++k) u[k] = (j[k] + Fb[k] * 0.5) / rho;
+    // solid fraction and weighting, Eq. 5 / Eq. 6
+    T e(eps_c);
+    if (!delta.empty()) e = e + delta[c];
+    T Bw = weighting<T>(cfg.weighting, e, tau);
+    // solid velocity u_s = omega x (x_c - R_n) + v of the owner body
+    T us[3] = {T(0.0), T(0.0), T(0.0)};
+    if (owner_c >= 0) {
+      const Body<T>& Bd = bodies[owner_c];
+      T r[3] = {T(x + 0.5 - poses[owner_c].R[0]), T(y + 0.5 - poses[owner_c].R[1]),
+                T(z + 0.5 - poses[owner_c].R[2])};
+      us[0] = Bd.omega[1] * r[2] - Bd.omega[2] * r[1] + Bd.v[0];
+      us[1] = Bd.omega[2] * r[0] - Bd.omega[0] * r[2] + Bd.v[1];
+      us[2] = Bd.omega[0] * r[1] - Bd.omega[1] * r[0] + Bd.v[2];
+    }
+    for (int i = 0; i < Q; ++i) {
+      E[i] = feq<T>(L, i, rho, u);    // f^eq(rho, u)
+      G[i] = feq<T>(L, i, rho, us);   // f^eq(rho, u_s)
+    }
+    // fluid collision: Eq. 2 (BGK) or two-relaxation-time
+    for (int i = 0; i < Q; ++i) {
+      const int ib = L.opp[i];
+      if (cfg.fluid == 0) {
+        OF[i] = -(fl[i] - E[i]) / tau;
+      } else {
+        T fp = (fl[i] + fl[ib]) * 0.5, fm = (fl[i] - fl[ib]) * 0.5;
+        T ep = (E[i] + E[ib]) * 0.5, em = (E[i] - E[ib]) * 0.5;
+        OF[i] = -(fp - ep) * om_p - (fm - em) * om_m;
+      }
+    }
+    // solid collision, Eq. 7 (SC1), Eq. 8 (SC2, as printed: u_s in both
+    // brackets), Eq. 9 (SC3)
+    for (int i = 0; i < Q; ++i) {
+      const int ib = L.opp[i];
+      if (cfg.solid == 1) {
+        OS[i] = (fl[ib] - E[ib]) - (fl[i] - G[i]);
+      } else if (cfg.solid == 2) {
+        OS[i] = (G[i] - fl[i]) + (fl[i] - G[i]) * (1.0 - 1.0 / tau);
+      } else {
+        OS[i] = (fl[ib] - G[ib]) - (fl[i] - G[i]);
+      }
+    }
+    // PSM rule, Eq. 4
+    T gs[3] = {T(0.0), T(0.0), T(0.0)};
+    for (int i = 0; i < Q; ++i) {
+      T one_minus_B = T(1.0) - Bw;
+      post[i] = fl[i] + one_minus_B * OF[i] + Bw * OS[i];
+      for (int k = 0; k < 3; ++k) gs[k] += OS[i] * double(L.c[i][k]);
+    }
+    for (int k = 0; k < 3; ++k) g[k] = Bw * gs[k];
+    // Guo forcing source (oracle-only)
+    if (cfg.force[0] != 0.0 || cfg.force[1] != 0.0 || cfg.force[2] != 0.0) {
+      T S[27];
+      for (int i = 0; i < Q; ++i) {
+        T cu = u[0] * double(L.c[i][0]) + u[1] * double(L.c[i][1]) + u[2] * double(L.c[i][2]);
+        T acc(0.0);
+        for (int k = 0; k < 3; ++k)
+          acc += ((double(L.c[i][k]) - u[k]) / cs2 + cu * double(L.c[i][k]) / (cs2 * cs2)) * Fb[k];
+        S[i] = T(L.w[i]) * acc;
+      }
+      for (int i = 0; i < Q; ++i) {
+        const int ib = L.opp[i];
+        if (cfg.fluid == 0) {
+          post[i] += S[i] * (1.0 - 0.5 / tau);
+        } else {
+          T sp = (S[i] + S[ib]) * 0.5, sm = (S[i] - S[ib]) * 0.5;
+          post[i] += sp * (1.0 - 0.5 * om_p) + sm * (1.0 - 0.5 * om_m);
+        }
+      }
+    }
+  }
+
+  // f_i(x, n + 1) for sampled cells x, computed one by one from the current
+  // state f at step n: the collision of every upstream cell x - c_i, then the
+  // streaming rule of Eq. 1 (periodic x / y, ghost planes or periodic z).  No
+  // half-way walls or body force here.  out[k * Q + i].
+  void update_cells(const long* cells, long ncells_req, T* out) const {
+    const std::vector<Pose> poses = poses_at(step);
+    const int Q = L.Q;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    for (long k = 0; k < ncells_req; ++k) {
+      const long c = cells[k];
+      const int x = (int)(c % cfg.nx), y = (int)((c / cfg.nx) % cfg.ny), z = (int)(c / ((long)cfg.nx * cfg.ny));
+      T post[27], g[3];
+      for (int i = 0; i < Q; ++i) {
+        int xs = ((x - L.c[i][0]) % cfg.nx + cfg.nx) % cfg.nx;
+        int ys = ((y - L.c[i][1]) % cfg.ny + cfg.ny) % cfg.ny;
+        int zs = z - L.c[i][2];
+        if (zs < 0 || zs >= cfg.nz) {
+          if (cfg.bc_z == 1) { out[k * Q + i] = ghost(i); continue; }
+          zs = (zs + cfg.nz) % cfg.nz;
+        }
+        double e;
+        int o;
+        remap_one(poses, xs, ys, zs, e, o);
+        collide_cell(xs, ys, zs, e, o, poses, post, g);
+        out[k * Q + i] = post[i];
+      }
+    }
+  }
+
   void do_step() {
     const int Q = L.Q;
     const int nx = cfg.nx, ny = cfg.ny, nz = cfg.nz;
     const double tau = cfg.tau;
-    const double cs2 = 1.0 / 3.0;
     std::vector<double> eps;
     std::vector<int> owner;
     remap_all(step, eps, owner);
-    std::vector<Pose> poses;
-    for (auto& B : bodies) poses.push_back(pose_at(B.Q0, B.R0, B.omega_pose, B.v, step));
-    // TRT rates: omega+ = 1/tau, Lambda = (1/omega+ - 1/2)(1/omega- - 1/2).
-    const double om_p = 1.0 / tau;
-    const double om_m = 1.0 / (cfg.trt_lambda / (tau - 0.5) + 0.5);
+    const std::vector<Pose> poses = poses_at(step);
     const int nb = (int)bodies.size();
     // Per-cell force density g = B sum_i Omega^S_i c_i, kept for the
     // force/torque sums below (computed in a fixed order afterwards).
@@ -312,90 +452,12 @@ struct Sim {
 
 #pragma omp parallel for schedule(static) num_threads(nthreads)
     for (int z = 0; z < nz; ++z) {
-      T fl[27], E[27], G[27], OF[27], OS[27];
+      T pc[27];
       for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
           const long c = cell(x, y, z);
-          for (int i = 0; i < Q; ++i) fl[i] = f[i * ncell + c];
-          // moments of the pre-collision PDFs
-          T rho(0.0), j[3] = {T(0.0), T(0.0), T(0.0)};
-          for (int i = 0; i < Q; ++i) {
-            rho += fl[i];
-            for (int k = 0; k < 3; ++k) j[k] += fl[i] * double(L.c[i][k]);
-          }
-          T u[3];
-          T Fb[3] = {T(cfg.force[0]), T(cfg.force[1]), T(cfg.force[2])};
-          // Guo forcing (oracle-only, for the Poiseuille pin): u = (j + F/2)/rho
-          for (int k = 0; k < 3; ++k) u[k] = (j[k] + Fb[k] * 0.5) / rho;
-          // solid fraction and weighting, Eq. 5 / Eq. 6
-          T e(eps[c]);
-          if (!delta.empty()) e = e + delta[c];
-          T Bw = weighting<T>(cfg.weighting, e, tau);
-          // solid velocity u_s = omega x (x_c - R_n) + v of the owner body
-          T us[3] = {T(0.0), T(0.0), T(0.0)};
-          int ob = owner[c];
-          if (ob >= 0) {
-            const Body<T>& Bd = bodies[ob];
-            T r[3] = {T(x + 0.5 - poses[ob].R[0]), T(y + 0.5 - poses[ob].R[1]), T(z + 0.5 - poses[ob].R[2])};
-            us[0] = Bd.omega[1] * r[2] - Bd.omega[2] * r[1] + Bd.v[0];
-            us[1] = Bd.omega[2] * r[0] - Bd.omega[0] * r[2] + Bd.v[1];
-            us[2] = Bd.omega[0] * r[1] - Bd.omega[1] * r[0] + Bd.v[2];
-          }
-          for (int i = 0; i < Q; ++i) {
-            E[i] = feq<T>(L, i, rho, u);    // f^eq(rho, u)
-            G[i] = feq<T>(L, i, rho, us);   // f^eq(rho, u_s)
-          }
-          // fluid collision: Eq. 2 (BGK) or two-relaxation-time
-          for (int i = 0; i < Q; ++i) {
-            const int ib = L.opp[i];
-            if (cfg.fluid == 0) {
-              OF[i] = -(fl[i] - E[i]) / tau;
-            } else {
-              T fp = (fl[i] + fl[ib]) * 0.5, fm = (fl[i] - fl[ib]) * 0.5;
-              T ep = (E[i] + E[ib]) * 0.5, em = (E[i] - E[ib]) * 0.5;
-              OF[i] = -(fp - ep) * om_p - (fm - em) * om_m;
-            }
-          }
-          // solid collision, Eq. 7 (SC1), Eq. 8 (SC2, as printed: u_s in both
-          // brackets), Eq. 9 (SC3)
-          for (int i = 0; i < Q; ++i) {
-            const int ib = L.opp[i];
-            if (cfg.solid == 1) {
-              OS[i] = (fl[ib] - E[ib]) - (fl[i] - G[i]);
-            } else if (cfg.solid == 2) {
-              OS[i] = (G[i] - fl[i]) + (fl[i] - G[i]) * (1.0 - 1.0 / tau);
-            } else {
-              OS[i] = (fl[ib] - G[ib]) - (fl[i] - G[i]);
-            }
-          }
-          // PSM rule, Eq. 4
-          T gs[3] = {T(0.0), T(0.0), T(0.0)};
-          for (int i = 0; i < Q; ++i) {
-            T one_minus_B = T(1.0) - Bw;
-            post[i * ncell + c] = fl[i] + one_minus_B * OF[i] + Bw * OS[i];
-            for (int k = 0; k < 3; ++k) gs[k] += OS[i] * double(L.c[i][k]);
-          }
-          for (int k = 0; k < 3; ++k) g[3 * c + k] = Bw * gs[k];
-          // Guo forcing source (oracle-only)
-          if (cfg.force[0] != 0.0 || cfg.force[1] != 0.0 || cfg.force[2] != 0.0) {
-            T S[27];
-            for (int i = 0; i < Q; ++i) {
-              T cu = u[0] * double(L.c[i][0]) + u[1] * double(L.c[i][1]) + u[2] * double(L.c[i][2]);
-              T acc(0.0);
-              for (int k = 0; k < 3; ++k)
-                acc += ((double(L.c[i][k]) - u[k]) / cs2 + cu * double(L.c[i][k]) / (cs2 * cs2)) * Fb[k];
-              S[i] = T(L.w[i]) * acc;
-            }
-            for (int i = 0; i < Q; ++i) {
-              const int ib = L.opp[i];
-              if (cfg.fluid == 0) {
-                post[i * ncell + c] += S[i] * (1.0 - 0.5 / tau);
-              } else {
-                T sp = (S[i] + S[ib]) * 0.5, sm = (S[i] - S[ib]) * 0.5;
-                post[i * ncell + c] += sp * (1.0 - 0.5 * om_p) + sm * (1.0 - 0.5 * om_m);
-              }
-            }
-          }
+          collide_cell(x, y, z, eps[c], owner[c], poses, pc, &g[3 * c]);
+          for (int i = 0; i < Q; ++i) post[i * ncell + c] = pc[i];
         }
     }
 
@@ -685,6 +747,15 @@ int or_eps(void* h, long n, double* eps, int* owner) {
   S->remap_all(n, e, o);
   std::memcpy(eps, e.data(), sizeof(double) * e.size());
   if (owner) std::memcpy(owner, o.data(), sizeof(int) * o.size());
+  return 0;
+}
+// f_i(x, n + 1) at the listed cells from the current state (no stepping):
+// out[k * Q + i] in the oracle's direction order.
+int or_update_cells(void* h, const long* cells, long n, double* out) {
+  auto* S = static_cast<Sim<double>*>(h);
+  for (long k = 0; k < n; ++k)
+    if (cells[k] < 0 || cells[k] >= S->ncell) return -1;
+  S->update_cells(cells, n, out);
   return 0;
 }
 // rho and u = j/rho (no forcing shift) per cell

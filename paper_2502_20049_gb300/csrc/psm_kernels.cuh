@@ -181,23 +181,25 @@ __device__ __forceinline__ float cell_eps(const DevBody* bodies, int nb, int x, 
 // Neighbour offsets of a cell (periodic x, y; periodic or bounded z)
 // ---------------------------------------------------------------------------
 struct Nbr {
-  long long dxm, dxp, dym, dyp, dzm, dzp;
+  // 32-bit unsigned offsets: cell indices are < 2^32 and the sum cell + off
+  // wraps modulo 2^32 onto the neighbour's index
+  unsigned dxm, dxp, dym, dyp, dzm, dzp;
   bool zlo_out, zhi_out;  // z - 1 (resp. z + 1) lies outside (ghost plane)
   __device__ __forceinline__ void init(const Grid3& g, int x, int y, int z) {
-    const long long nx = g.nx, plane = (long long)g.nx * g.ny;
-    dxm = (x == 0) ? nx - 1 : -1;
-    dxp = (x == g.nx - 1) ? -(nx - 1) : 1;
-    dym = (y == 0) ? (long long)(g.ny - 1) * nx : -nx;
-    dyp = (y == g.ny - 1) ? -(long long)(g.ny - 1) * nx : nx;
-    dzm = (z == 0) ? (long long)(g.nz - 1) * plane : -plane;
-    dzp = (z == g.nz - 1) ? -(long long)(g.nz - 1) * plane : plane;
+    const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
+    dxm = (x == 0) ? nx - 1u : 0u - 1u;
+    dxp = (x == g.nx - 1) ? 0u - (nx - 1u) : 1u;
+    dym = (y == 0) ? (unsigned)(g.ny - 1) * nx : 0u - nx;
+    dyp = (y == g.ny - 1) ? 0u - (unsigned)(g.ny - 1) * nx : nx;
+    dzm = (z == 0) ? (unsigned)(g.nz - 1) * plane : 0u - plane;
+    dzp = (z == g.nz - 1) ? 0u - (unsigned)(g.nz - 1) * plane : plane;
     const bool ghost = g.bc_z == PSM_BC_EQ_INLET_OUTLET;
     zlo_out = ghost && z == 0;
     zhi_out = ghost && z == g.nz - 1;
   }
-  __device__ __forceinline__ long long off(int dx, int dy, int dz) const {
-    return (dx < 0 ? dxm : (dx > 0 ? dxp : 0)) + (dy < 0 ? dym : (dy > 0 ? dyp : 0)) +
-           (dz < 0 ? dzm : (dz > 0 ? dzp : 0));
+  __device__ __forceinline__ unsigned off(int dx, int dy, int dz) const {
+    return (dx < 0 ? dxm : (dx > 0 ? dxp : 0u)) + (dy < 0 ? dym : (dy > 0 ? dyp : 0u)) +
+           (dz < 0 ? dzm : (dz > 0 ? dzp : 0u));
   }
   // x - c_i lies in a ghost plane: population i enters from the ghost plane
   __device__ __forceinline__ bool from_ghost(int cz) const { return (cz > 0 && zlo_out) || (cz < 0 && zhi_out); }
@@ -213,12 +215,11 @@ __device__ __forceinline__ T feq_shifted(int i, T drho, T rho, T vx, T vy, T vz,
   return T(lat_w<Q>(i)) * (drho + rho * (T(3) * cv + T(4.5) * cv * cv - T(1.5) * vv));
 }
 
-template <int Q>
-__device__ __forceinline__ int tile_coords(const Tiling& t, long long tile, int& x, int& y, int& z) {
-  const int tx = (int)(tile % t.ntx);
-  const long long r = tile / t.ntx;
-  const int ty = (int)(r % t.nty);
-  z = (int)(r / t.nty);
+__device__ __forceinline__ int tile_coords(const Tiling& t, int tile, int& x, int& y, int& z) {
+  const int tx = tile % t.ntx;
+  const int r = tile / t.ntx;
+  const int ty = r % t.nty;
+  z = r / t.nty;
   x = tx * t.tx + (int)(threadIdx.x % t.tx);
   y = ty * t.ty + (int)(threadIdx.x / t.tx);
   return 0;
@@ -264,8 +265,17 @@ __device__ __forceinline__ void grid_reduce(const double* blk, int ncomp, double
 // ---------------------------------------------------------------------------
 // The fused step kernel (persistent: blocks stride over row tiles).
 // ---------------------------------------------------------------------------
+// Resident blocks per SM the register allocation aims at (D3Q19 / D3Q27).
+#ifndef PSM_MIN_BLOCKS_Q19
+#define PSM_MIN_BLOCKS_Q19 3
+#endif
+#ifndef PSM_MIN_BLOCKS_Q27
+#define PSM_MIN_BLOCKS_Q27 2
+#endif
+
 template <class S, int Q, int MODE, int TRT>
-__global__ void __launch_bounds__(PSM_THREADS) k_step(const __grid_constant__ StepParams p) {
+__global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
+    k_step(const __grid_constant__ StepParams p) {
   using T = typename Store<S>::T;
   constexpr int NW = PSM_THREADS / 32;
   __shared__ double s_ft[NW][PSM_MAX_BODIES * 6];
@@ -280,15 +290,16 @@ __global__ void __launch_bounds__(PSM_THREADS) k_step(const __grid_constant__ St
   const T om_a = T(p.om_a), om_b = T(p.om_b);
   const T inv_tau = T(1.0 / p.tau);
 
-  for (long long tile = blockIdx.x; tile < p.t.ntiles; tile += gridDim.x) {
+  const int ntiles = (int)p.t.ntiles;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int x, y, z;
-    tile_coords<Q>(p.t, tile, x, y, z);
+    tile_coords(p.t, tile, x, y, z);
     const bool active = x < p.g.nx && y < p.g.ny;
     int owner = -1;
     bool solid_cell = false;
     double ft[6] = {0, 0, 0, 0, 0, 0};
     if (active) {
-      const long long cell = ((long long)z * p.g.ny + y) * p.g.nx + x;
+      const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
       Nbr nbr;
       nbr.init(p.g, x, y, z);
       // ---- load (pre-collision f, shifted) ----
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(PSM_THREADS) k_step(const __grid_constant__ St
         if (nbr.from_ghost(cz)) {
           f[i] = T(p.ghost[i]);
         } else if (MODE == MODE_AA_ODD) {
-          f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + cell + nbr.off(-cx, -cy, -cz));
+          f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
         } else {
           f[i] = Store<S>::ld(buf + (long long)i * N + cell);
         }
@@ -422,7 +433,7 @@ __global__ void __launch_bounds__(PSM_THREADS) k_step(const __grid_constant__ St
           Store<S>::st(buf + (long long)lat_opp(i) * N + cell, f[i]);
         } else if (!nbr.to_ghost(cz)) {
           S* base = (MODE == MODE_TG) ? dst : buf;
-          Store<S>::st(base + (long long)i * N + cell + nbr.off(cx, cy, cz), f[i]);
+          Store<S>::st(base + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
         }
       }
     }
@@ -482,7 +493,8 @@ __device__ __forceinline__ void read_state(const IoParams& p, const S* buf, cons
     if (nbr.from_ghost(lat_cz(i))) {
       f[i] = T(p.ghost[i]);
     } else if (p.layout == LAYOUT_SWAPPED) {
-      f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i)));
+      f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N +
+                          (unsigned)((unsigned)cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i))));
     } else {
       f[i] = Store<S>::ld(buf + (long long)i * N + cell);
     }
@@ -515,7 +527,7 @@ __global__ void k_import(const __grid_constant__ IoParams p) {
       int slot;
       if (p.layout == LAYOUT_SWAPPED) {
         slot = lat_opp(i);
-        dstc = cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i));
+        dstc = (unsigned)((unsigned)cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i)));
       } else {
         slot = i;
         dstc = cell;

@@ -45,9 +45,15 @@ def u_err(a, b, case):
     return np.abs(a["u"] - b["u"]).max() / np.linalg.norm(case.u_in)
 
 
-def ft_err(a, b):
-    """max |FT_a - FT_b| per component, relative to the component's max |FT_b|."""
-    fa, fb = a["ft"], b["ft"]
-    scale = np.abs(fb).max(axis=0, keepdims=True)
-    scale = np.maximum(scale, 1e-300)
-    return (np.abs(fa - fb) / scale).max()
+def ft_err(a, b, lever=1.0):
+    """Force/torque error of series a against b: max |dF| over the force
+    components relative to the largest |F| of b, and max |dT| relative to
+    max(largest |T| of b, largest |F| of b x a lever arm of `lever` cells), so
+    that components that vanish by symmetry are compared at the scale of the
+    ones that do not."""
+    fa, fb = np.asarray(a["ft"]), np.asarray(b["ft"])
+    sF = np.abs(fb[..., :3]).max()
+    sT = max(np.abs(fb[..., 3:]).max(), sF * lever)
+    eF = np.abs(fa[..., :3] - fb[..., :3]).max() / max(sF, 1e-300)
+    eT = np.abs(fa[..., 3:] - fb[..., 3:]).max() / max(sT, 1e-300)
+    return max(eF, eT)

@@ -37,6 +37,7 @@ def test_c1_fp64_full(streaming):
     case = W.c1_sphere().with_(streaming=streaming)
     g, o = run_gpu(case), run_oracle(case)
     perm = perm_lib_to_oracle(19)
+    print(f"C1 fp64 {streaming}: u {u_err(g, o, case):.2e}, F/T {ft_err(g, o):.2e}")
     assert u_err(g, o, case) <= 1e-12
     assert np.abs(g["f"] - o["f"][perm]).max() <= 1e-13
     assert ft_err(g, o) <= 1e-10
@@ -47,6 +48,7 @@ def test_c1_fp64_full(streaming):
 def test_c1_fp32():
     case = W.c1_sphere().with_(storage="fp32")
     g, o = run_gpu(case), run_oracle(case)
+    print(f"C1 fp32: u {u_err(g, o, case):.2e}, F/T {ft_err(g, o):.2e}")
     assert u_err(g, o, case) <= 2e-5
     assert ft_err(g, o) <= 1e-4
 
@@ -55,6 +57,7 @@ def test_c1_fp32():
 def test_c2_reduced_fp32_trt_rotating(streaming):
     case = c2_reduced("fp32", streaming)
     g, o = run_gpu(case), run_oracle(case)
+    print(f"C2/64 fp32 {streaming}: u {u_err(g, o, case):.2e}, F/T {ft_err(g, o):.2e}")
     assert u_err(g, o, case) <= 2e-5
     assert ft_err(g, o) <= 1e-4
     assert np.abs(o["ft"][:, 0, 5]).max() > 0
@@ -128,6 +131,7 @@ def test_d3q27_rotor_proxy(storage, tol):
     case = W.c3_rotor(storage=storage, scale=0.12, dims=(48, 48, 60), steps=60)
     case = case.with_(bodies=[b for b in case.bodies])
     g, o = run_gpu(case), run_oracle(case)
+    print(f"D3Q27 rotor {storage}: u {u_err(g, o, case):.2e}, F/T {ft_err(g, o):.2e}")
     assert u_err(g, o, case) <= tol
     assert ft_err(g, o) <= (1e-10 if storage == "fp64" else 1e-4)
     assert len(case.bodies) == 2 and np.abs(o["ft"][:, 1, 5]).max() > 0
