@@ -238,8 +238,24 @@ int psm_series_capacity(psm_handle h, int64_t* out);
  * PSM_ERR_NONFINITE if it is not finite. */
 int psm_mass(psm_handle h, double* out);
 
-/* Wait for all work of the handle. */
+/* Wait for all work of the handle.  PSM_ERR_CUDA if a step kernel gave up
+ * waiting for its staged loads (it records this in a flag instead of
+ * trapping). */
 int psm_synchronize(psm_handle h);
+
+/* Step-kernel variant: PSM_KERNEL_AUTO (default) uses the TMA-staged kernel
+ * when the shape allows it, else plain global loads; PSM_KERNEL_PLAIN forces
+ * plain loads; PSM_KERNEL_TMA forces TMA staging (PSM_ERR_UNSUPPORTED if the
+ * shape does not allow it).  TMA shapes: with TX = min(256, nx):
+ * nx % TX == 0, 256 % nx == 0 when nx < 256, TX >= 32, ny % (256 / TX) == 0,
+ * nx * sizeof(PDF) a multiple of 16 bytes.  Both variants compute the same
+ * results. */
+#define PSM_KERNEL_AUTO 0
+#define PSM_KERNEL_PLAIN 1
+#define PSM_KERNEL_TMA 2
+int psm_set_kernel_variant(psm_handle h, int variant);
+/* The variant psm_step uses now (PSM_KERNEL_PLAIN or PSM_KERNEL_TMA). */
+int psm_kernel_variant(psm_handle h, int* out);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "psm_kernels.cuh"
 
 namespace {
@@ -101,6 +103,12 @@ struct psm_solver {
   int64_t cap = 0;
   double* d_sum = nullptr;
   float* d_delta = nullptr;
+  int* d_err = nullptr;
+  // TMA-staged step kernel: eligibility, its tiling and the tensor maps per buffer
+  bool tma_ok = false;
+  int variant = PSM_KERNEL_AUTO;
+  psm::Tiling tma_tiling;
+  psm::TmaMaps maps[2];
 };
 
 namespace psm {
@@ -220,6 +228,8 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
     d.R[k] = R[k];
     d.omega[k] = b.omega[k];
     d.v[k] = b.v[k];
+    d.omegaf[k] = (float)b.omega[k];
+    d.vf[k] = (float)b.v[k];
   }
   double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
   const double ext[3] = {(double)b.gx, (double)b.gy, (double)b.gz};
@@ -288,6 +298,88 @@ int import_uniform(psm_solver* h, double rho, const double u[3]) {
 }
 
 bool valid_handle(psm_handle h) { return h != nullptr; }
+
+// TMA shape rules (see k_step_tma): TX = min(256, nx), nx % TX == 0,
+// 256 % nx == 0 if nx < 256, TY = 256 / TX divides ny, rows of 16-byte
+// multiples, at least 32 cells per row segment.
+bool tma_shape(const psm_solver* h, psm::Tiling& t) {
+  const int64_t nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
+  const int64_t b = (int64_t)storage_bytes(h->lat.storage);
+  const int64_t TX = nx >= 256 ? 256 : nx;
+  if (TX < 32 || nx % TX != 0 || (nx < 256 && 256 % nx != 0)) return false;
+  const int64_t TY = 256 / TX;
+  if (ny % TY != 0 || (TX * b) % 16 != 0 || (nx * b) % 16 != 0) return false;
+  t.tx = (int)TX;
+  t.ty = (int)TY;
+  t.ntx = (int)(nx / TX);
+  t.nty = (int)(ny / TY);
+  t.ntiles = (long long)t.ntx * t.nty * nz;
+  return true;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      ptr = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }();
+  return fn;
+}
+
+// Tensor maps of PDF buffer `buf` as a (x, y, z, slot) tensor.
+bool encode_maps(const psm_solver* h, void* buf, psm::TmaMaps& m) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return false;
+  CUtensorMapDataType dt = h->lat.storage == PSM_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : h->lat.storage == PSM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : h->lat.storage == PSM_FP16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t b = storage_bytes(h->lat.storage);
+  const cuuint64_t dims[4] = {(cuuint64_t)h->grid.nx, (cuuint64_t)h->grid.ny, (cuuint64_t)h->grid.nz,
+                              (cuuint64_t)h->Q};
+  const cuuint64_t strides[3] = {dims[0] * b, dims[0] * dims[1] * b, dims[0] * dims[1] * dims[2] * b};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  const cuuint32_t box_q[4] = {(cuuint32_t)h->tma_tiling.tx, 1, 1, (cuuint32_t)h->Q};
+  const cuuint32_t box_1[4] = {(cuuint32_t)h->tma_tiling.tx, 1, 1, 1};
+  CUresult r1 = enc(&m.rowq, dt, 4, buf, dims, strides, box_q, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = enc(&m.row1, dt, 4, buf, dims, strides, box_1, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+}
+
+template <class T>
+void fill_consts(const psm_solver* h, psm::ConstT<T>& c) {
+  c.rho0 = (T)h->grid.rho0;
+  if (h->col.fluid == PSM_TRT) {
+    const double wp = 1.0 / h->col.tau;
+    const double wm = 1.0 / (h->col.trt_lambda / (h->col.tau - 0.5) + 0.5);
+    c.om_a = (T)(0.5 * (wp + wm));
+    c.om_b = (T)(0.5 * (wp - wm));
+  } else {
+    c.om_a = (T)(1.0 / h->col.tau);
+    c.om_b = (T)0;
+  }
+  c.inv_tau = (T)(1.0 / h->col.tau);
+  c.tmh = (T)(h->col.tau - 0.5);
+  for (int i = 0; i < 27; ++i) c.ghost[i] = (T)h->ghost[i];
+}
+
+// A kernel gave up on a bounded wait: report it once.
+int check_err(psm_solver* h) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "error-flag read");
+  if (flag) {
+    cudaMemset(h->d_err, 0, sizeof(int));
+    return fail(PSM_ERR_CUDA, "a step kernel timed out waiting for its staged loads (results invalid)");
+  }
+  return PSM_OK;
+}
 
 }  // namespace
 
@@ -369,7 +461,15 @@ int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_colli
   h->cap = 1 << 16;
   if (e == cudaSuccess) e = cudaMalloc(&h->d_series, sizeof(double) * (size_t)h->cap * PSM_MAX_BODIES * 6);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_sum, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch allocation"));
+  e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch initialisation"));
+  // the TMA-staged kernel where the shape allows it
+  if (tma_shape(h, h->tma_tiling)) {
+    h->tma_ok = true;
+    for (int b = 0; b < nbuf; ++b) h->tma_ok = h->tma_ok && encode_maps(h, h->buf[b], h->maps[b]);
+  }
   e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), h->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->d_series, 0, sizeof(double) * (size_t)h->cap * PSM_MAX_BODIES * 6, h->stream);
@@ -390,6 +490,7 @@ int psm_destroy(psm_handle h) {
   cudaFree(h->d_series);
   cudaFree(h->d_sum);
   cudaFree(h->d_delta);
+  cudaFree(h->d_err);
   delete h;
   return PSM_OK;
 }
@@ -566,46 +667,56 @@ int psm_step(psm_handle h, int n) {
   if (n < 0) return fail(PSM_ERR_ARG, "psm_step: n must be >= 0");
   StepParams p;
   std::memset(&p, 0, sizeof p);
+  const bool use_tma = h->tma_ok && h->variant != PSM_KERNEL_PLAIN;
   p.g = h->g;
-  p.t = h->tiling;
-  for (int i = 0; i < 27; ++i) p.ghost[i] = h->ghost[i];
-  p.rho0 = h->grid.rho0;
-  p.tau = h->col.tau;
-  if (h->col.fluid == PSM_TRT) {
-    const double wp = 1.0 / h->col.tau;
-    const double wm = 1.0 / (h->col.trt_lambda / (h->col.tau - 0.5) + 0.5);
-    p.om_a = 0.5 * (wp + wm);
-    p.om_b = 0.5 * (wp - wm);
-    p.trt = 1;
-  } else {
-    p.om_a = 1.0 / h->col.tau;
-    p.om_b = 0.0;
-    p.trt = 0;
-  }
+  p.t = use_tma ? h->tma_tiling : h->tiling;
+  fill_consts<float>(h, p.cf);
+  fill_consts<double>(h, p.cd);
+  p.trt = h->col.fluid == PSM_TRT ? 1 : 0;
   p.solid = h->col.solid;
   p.weighting = h->col.weighting;
   p.nbodies = h->nbodies;
   p.delta = h->d_delta;
   p.partials = h->d_partials;
   p.ticket = h->d_ticket;
+  p.err = h->d_err;
   for (int k = 0; k < n; ++k) {
     for (int b = 0; b < h->nbodies; ++b) p.body[b] = dev_body(h, b, h->step);
     p.ft_out = h->d_series + (size_t)(h->step % h->cap) * PSM_MAX_BODIES * 6;
-    int mode;
+    int mode, src;
     if (h->lat.streaming == PSM_STREAM_TWO_GRID) {
       mode = psm::MODE_TG;
+      src = h->cur;
       p.f = h->buf[h->cur];
       p.f_dst = h->buf[h->cur ^ 1];
     } else {
       mode = (h->step & 1) ? psm::MODE_AA_ODD : psm::MODE_AA_EVEN;
+      src = 0;
       p.f = h->buf[0];
       p.f_dst = nullptr;
     }
-    cudaError_t e = psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);
+    cudaError_t e = use_tma ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, h->maps[src], h->stream)
+                            : psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     if (h->lat.streaming == PSM_STREAM_TWO_GRID) h->cur ^= 1;
     h->step++;
   }
+  return PSM_OK;
+}
+
+int psm_set_kernel_variant(psm_handle h, int variant) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_set_kernel_variant: NULL handle");
+  if (variant != PSM_KERNEL_AUTO && variant != PSM_KERNEL_PLAIN && variant != PSM_KERNEL_TMA)
+    return fail(PSM_ERR_ARG, "unknown kernel variant %d", variant);
+  if (variant == PSM_KERNEL_TMA && !h->tma_ok)
+    return fail(PSM_ERR_UNSUPPORTED, "the TMA-staged kernel does not support this grid shape / storage");
+  h->variant = variant;
+  return PSM_OK;
+}
+
+int psm_kernel_variant(psm_handle h, int* out) {
+  if (!valid_handle(h) || !out) return fail(PSM_ERR_ARG, "psm_kernel_variant: NULL argument");
+  *out = (h->tma_ok && h->variant != PSM_KERNEL_PLAIN) ? PSM_KERNEL_TMA : PSM_KERNEL_PLAIN;
   return PSM_OK;
 }
 
@@ -631,6 +742,10 @@ int psm_force_torque(psm_handle h, int body, int64_t step_from, int64_t count, d
     return fail(PSM_ERR_ARG, "step %lld is older than the kept series (%lld steps)", (long long)step_from,
                 (long long)h->cap);
   PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  {
+    const int rc = check_err(h);
+    if (rc != PSM_OK) return rc;
+  }
   const size_t row = PSM_MAX_BODIES * 6;
   std::vector<double> tmp(row);
   bool finite = true;
@@ -672,6 +787,10 @@ int psm_mass(psm_handle h, double* out) {
   PSM_CUDA(psm::launch_mass(h->lat.storage, h->Q, p, (int)blocks, h->stream), "mass kernel");
   PSM_CUDA(cudaMemcpyAsync(out, h->d_sum, sizeof(double), cudaMemcpyDefault, h->stream), "mass download");
   PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  {
+    const int rc = check_err(h);
+    if (rc != PSM_OK) return rc;
+  }
   if (!std::isfinite(*out)) return fail(PSM_ERR_NONFINITE, "mass is NaN or Inf");
   return PSM_OK;
 }
@@ -679,7 +798,7 @@ int psm_mass(psm_handle h, double* out) {
 int psm_synchronize(psm_handle h) {
   if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_synchronize: NULL handle");
   PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
-  return PSM_OK;
+  return check_err(h);
 }
 
 }  // extern "C"

@@ -2,6 +2,7 @@
 // translation units (psm_kern_*.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,10 +33,12 @@ struct DevBody {
   float Qf[9];  // world <- body, row-major
   float Rf[3];  // reference point R_n
   float Cf[3];  // lo + 1/2
-  // kinematics in double (converted to the compute precision in the kernel)
+  // kinematics in double (FP64 path, force/torque lever arm) and float (FP32 path)
   double R[3];
   double omega[3];
   double v[3];
+  float omegaf[3];
+  float vf[3];
   // cells tested for this body: [x0, x1) x [y0, y1) x [z0, z1)
   int x0, x1, y0, y1, z0, z1;
 };
@@ -52,15 +55,22 @@ struct Tiling {
   long long ntiles;
 };
 
+// Per-step constants in the compute precision, precomputed on the host so that
+// no kernel converts or divides doubles per cell.
+template <class T>
+struct ConstT {
+  T rho0;
+  T om_a, om_b;  // TRT as Omega^F_i = -om_a n_i - om_b n_opp(i); BGK: om_a = 1/tau, om_b = 0
+  T inv_tau;     // 1 / tau (SC2)
+  T tmh;         // tau - 1/2 (Eq. 6)
+  T ghost[27];   // shifted ghost-plane populations f^eq_i(rho0, u_in) - w_i rho0
+};
+
 struct StepParams {
   Grid3 g;
   Tiling t;
   void* f;      // AA: the buffer; TG: source
   void* f_dst;  // TG: destination
-  double ghost[27];  // shifted ghost-plane populations f^eq_i(rho0, u_in) - w_i rho0
-  double rho0;
-  double tau;
-  double om_a, om_b;  // TRT as Omega^F_i = -om_a n_i - om_b n_opp(i); BGK: om_a = 1/tau, om_b = 0
   int trt;
   int solid;      // 1, 2, 3
   int weighting;  // 0 direct, 1 tau-weighted
@@ -71,6 +81,16 @@ struct StepParams {
   double* partials;      // [gridDim.x][nbodies * 6]
   unsigned int* ticket;  // zero between launches
   double* ft_out;        // [nbodies * 6] of this step (body convention)
+  int* err;              // set non-zero by a kernel that gave up waiting (never traps)
+  ConstT<float> cf;      // constants for FP32 arithmetic
+  ConstT<double> cd;     // constants for FP64 arithmetic
+};
+
+// Tensor maps of one PDF buffer viewed as a 4-D tensor (x, y, z, slot):
+// rowq = box (TX, 1, 1, Q) (a tile row of every slot), row1 = box (TX, 1, 1, 1).
+struct TmaMaps {
+  CUtensorMap rowq;
+  CUtensorMap row1;
 };
 
 // Parameters of the import / export / reduction kernels.
@@ -114,6 +134,10 @@ Tiling make_tiling(int nx, int ny, int nz);
 // returns cudaSuccess or the launch error.  `grid_out` reports the number of
 // blocks the step kernel uses (so the host sizes the partials array).
 cudaError_t launch_step(int storage, int Q, int mode, const StepParams& p, cudaStream_t st);
+// TMA-staged variant (shape rules at k_step_tma); p.t must be the TMA tiling.
+cudaError_t launch_step_tma(int storage, int Q, int mode, const StepParams& p, const TmaMaps& m, cudaStream_t st);
+// dynamic shared memory bytes the TMA variant needs for a TX x TY tile
+int tma_smem_bytes(int storage, int Q, int mode, int tx, int ty);
 int step_grid_blocks(int storage, int Q, int mode, int trt);
 cudaError_t launch_import(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_export(int storage, int Q, const IoParams& p, cudaStream_t st);
@@ -123,6 +147,9 @@ cudaError_t launch_remap(const RemapParams& p, cudaStream_t st);
 
 #define PSM_DECLARE_STORAGE(NAME)                                                          \
   cudaError_t launch_step_##NAME(int Q, int mode, int trt, const StepParams& p, cudaStream_t st); \
+  cudaError_t launch_step_tma_##NAME(int Q, int mode, int trt, const StepParams& p, const TmaMaps& m, \
+                                     cudaStream_t st);                                    \
+  int tma_smem_bytes_##NAME(int Q, int mode, int tx, int ty);                             \
   int step_grid_blocks_##NAME(int Q, int mode, int trt);                                  \
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st);            \

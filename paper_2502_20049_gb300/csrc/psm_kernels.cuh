@@ -273,12 +273,201 @@ __device__ __forceinline__ void grid_reduce(const double* blk, int ncomp, double
 #define PSM_MIN_BLOCKS_Q27 2
 #endif
 
+template <class T>
+__device__ __forceinline__ const ConstT<T>& cst(const StepParams& p) {
+  if constexpr (sizeof(T) == 4) return p.cf;
+  else return p.cd;
+}
+
+// One cell's PSM update in registers, from its pre-collision (shifted) PDFs f:
+// remap (Sec. 3), B (Eq. 5/6), moments, u_s = omega x r + v, Omega^F (Eq. 2 /
+// TRT), Omega^S (Eq. 7/8/9), blend (Eq. 4).  f becomes the post-collision
+// state.  For a cell in contact with a body (B > 0) ft receives the force and
+// torque on the body (minus Eq. 10 / 11 per cell, about R_n).
+template <class T, int Q, int TRT>
+__device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int x, int y, int z, unsigned cell,
+                                            int& owner, bool& solid_cell, double (&ft)[6]) {
+  const ConstT<T>& C = cst<T>(p);
+  const T rho0 = C.rho0;
+  const T om_a = C.om_a, om_b = C.om_b;
+  const T inv_tau = C.inv_tau;
+  // ---- remap (Sec. 3) and weighting (Eq. 5/6) ----
+  const float epsf = cell_eps(p.body, p.nbodies, x, y, z, owner);
+  T eps = T(epsf);
+  if (p.delta) eps += T(p.delta[cell]);
+  T Bw = eps;
+  if (p.weighting == PSM_B_TAU_WEIGHTED) {
+    const T t = C.tmh;
+    Bw = eps * t / ((T(1) - eps) + t);
+  }
+  // ---- moments ----
+  T drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += f[i];
+    if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
+    if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
+    if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
+  }
+  const T rho = rho0 + drho;
+  const T inv_rho = T(1) / rho;
+  const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+  const T uu = ux * ux + uy * uy + uz * uz;
+  solid_cell = Bw != T(0);
+  if (!solid_cell) {
+    // ---- pure fluid: f* = f + Omega^F ----
+    {
+      const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
+      f[0] = f[0] - (om_a + om_b) * n0;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const int j = i + 1;
+      const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
+      const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
+      if (TRT) {
+        f[i] = f[i] - om_a * ni - om_b * nj;
+        f[j] = f[j] - om_a * nj - om_b * ni;
+      } else {
+        f[i] = f[i] - om_a * ni;
+        f[j] = f[j] - om_a * nj;
+      }
+    }
+    return;
+  }
+  // ---- PSM cell: f* = f + (1 - B) Omega^F + B Omega^S (Eq. 4) ----
+  T usx = 0, usy = 0, usz = 0;
+  if (owner >= 0) {
+    const DevBody& b = p.body[owner];
+    T rx, ry, rz, wx, wy, wz, vx, vy, vz;
+    if constexpr (sizeof(T) == 4) {
+      rx = (T(x) + T(0.5)) - b.Rf[0];
+      ry = (T(y) + T(0.5)) - b.Rf[1];
+      rz = (T(z) + T(0.5)) - b.Rf[2];
+      wx = b.omegaf[0], wy = b.omegaf[1], wz = b.omegaf[2];
+      vx = b.vf[0], vy = b.vf[1], vz = b.vf[2];
+    } else {
+      rx = (double)x + 0.5 - b.R[0];
+      ry = (double)y + 0.5 - b.R[1];
+      rz = (double)z + 0.5 - b.R[2];
+      wx = b.omega[0], wy = b.omega[1], wz = b.omega[2];
+      vx = b.v[0], vy = b.v[1], vz = b.v[2];
+    }
+    usx = wy * rz - wz * ry + vx;
+    usy = wz * rx - wx * rz + vy;
+    usz = wx * ry - wy * rx + vz;
+  }
+  const T usus = usx * usx + usy * usy + usz * usz;
+  const T omB = T(1) - Bw;
+  T gx = 0, gy = 0, gz = 0;
+  {
+    const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
+    const T m0 = f[0] - feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
+    const T of = -(om_a + om_b) * n0;
+    T os;
+    if (p.solid == PSM_SC1) os = n0 - m0;
+    else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
+    else os = T(0);
+    f[0] = f[0] + omB * of + Bw * os;
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int j = i + 1;
+    const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
+    const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
+    const T mi = f[i] - feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
+    const T mj = f[j] - feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
+    const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
+    const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);
+    T osi, osj;
+    if (p.solid == PSM_SC1) {
+      osi = nj - mi;
+      osj = ni - mj;
+    } else if (p.solid == PSM_SC2) {
+      osi = -mi * inv_tau;
+      osj = -mj * inv_tau;
+    } else {
+      osi = mj - mi;
+      osj = mi - mj;
+    }
+    f[i] = f[i] + omB * ofi + Bw * osi;
+    f[j] = f[j] + omB * ofj + Bw * osj;
+    // c_j = -c_i: sum_i Omega^S_i c_i over the pair
+    const T d = osi - osj;
+    if (lat_cx(i)) gx += T(lat_cx(i)) * d;
+    if (lat_cy(i)) gy += T(lat_cy(i)) * d;
+    if (lat_cz(i)) gz += T(lat_cz(i)) * d;
+  }
+  if (owner >= 0) {
+    // Eq. 10 / 11 per cell; the body receives minus the solid's momentum transfer
+    const double Gx = (double)(Bw * gx), Gy = (double)(Bw * gy), Gz = (double)(Bw * gz);
+    const DevBody& b = p.body[owner];
+    const double Rx = (double)x + 0.5 - b.R[0], Ry = (double)y + 0.5 - b.R[1], Rz = (double)z + 0.5 - b.R[2];
+    ft[0] = -Gx;
+    ft[1] = -Gy;
+    ft[2] = -Gz;
+    ft[3] = -(Ry * Gz - Rz * Gy);
+    ft[4] = -(Rz * Gx - Rx * Gz);
+    ft[5] = -(Rx * Gy - Ry * Gx);
+  }
+}
+
+// Streamed store (Eq. 1) of one cell's post-collision PDFs.
+template <class S, int Q, int MODE, class T>
+__device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Nbr& nbr, unsigned cell, const T (&f)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+    if (MODE == MODE_AA_EVEN) {
+      Store<S>::st(buf + (long long)lat_opp(i) * N + cell, f[i]);
+    } else if (!nbr.to_ghost(cz)) {
+      S* base = (MODE == MODE_TG) ? dst : buf;
+      Store<S>::st(base + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
+    }
+  }
+}
+
+// Per-warp force/torque accumulation into s_ft[warp] (fixed order: warp
+// butterfly, then in tile order).  All 32 lanes must call it.
+__device__ __forceinline__ void warp_ft(double (*s_ft)[PSM_MAX_BODIES * 6], int nb, bool contributes, int owner,
+                                        const double (&ft)[6]) {
+  if (nb == 0 || !__any_sync(0xffffffffu, contributes)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int bi = 0; bi < nb; ++bi) {
+    const bool mine = contributes && owner == bi;
+    if (!__any_sync(0xffffffffu, mine)) continue;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double v = warp_sum(mine ? ft[k] : 0.0);
+      if (lane == 0) s_ft[warp][bi * 6 + k] += v;
+    }
+  }
+}
+
+// Block sum of the per-warp slots (fixed order), then the grid-wide ordered sum.
+__device__ __forceinline__ void block_ft_finish(double (*s_ft)[PSM_MAX_BODIES * 6], const StepParams& p) {
+  constexpr int NW = PSM_THREADS / 32;
+  __shared__ double blk[PSM_MAX_BODIES * 6];
+  const int ncomp = p.nbodies * 6;
+  __syncthreads();
+  if ((int)threadIdx.x < ncomp) {
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w) s += s_ft[w][threadIdx.x];
+    blk[threadIdx.x] = s;
+  }
+  __syncthreads();
+  grid_reduce(blk, ncomp, p.partials, p.ticket, p.ft_out);
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel with plain global loads (any grid shape; persistent:
+// blocks stride over row tiles).
+// ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int TRT>
 __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
     k_step(const __grid_constant__ StepParams p) {
   using T = typename Store<S>::T;
-  constexpr int NW = PSM_THREADS / 32;
-  __shared__ double s_ft[NW][PSM_MAX_BODIES * 6];
+  __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
   const int nb = p.nbodies;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
@@ -286,10 +475,6 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   S* __restrict__ buf = static_cast<S*>(p.f);
   S* __restrict__ dst = static_cast<S*>(p.f_dst);
   const long long N = p.g.ncell;
-  const T rho0 = T(p.rho0);
-  const T om_a = T(p.om_a), om_b = T(p.om_b);
-  const T inv_tau = T(1.0 / p.tau);
-
   const int ntiles = (int)p.t.ntiles;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int x, y, z;
@@ -302,168 +487,269 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
       const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
       Nbr nbr;
       nbr.init(p.g, x, y, z);
-      // ---- load (pre-collision f, shifted) ----
       T f[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
         if (nbr.from_ghost(cz)) {
-          f[i] = T(p.ghost[i]);
+          f[i] = cst<T>(p).ghost[i];
         } else if (MODE == MODE_AA_ODD) {
           f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
         } else {
           f[i] = Store<S>::ld(buf + (long long)i * N + cell);
         }
       }
-      // ---- remap (Sec. 3) and weighting (Eq. 5/6) ----
-      const float epsf = cell_eps(p.body, nb, x, y, z, owner);
-      T eps = T(epsf);
-      if (p.delta) eps += T(p.delta[cell]);
-      T Bw = eps;
-      if (p.weighting == PSM_B_TAU_WEIGHTED) {
-        const T t = T(p.tau - 0.5);
-        Bw = eps * t / ((T(1) - eps) + t);
-      }
-      // ---- moments ----
-      T drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        drho += f[i];
-        if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
-        if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
-        if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
-      }
-      const T rho = rho0 + drho;
-      const T inv_rho = T(1) / rho;
-      const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-      const T uu = ux * ux + uy * uy + uz * uz;
-      solid_cell = Bw != T(0);
-      if (!solid_cell) {
-        // ---- pure fluid: f* = f + Omega^F ----
-        {
-          const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
-          f[0] = f[0] - (om_a + om_b) * n0;
-        }
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-          const int j = i + 1;
-          const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
-          const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
-          if (TRT) {
-            f[i] = f[i] - om_a * ni - om_b * nj;
-            f[j] = f[j] - om_a * nj - om_b * ni;
-          } else {
-            f[i] = f[i] - om_a * ni;
-            f[j] = f[j] - om_a * nj;
-          }
-        }
-      } else {
-        // ---- PSM cell: f* = f + (1 - B) Omega^F + B Omega^S (Eq. 4) ----
-        T usx = 0, usy = 0, usz = 0;
-        T rx = 0, ry = 0, rz = 0;
-        if (owner >= 0) {
-          const DevBody& b = p.body[owner];
-          rx = T((double)x + 0.5 - b.R[0]);
-          ry = T((double)y + 0.5 - b.R[1]);
-          rz = T((double)z + 0.5 - b.R[2]);
-          const T wx = T(b.omega[0]), wy = T(b.omega[1]), wz = T(b.omega[2]);
-          usx = wy * rz - wz * ry + T(b.v[0]);
-          usy = wz * rx - wx * rz + T(b.v[1]);
-          usz = wx * ry - wy * rx + T(b.v[2]);
-        }
-        const T usus = usx * usx + usy * usy + usz * usz;
-        const T omB = T(1) - Bw;
-        T gx = 0, gy = 0, gz = 0;
-        {
-          const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
-          const T m0 = f[0] - feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
-          const T of = -(om_a + om_b) * n0;
-          T os;
-          if (p.solid == PSM_SC1) os = n0 - m0;
-          else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
-          else os = T(0);
-          f[0] = f[0] + omB * of + Bw * os;
-        }
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-          const int j = i + 1;
-          const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
-          const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
-          const T mi = f[i] - feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
-          const T mj = f[j] - feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
-          const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
-          const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);
-          T osi, osj;
-          if (p.solid == PSM_SC1) {
-            osi = nj - mi;
-            osj = ni - mj;
-          } else if (p.solid == PSM_SC2) {
-            osi = -mi * inv_tau;
-            osj = -mj * inv_tau;
-          } else {
-            osi = mj - mi;
-            osj = mi - mj;
-          }
-          f[i] = f[i] + omB * ofi + Bw * osi;
-          f[j] = f[j] + omB * ofj + Bw * osj;
-          // c_j = -c_i: sum_i Omega^S_i c_i over the pair
-          const T d = osi - osj;
-          if (lat_cx(i)) gx += T(lat_cx(i)) * d;
-          if (lat_cy(i)) gy += T(lat_cy(i)) * d;
-          if (lat_cz(i)) gz += T(lat_cz(i)) * d;
-        }
-        if (owner >= 0) {
-          // Eq. 10 / 11 per cell; the body receives minus the solid's momentum transfer
-          const double Gx = (double)(Bw * gx), Gy = (double)(Bw * gy), Gz = (double)(Bw * gz);
-          const DevBody& b = p.body[owner];
-          const double Rx = (double)x + 0.5 - b.R[0], Ry = (double)y + 0.5 - b.R[1], Rz = (double)z + 0.5 - b.R[2];
-          ft[0] = -Gx;
-          ft[1] = -Gy;
-          ft[2] = -Gz;
-          ft[3] = -(Ry * Gz - Rz * Gy);
-          ft[4] = -(Rz * Gx - Rx * Gz);
-          ft[5] = -(Rx * Gy - Ry * Gx);
-        }
-      }
-      // ---- streamed store (Eq. 1) ----
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
-        if (MODE == MODE_AA_EVEN) {
-          Store<S>::st(buf + (long long)lat_opp(i) * N + cell, f[i]);
-        } else if (!nbr.to_ghost(cz)) {
-          S* base = (MODE == MODE_TG) ? dst : buf;
-          Store<S>::st(base + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
-        }
-      }
+      psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
+      psm_store<S, Q, MODE>(buf, dst, N, nbr, cell, f);
     }
-    // ---- per-warp force/torque accumulation (fixed order) ----
-    if (nb > 0) {
-      const bool contributes = active && solid_cell && owner >= 0;
-      if (__any_sync(0xffffffffu, contributes)) {
-        for (int bi = 0; bi < nb; ++bi) {
-          const bool mine = contributes && owner == bi;
-          if (!__any_sync(0xffffffffu, mine)) continue;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const double v = warp_sum(mine ? ft[k] : 0.0);
-            if (lane == 0) s_ft[warp][bi * 6 + k] += v;
-          }
-        }
-      }
-    }
+    warp_ft(s_ft, nb, active && solid_cell && owner >= 0, owner, ft);
   }
   if (nb == 0) return;
-  __syncthreads();
-  __shared__ double blk[PSM_MAX_BODIES * 6];
-  const int ncomp = nb * 6;
-  if ((int)threadIdx.x < ncomp) {
-    double s = 0.0;
-    for (int w = 0; w < NW; ++w) s += s_ft[w][threadIdx.x];
-    blk[threadIdx.x] = s;
+  block_ft_finish(s_ft, p);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged step kernel.  Shapes: nx % TX == 0 with TX = min(256, nx) (and
+// 256 % nx == 0 when nx < 256), TY = 256 / TX rows per tile, ny % TY == 0, and
+// TX * sizeof(S) a multiple of 16 bytes.  Persistent blocks stride over tiles;
+// thread 0 keeps PSM_TMA_STAGES tiles of pre-collision rows in flight in
+// shared memory (cp.async.bulk.tensor row boxes, plus 16-byte
+// cp.async.bulk edge chunks for the neighbours' x - c_x in the AA odd step)
+// while all threads collide the oldest staged tile from shared memory.
+// ---------------------------------------------------------------------------
+#ifndef PSM_TMA_STAGES
+#define PSM_TMA_STAGES 3
+#endif
+
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+  return (unsigned)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load_16(void* dst, const void* src, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Shared-memory layout of one stage (bytes), 128-byte aligned row boxes.
+template <class S, int Q, int MODE>
+struct TmaLayout {
+  static constexpr int EP = 16 / (int)sizeof(S);  // elements per 16-byte edge chunk
+  __host__ __device__ static int row_bytes(int tx) { return ((tx * (int)sizeof(S) + 127) / 128) * 128; }
+  // own-row modes: one [Q][TX] box per tile row; odd step: one [TX] box per row and direction
+  __host__ __device__ static int box_bytes(int tx) {
+    return MODE == MODE_AA_ODD ? row_bytes(tx) : ((Q * tx * (int)sizeof(S) + 127) / 128) * 128;
+  }
+  __host__ __device__ static int main_bytes(int tx, int ty) {
+    return MODE == MODE_AA_ODD ? ty * Q * row_bytes(tx) : ty * box_bytes(tx);
+  }
+  __host__ __device__ static int edge_bytes(int ty) { return MODE == MODE_AA_ODD ? ty * Q * 2 * 16 : 0; }
+  __host__ __device__ static int stage_bytes(int tx, int ty) {
+    return ((main_bytes(tx, ty) + edge_bytes(ty) + 127) / 128) * 128;
+  }
+  // + 128 B of barriers, + 128 B of alignment slack
+  __host__ __device__ static int smem_bytes(int tx, int ty) { return 256 + PSM_TMA_STAGES * stage_bytes(tx, ty); }
+};
+
+template <class S, int Q, int MODE, int TRT>
+__global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
+    k_step_tma(const __grid_constant__ StepParams p, const __grid_constant__ TmaMaps maps) {
+  using T = typename Store<S>::T;
+  using L = TmaLayout<S, Q, MODE>;
+  constexpr int NST = PSM_TMA_STAGES;
+  constexpr int EP = L::EP;
+  __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
+  __shared__ int s_abort;
+  __shared__ int s_issued[NST];  // loads issued per stage (thread 0 only)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // dynamic shared memory is only guaranteed 16-byte alignment: align by hand
+  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(base);  // NST barriers in the first 128 B
+  unsigned char* stages = base + 128;
+
+  const int nb = p.nbodies;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
+  const int TX = p.t.tx, TY = p.t.ty;
+  const int SB = L::stage_bytes(TX, TY);
+  const int RB = L::row_bytes(TX), BB = L::box_bytes(TX), MB = L::main_bytes(TX, TY);
+  const long long N = p.g.ncell;
+  S* __restrict__ buf = static_cast<S*>(p.f);
+  S* __restrict__ dst = static_cast<S*>(p.f_dst);
+  const void* map_rows = (MODE == MODE_AA_ODD) ? (const void*)&maps.row1 : (const void*)&maps.rowq;
+  const int ntiles = (int)p.t.ntiles;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&bars[s], 1);
+      s_issued[s] = 0;
+    }
+    fence_mbar_init();
   }
   __syncthreads();
-  grid_reduce(blk, ncomp, p.partials, p.ticket, p.ft_out);
+
+  // producer: stage the pre-collision rows of tile `tile` into stage `s`
+  auto produce = [&](int tile, int s) {
+    int tx0, y0, z;
+    {
+      const int tx = tile % p.t.ntx;
+      const int r = tile / p.t.ntx;
+      const int ty = r % p.t.nty;
+      z = r / p.t.nty;
+      tx0 = tx * TX;
+      y0 = ty * TY;
+    }
+    unsigned char* st = stages + (long long)s * SB;
+    unsigned long long* bar = &bars[s];
+    fence_proxy_async();
+    for (int r = 0; r < TY; ++r) {
+      const int y = y0 + r;
+      if (MODE != MODE_AA_ODD) {
+        mbar_expect_tx(bar, (unsigned)(Q * TX * (int)sizeof(S)));
+        tma_load_4d(st + r * BB, map_rows, tx0, y, z, 0, bar);
+      } else {
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+          const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+          int zs = z - cz;
+          if (zs < 0 || zs >= p.g.nz) {
+            if (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET) continue;  // ghost populations: no load
+            zs = zs < 0 ? zs + p.g.nz : zs - p.g.nz;
+          }
+          int ys = y - cy;
+          ys = ys < 0 ? ys + p.g.ny : (ys >= p.g.ny ? ys - p.g.ny : ys);
+          const int slot = lat_opp(i);
+          mbar_expect_tx(bar, (unsigned)(TX * (int)sizeof(S)));
+          tma_load_4d(st + (r * Q + i) * RB, map_rows, tx0, ys, zs, slot, bar);
+          if (cx != 0) {
+            // cx = +1 reads x0 - 1 (left chunk), cx = -1 reads x0 + TX (right chunk), wrapped in x
+            const int xe = cx > 0 ? (tx0 == 0 ? p.g.nx - EP : tx0 - EP) : (tx0 + TX == p.g.nx ? 0 : tx0 + TX);
+            const S* src = buf + (long long)slot * N + ((long long)zs * p.g.ny + ys) * p.g.nx + xe;
+            unsigned char* e = st + MB + ((r * Q + i) * 2 + (cx > 0 ? 0 : 1)) * 16;
+            mbar_expect_tx(bar, 16u);
+            bulk_load_16(e, src, bar);
+          }
+        }
+      }
+    }
+    mbar_arrive(bar);
+    s_issued[s] += 1;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NST; ++k) {
+      const int tile = blockIdx.x + k * gridDim.x;
+      if (tile < ntiles) produce(tile, k);
+    }
+  }
+
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    const int s = k % NST;
+    const unsigned parity = (unsigned)((k / NST) & 1);
+    // bounded wait for the stage (2^22 polls); on time-out record an error and leave
+    if (!mbar_try_wait(&bars[s], parity)) {
+      unsigned it = 0;
+      while (!mbar_try_wait(&bars[s], parity)) {
+        if (++it > (1u << 22)) {
+          atomicExch(&s_abort, 1);
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) {
+      if (threadIdx.x == 0) {
+        if (p.err) atomicExch(p.err, 1);
+        // let the copies already issued land before the block's shared memory is released
+        for (int s2 = 0; s2 < NST; ++s2) {
+          if (s_issued[s2] == 0) continue;
+          const unsigned last = (unsigned)((s_issued[s2] - 1) & 1);
+          for (unsigned it = 0; it < (1u << 20) && !mbar_try_wait(&bars[s2], last); ++it) {
+          }
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    int x, y, z;
+    {
+      const int tx = tile % p.t.ntx;
+      const int r = tile / p.t.ntx;
+      const int ty = r % p.t.nty;
+      z = r / p.t.nty;
+      x = tx * TX + lx;
+      y = ty * TY + ly;
+    }
+    const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
+    Nbr nbr;
+    nbr.init(p.g, x, y, z);
+    const unsigned char* st = stages + (long long)s * SB;
+    T f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = lat_cx(i), cz = lat_cz(i);
+      if (nbr.from_ghost(cz)) {
+        f[i] = cst<T>(p).ghost[i];
+      } else if (MODE != MODE_AA_ODD) {
+        f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + ly * BB) + i * TX + lx);
+      } else {
+        const S* row = reinterpret_cast<const S*>(st + (ly * Q + i) * RB);
+        const int xs = lx - cx;
+        if (xs < 0) {
+          f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + MB + ((ly * Q + i) * 2 + 0) * 16) + (EP - 1));
+        } else if (xs >= TX) {
+          f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + MB + ((ly * Q + i) * 2 + 1) * 16));
+        } else {
+          f[i] = Store<S>::ld(row + xs);
+        }
+      }
+    }
+    __syncthreads();  // stage s fully read: thread 0 may refill it
+    if (threadIdx.x == 0) {
+      const int next = tile + NST * gridDim.x;
+      if (next < ntiles) produce(next, s);
+    }
+    int owner = -1;
+    bool solid_cell = false;
+    double ft[6] = {0, 0, 0, 0, 0, 0};
+    psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
+    psm_store<S, Q, MODE>(buf, dst, N, nbr, cell, f);
+    warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
+  }
+  if (nb == 0) return;
+  block_ft_finish(s_ft, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -636,6 +922,44 @@ cudaError_t launch_step_t(const StepParams& p, cudaStream_t st) {
 }
 
 template <class S, int Q, int MODE, int TRT>
+cudaError_t launch_step_tma_t(const StepParams& p, const TmaMaps& m, cudaStream_t st) {
+  using L = TmaLayout<S, Q, MODE>;
+  const int smem = L::smem_bytes(p.t.tx, p.t.ty);
+  static int configured = -1;  // largest dynamic shared memory set so far
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, Q, MODE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<S, Q, MODE, TRT>, PSM_THREADS, smem);
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = (long long)sms * per_sm;
+  if (blocks > 8ll * sms) blocks = 8ll * sms;
+  if (p.t.ntiles < blocks) blocks = p.t.ntiles;
+  k_step_tma<S, Q, MODE, TRT><<<(int)blocks, PSM_THREADS, smem, st>>>(p, m);
+  return cudaGetLastError();
+}
+
+template <class S, int Q>
+cudaError_t launch_step_tma_q(int mode, int trt, const StepParams& p, const TmaMaps& m, cudaStream_t st) {
+  if (mode == MODE_TG)
+    return trt ? launch_step_tma_t<S, Q, MODE_TG, 1>(p, m, st) : launch_step_tma_t<S, Q, MODE_TG, 0>(p, m, st);
+  if (mode == MODE_AA_EVEN)
+    return trt ? launch_step_tma_t<S, Q, MODE_AA_EVEN, 1>(p, m, st) : launch_step_tma_t<S, Q, MODE_AA_EVEN, 0>(p, m, st);
+  return trt ? launch_step_tma_t<S, Q, MODE_AA_ODD, 1>(p, m, st) : launch_step_tma_t<S, Q, MODE_AA_ODD, 0>(p, m, st);
+}
+
+template <class S, int Q>
+int tma_smem_q(int mode, int tx, int ty) {
+  if (mode == MODE_TG) return TmaLayout<S, Q, MODE_TG>::smem_bytes(tx, ty);
+  if (mode == MODE_AA_EVEN) return TmaLayout<S, Q, MODE_AA_EVEN>::smem_bytes(tx, ty);
+  return TmaLayout<S, Q, MODE_AA_ODD>::smem_bytes(tx, ty);
+}
+
+template <class S, int Q, int MODE, int TRT>
 int step_blocks_t() {
   static int blocks = persistent_blocks(k_step<S, Q, MODE, TRT>, 1ll << 40);
   return blocks;
@@ -670,6 +994,13 @@ inline int io_grid(const IoParams& p) {
   namespace psm {                                                                                       \
   cudaError_t launch_step_##NAME(int Q, int mode, int trt, const StepParams& p, cudaStream_t st) {      \
     return Q == 19 ? launch_step_q<S, 19>(mode, trt, p, st) : launch_step_q<S, 27>(mode, trt, p, st);   \
+  }                                                                                                     \
+  cudaError_t launch_step_tma_##NAME(int Q, int mode, int trt, const StepParams& p, const TmaMaps& m,   \
+                                     cudaStream_t st) {                                                 \
+    return Q == 19 ? launch_step_tma_q<S, 19>(mode, trt, p, m, st) : launch_step_tma_q<S, 27>(mode, trt, p, m, st); \
+  }                                                                                                     \
+  int tma_smem_bytes_##NAME(int Q, int mode, int tx, int ty) {                                          \
+    return Q == 19 ? tma_smem_q<S, 19>(mode, tx, ty) : tma_smem_q<S, 27>(mode, tx, ty);                 \
   }                                                                                                     \
   int step_grid_blocks_##NAME(int Q, int mode, int trt) {                                               \
     return Q == 19 ? step_blocks_q<S, 19>(mode, trt) : step_blocks_q<S, 27>(mode, trt);                 \

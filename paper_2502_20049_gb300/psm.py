@@ -103,6 +103,8 @@ def lib() -> ctypes.CDLL:
                 "psm_series_capacity": (i, [H, P(i64)]),
                 "psm_mass": (i, [H, P(d)]),
                 "psm_synchronize": (i, [H]),
+                "psm_set_kernel_variant": (i, [H, i]),
+                "psm_kernel_variant": (i, [H, P(i)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -374,6 +376,18 @@ class Solver:
 
     def synchronize(self):
         check(lib().psm_synchronize(self._h))
+
+    KERNELS = {"auto": 0, "plain": 1, "tma": 2}
+
+    @property
+    def kernel_variant(self) -> str:
+        """'plain' or 'tma': the step kernel psm_step uses."""
+        v = ctypes.c_int()
+        check(lib().psm_kernel_variant(self._h, ctypes.byref(v)))
+        return {1: "plain", 2: "tma"}[v.value]
+
+    def set_kernel_variant(self, name: str):
+        check(lib().psm_set_kernel_variant(self._h, self.KERNELS[name]))
 
     def bytes_per_cell_update(self) -> int:
         """Algorithmic bytes per cell update: one read and one write of every PDF."""

@@ -161,3 +161,46 @@ def test_empty_domain_and_single_cell():
     g, o = run_gpu(one), run_oracle(one)
     assert np.abs(g["f"] - o["f"][perm_lib_to_oracle(27)]).max() <= 1e-14
     assert ft_err(g, o) <= 1e-12
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("streaming", ["aa", "twogrid"])
+def test_tma_staged_equals_plain_bitwise(storage, streaming):
+    """The TMA-staged step kernel and the plain-load kernel compute the same bits
+    (64^3: TMA tiles of 64 x 4 cells; 41 steps end on an odd AA step)."""
+    from paper_2502_20049_gb300 import psm
+
+    case = c2_reduced(storage, streaming, steps=41)
+    a = psm.Solver.from_case(case)
+    b = psm.Solver.from_case(case)
+    b.set_kernel_variant("plain")
+    assert a.kernel_variant == "tma" and b.kernel_variant == "plain"
+    a.step(41)
+    b.step(41)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.force_torque(0), b.force_torque(0))
+
+
+@pytest.mark.parametrize("streaming", ["aa", "twogrid"])
+def test_tma_full_rows_periodic_fp32(streaming):
+    """TMA tiles of one full 256-cell row (the benchmark's tiling), periodic z,
+    a translating + rotating body, against the oracle."""
+    from paper_2502_20049_gb300 import psm
+
+    case = W.Case("rows256", 256, 12, 10, Q=19, storage="fp32", streaming=streaming, fluid="trt", tau=0.6, bc_z=0,
+                  u_in=(0.02, 0.0, 0.01), steps=25,
+                  bodies=[W.BodyCase(W.ELLIPSOID, (9.0, 3.0, 2.5), 2, (20.0, 6.0, 5.0), omega=(0.0, 0.02, 0.05),
+                                     v=(0.05, 0.0, 0.0))])
+    g, o = run_gpu(case), run_oracle(case)
+    assert g["solver"].kernel_variant == "tma"
+    assert u_err(g, o, case) <= 2e-5
+    assert ft_err(g, o) <= 1e-4
+
+
+def test_ragged_shapes_use_plain_kernel():
+    from paper_2502_20049_gb300 import psm
+
+    s = psm.Solver(psm.SolverConfig(37, 23, 19, storage="fp32"))
+    assert s.kernel_variant == "plain"
+    with pytest.raises(psm.PSMError):
+        s.set_kernel_variant("tma")
