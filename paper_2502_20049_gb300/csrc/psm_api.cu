@@ -135,6 +135,22 @@ cudaError_t launch_step(int storage, int Q, int mode, const StepParams& p, cudaS
     default: return launch_step_bf16(Q, mode, p.trt, p, st);
   }
 }
+cudaError_t launch_step_tma(int storage, int Q, int mode, const StepParams& p, const TmaMaps& m, cudaStream_t st) {
+  switch (storage) {
+    case PSM_FP64: return launch_step_tma_fp64(Q, mode, p.trt, p, m, st);
+    case PSM_FP32: return launch_step_tma_fp32(Q, mode, p.trt, p, m, st);
+    case PSM_FP16_SHIFTED: return launch_step_tma_fp16(Q, mode, p.trt, p, m, st);
+    default: return launch_step_tma_bf16(Q, mode, p.trt, p, m, st);
+  }
+}
+int tma_smem_bytes(int storage, int Q, int mode, int tx, int ty) {
+  switch (storage) {
+    case PSM_FP64: return tma_smem_bytes_fp64(Q, mode, tx, ty);
+    case PSM_FP32: return tma_smem_bytes_fp32(Q, mode, tx, ty);
+    case PSM_FP16_SHIFTED: return tma_smem_bytes_fp16(Q, mode, tx, ty);
+    default: return tma_smem_bytes_bf16(Q, mode, tx, ty);
+  }
+}
 int step_grid_blocks(int storage, int Q, int mode, int trt) {
   switch (storage) {
     case PSM_FP64: return step_grid_blocks_fp64(Q, mode, trt);
