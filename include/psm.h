@@ -250,6 +250,41 @@ int psm_synchronize(psm_handle h);
  * nx % TX == 0, 256 % nx == 0 when nx < 256, TX >= 32, ny % (256 / TX) == 0,
  * nx * sizeof(PDF) a multiple of 16 bytes.  Both variants compute the same
  * results. */
+/* ------------------------------------------------------------------------ */
+/* Differentiation (not in the paper): discrete adjoint of the step          */
+/* ------------------------------------------------------------------------ */
+
+/* Per-cell additive perturbation delta of the solid fraction: every step uses
+ * B(eps_n(x) + delta(x)) (Eq. 5 / 6, not clamped).  delta: ncell floats
+ * [nz][ny][nx], host or device, copied; NULL removes it. */
+int psm_set_eps_delta(psm_handle h, const float* delta);
+
+/* Start recording the trajectory for psm_backward at the current step n0:
+ * the state is checkpointed now and before every K-th later step (device
+ * memory, stream-ordered allocation).  K = 0 stops recording and frees the
+ * checkpoints.  With AA streaming, n0 and K must be even.  flags:
+ * PSM_RECORD_INIT_FROM_INFLOW declares that the state at n0 is
+ * f^eq(rho0, u_in) (psm_create or psm_init_equilibrium(rho0, u_in)), so that
+ * the gradient with respect to u_in includes the initial state. */
+#define PSM_RECORD_INIT_FROM_INFLOW 1
+int psm_record(psm_handle h, int K, int flags);
+
+/* Gradient of J = sum_{n, body, k} w[n][body][k] * FT[n][body][k] over the
+ * recorded steps n0 <= n < step (FT as psm_force_torque returns it) by the
+ * discrete adjoint: segments between checkpoints are recomputed (two-grid
+ * step kernel) and swept backwards with the adjoint step kernel.
+ *   dJ_dFT:     w, (step - n0) * nbodies * 6 doubles; NULL = mean torque
+ *               about z on body 0, w[n][0][5] = 1 / (step - n0);
+ *   grad_eps:   dJ/d delta per cell, ncell doubles (NULL: not returned);
+ *   grad_omega: dJ/d omega per body (the geometry sequence is held fixed:
+ *               omega enters through u_s only), nbodies * 3 doubles (or NULL);
+ *   grad_uin:   dJ/d u_in (ghost planes, plus the initial state if recorded
+ *               with PSM_RECORD_INIT_FROM_INFLOW), 3 doubles (or NULL).
+ * Adjoint arithmetic is FP32 (FP64 for PSM_FP64 storage); sums are FP64.
+ * Synchronises; the handle keeps its state and step counter.
+ * PSM_ERR_STATE without a recorded forward. */
+int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* grad_omega, double* grad_uin);
+
 #define PSM_KERNEL_AUTO 0
 #define PSM_KERNEL_PLAIN 1
 #define PSM_KERNEL_TMA 2

@@ -1,0 +1,376 @@
+// Discrete adjoint (reverse-time) PSM step.  Not in the paper: it is the exact
+// transpose of the forward step of psm_kernels.cuh, for gradients of a linear
+// functional J of the force/torque series with respect to a per-cell
+// perturbation delta of the solid fraction, the angular velocities and the
+// inflow velocity.
+//
+// Forward step n (pre-collision state f^n, natural layout):
+//   f^{n+1} = S(C_n(f^n)),   C_n = per-cell Eq. 4 with B = B(eps_n + delta),
+//   S = streaming (pull from x - c_i; ghost value where x - c_i is outside).
+// Adjoint step n, per cell y, with mu_i(y) = lambda^{n+1}_i(y + c_i) (zero where
+// y + c_i is outside: the population left the domain):
+//   lambda^n(y) = (dC_n/df)^T mu(y) + dJ_n/df(y),
+//   dJ/d delta(y) += [mu . dC_n/dB + dJ_n/dB] B'(eps + delta),
+//   dJ/d omega_b  += (x_c - R_n) x (dJ/du_s) over the cells owned by body b,
+//   dJ/d u_in     += lambda^n_i(y) d g_i/d u_in for populations taken from a
+//                    ghost plane (g_i = f^eq_i(rho0, u_in)).
+// The eps sequence is the forward's (frozen geometry: eps is piecewise
+// constant in omega).  All arithmetic is in the compute precision T (FP32 for
+// FP32/FP16/BF16 storage, FP64 for FP64); the scalar gradients are summed in
+// FP64 in a fixed order.
+#pragma once
+
+#include "psm_kernels.cuh"
+
+namespace psm {
+
+struct AdjParams {
+  Grid3 g;
+  Tiling t;
+  const void* f;        // f^n, natural layout, storage S, shifted
+  const void* lam_in;   // lambda^{n+1}, [Q][ncell] in T
+  void* lam_out;        // lambda^n
+  double* grad;         // [ncell]: += dJ/d delta (FP64 accumulator)
+  int trt, solid, weighting, nbodies;
+  DevBody body[PSM_MAX_BODIES];
+  const float* delta;
+  const double* w;      // [nbodies][6] weights of this step's force/torque in J (null: none)
+  double dghost[27][3]; // d g_i / d u_in
+  double* partials;
+  unsigned int* ticket;
+  double* acc_out;      // [nbodies * 3 + 3]: dJ/d omega per body, dJ/d u_in
+  ConstT<float> cf;
+  ConstT<double> cd;
+};
+
+#define PSM_DECLARE_ADJOINT(NAME)                                                              \
+  cudaError_t launch_adjoint_##NAME(int Q, int trt, const AdjParams& p, cudaStream_t st);      \
+  cudaError_t launch_adjoint_init_##NAME(int Q, const AdjParams& p, int blocks, cudaStream_t st);
+PSM_DECLARE_ADJOINT(fp64)
+PSM_DECLARE_ADJOINT(fp32)
+PSM_DECLARE_ADJOINT(fp16)
+PSM_DECLARE_ADJOINT(bf16)
+
+template <class T>
+__device__ __forceinline__ const ConstT<T>& acst(const AdjParams& p) {
+  if constexpr (sizeof(T) == 4) return p.cf;
+  else return p.cd;
+}
+
+// phi_i(v) = d f^eq_i / d rho = w_i (1 + 3 c.v + 4.5 (c.v)^2 - 1.5 v.v)
+template <int Q, class T>
+__device__ __forceinline__ T phi(int i, T cv, T vv) {
+  return T(lat_w<Q>(i)) * (T(1) + T(3) * cv + T(4.5) * cv * cv - T(1.5) * vv);
+}
+
+template <class S, int Q, int TRT>
+__global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constant__ AdjParams p) {
+  using T = typename Store<S>::T;
+  constexpr int NW = PSM_THREADS / 32;
+  constexpr int NC = PSM_MAX_BODIES * 3 + 3;
+  __shared__ double s_acc[NW][NC];
+  const int nb = p.nbodies;
+  const int ncomp = nb * 3 + 3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = lane; k < NC; k += 32) s_acc[warp][k] = 0.0;
+  const S* __restrict__ fb = static_cast<const S*>(p.f);
+  const T* __restrict__ lin = static_cast<const T*>(p.lam_in);
+  T* __restrict__ lout = static_cast<T*>(p.lam_out);
+  double* __restrict__ grad = p.grad;
+  const long long N = p.g.ncell;
+  const ConstT<T>& C = acst<T>(p);
+  const T om_a = C.om_a, om_b = C.om_b, inv_tau = C.inv_tau;
+  const int ntiles = (int)p.t.ntiles;
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int x, y, z;
+    tile_coords(p.t, tile, x, y, z);
+    const bool active = x < p.g.nx && y < p.g.ny;
+    double aw0 = 0, aw1 = 0, aw2 = 0, au0 = 0, au1 = 0, au2 = 0;
+    bool has_w = false, has_u = false;
+    int owner = -1;
+    if (active) {
+      const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
+      Nbr nbr;
+      nbr.init(p.g, x, y, z);
+      T f[Q], mu[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+        f[i] = nbr.from_ghost(cz) ? C.ghost[i] : Store<S>::ld(fb + (long long)i * N + cell);
+        mu[i] = nbr.to_ghost(cz) ? T(0) : lin[(long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz))];
+      }
+      // ---- forward recomputation (same arithmetic as psm_collide) ----
+      const float epsf = cell_eps(p.body, nb, x, y, z, owner);
+      T e = T(epsf);
+      if (p.delta) e += T(p.delta[cell]);
+      T Bw = e, Bp = T(1);
+      if (p.weighting == PSM_B_TAU_WEIGHTED) {
+        const T t = C.tmh;
+        const T den = (T(1) - e) + t;
+        Bw = e * t / den;
+        Bp = t * (T(1) + t) / (den * den);
+      }
+      T drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        drho += f[i];
+        if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
+        if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
+        if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
+      }
+      const T rho = C.rho0 + drho;
+      const T inv_rho = T(1) / rho;
+      const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+      const T uu = ux * ux + uy * uy + uz * uz;
+      T usx = 0, usy = 0, usz = 0;
+      double Rx = 0, Ry = 0, Rz = 0;
+      if (owner >= 0) {
+        const DevBody& b = p.body[owner];
+        Rx = (double)x + 0.5 - b.R[0];
+        Ry = (double)y + 0.5 - b.R[1];
+        Rz = (double)z + 0.5 - b.R[2];
+        T rx, ry, rz, wx, wy, wz, vx, vy, vz;
+        if constexpr (sizeof(T) == 4) {
+          rx = (T(x) + T(0.5)) - b.Rf[0];
+          ry = (T(y) + T(0.5)) - b.Rf[1];
+          rz = (T(z) + T(0.5)) - b.Rf[2];
+          wx = b.omegaf[0], wy = b.omegaf[1], wz = b.omegaf[2];
+          vx = b.vf[0], vy = b.vf[1], vz = b.vf[2];
+        } else {
+          rx = Rx, ry = Ry, rz = Rz;
+          wx = b.omega[0], wy = b.omega[1], wz = b.omega[2];
+          vx = b.v[0], vy = b.v[1], vz = b.v[2];
+        }
+        usx = wy * rz - wz * ry + vx;
+        usy = wz * rx - wx * rz + vy;
+        usz = wx * ry - wy * rx + vz;
+      }
+      const T usus = usx * usx + usy * usy + usz * usz;
+      const T omB = T(1) - Bw;
+      // ---- adjoint of the force/torque terms: s = B sum_i Omega^S_i c_i ----
+      T sbx = 0, sby = 0, sbz = 0;
+      if (owner >= 0 && Bw > T(0) && p.w) {
+        const double* wv = p.w + owner * 6;
+        // J_n = sum_b w_F . F_b + w_T . T_b with F_b = -sum s, T_b = -sum r x s
+        sbx = T(-(wv[0] + (wv[4] * Rz - wv[5] * Ry)));
+        sby = T(-(wv[1] + (wv[5] * Rx - wv[3] * Rz)));
+        sbz = T(-(wv[2] + (wv[3] * Ry - wv[4] * Rx)));
+      }
+      // ---- reverse sweep over the rest population and the opposite pairs ----
+      T Bbar = 0, rhob = 0;
+      T ubx = 0, uby = 0, ubz = 0, usbx = 0, usby = 0, usbz = 0;
+      {
+        const T E0 = feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
+        const T G0 = feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
+        const T n0 = f[0] - E0, m0 = f[0] - G0;
+        const T of0 = -(om_a + om_b) * n0;
+        T os0;
+        if (p.solid == PSM_SC1) os0 = n0 - m0;
+        else if (p.solid == PSM_SC2) os0 = -m0 * inv_tau;
+        else os0 = T(0);
+        const T osb = Bw * mu[0], ofb = omB * mu[0];
+        Bbar += mu[0] * (os0 - of0);
+        T nb0 = -(om_a + om_b) * ofb, mb0;
+        if (p.solid == PSM_SC1) {
+          nb0 += osb;
+          mb0 = -osb;
+        } else if (p.solid == PSM_SC2) {
+          mb0 = -osb * inv_tau;
+        } else {
+          mb0 = T(0);
+        }
+        f[0] = mu[0] + nb0 + mb0;
+        const T Eb = -nb0, Gb = -mb0;
+        rhob += Eb * phi<Q, T>(0, T(0), uu) + Gb * phi<Q, T>(0, T(0), usus);
+        const T ke = T(-3) * rho * T(lat_w<Q>(0)) * Eb, kg = T(-3) * rho * T(lat_w<Q>(0)) * Gb;
+        ubx += ke * ux;
+        uby += ke * uy;
+        ubz += ke * uz;
+        usbx += kg * usx;
+        usby += kg * usy;
+        usbz += kg * usz;
+      }
+#pragma unroll
+      for (int i = 1; i < Q; i += 2) {
+        const int j = i + 1;
+        const T cx = T(lat_cx(i)), cy = T(lat_cy(i)), cz = T(lat_cz(i));
+        const T cu = cx * ux + cy * uy + cz * uz;
+        const T cs = cx * usx + cy * usy + cz * usz;
+        const T Ei = feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
+        const T Ej = feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
+        const T Gi = feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
+        const T Gj = feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
+        const T ni = f[i] - Ei, nj = f[j] - Ej, mi = f[i] - Gi, mj = f[j] - Gj;
+        const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
+        const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);
+        T osi, osj;
+        if (p.solid == PSM_SC1) {
+          osi = nj - mi;
+          osj = ni - mj;
+        } else if (p.solid == PSM_SC2) {
+          osi = -mi * inv_tau;
+          osj = -mj * inv_tau;
+        } else {
+          osi = mj - mi;
+          osj = mi - mj;
+        }
+        const T sci = sbx * cx + sby * cy + sbz * cz;  // sbar . c_i; c_j = -c_i
+        const T osbi = Bw * (mu[i] + sci), osbj = Bw * (mu[j] - sci);
+        const T ofbi = omB * mu[i], ofbj = omB * mu[j];
+        Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj) + sci * (osi - osj);
+        T nbi = TRT ? (-om_a * ofbi - om_b * ofbj) : (-om_a * ofbi);
+        T nbj = TRT ? (-om_a * ofbj - om_b * ofbi) : (-om_a * ofbj);
+        T mbi, mbj;
+        if (p.solid == PSM_SC1) {
+          nbi += osbj;
+          nbj += osbi;
+          mbi = -osbi;
+          mbj = -osbj;
+        } else if (p.solid == PSM_SC2) {
+          mbi = -osbi * inv_tau;
+          mbj = -osbj * inv_tau;
+        } else {
+          mbi = osbj - osbi;
+          mbj = osbi - osbj;
+        }
+        f[i] = mu[i] + nbi + mbi;
+        f[j] = mu[j] + nbj + mbj;
+        const T Ebi = -nbi, Ebj = -nbj, Gbi = -mbi, Gbj = -mbj;
+        rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + Gbi * phi<Q, T>(i, cs, usus) +
+                Gbj * phi<Q, T>(j, -cs, usus);
+        // d f^eq_i / d v = rho w_i (3 c_i + 9 (c_i.v) c_i - 3 v), and c_j = -c_i
+        const T rw = rho * T(lat_w<Q>(i));
+        const T ae = rw * (T(3) * (Ebi - Ebj) + T(9) * cu * (Ebi + Ebj)), be = T(-3) * rw * (Ebi + Ebj);
+        const T ag = rw * (T(3) * (Gbi - Gbj) + T(9) * cs * (Gbi + Gbj)), bg = T(-3) * rw * (Gbi + Gbj);
+        ubx += ae * cx + be * ux;
+        uby += ae * cy + be * uy;
+        ubz += ae * cz + be * uz;
+        usbx += ag * cx + bg * usx;
+        usby += ag * cy + bg * usy;
+        usbz += ag * cz + bg * usz;
+      }
+      // u = j / rho
+      const T jbx = ubx * inv_rho, jby = uby * inv_rho, jbz = ubz * inv_rho;
+      rhob -= (ubx * ux + uby * uy + ubz * uz) * inv_rho;
+      // ---- lambda^n = fbar + drho/df rhobar + dj/df . jbar ----
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const T l = f[i] + rhob + T(lat_cx(i)) * jbx + T(lat_cy(i)) * jby + T(lat_cz(i)) * jbz;
+        lout[(long long)i * N + cell] = l;
+        if (nbr.from_ghost(lat_cz(i))) {
+          // the population is the ghost value g_i(u_in)
+          au0 += (double)l * p.dghost[i][0];
+          au1 += (double)l * p.dghost[i][1];
+          au2 += (double)l * p.dghost[i][2];
+          has_u = true;
+        }
+      }
+      grad[cell] += (double)(Bbar * Bp);
+      if (owner >= 0) {
+        // u_s = omega x r + v  =>  d/d omega = r x usbar
+        const double a = (double)usbx, b = (double)usby, c = (double)usbz;
+        aw0 = Ry * c - Rz * b;
+        aw1 = Rz * a - Rx * c;
+        aw2 = Rx * b - Ry * a;
+        has_w = true;
+      }
+    }
+    // ---- per-warp FP64 sums in a fixed order ----
+    if (__any_sync(0xffffffffu, has_w)) {
+      for (int bi = 0; bi < nb; ++bi) {
+        const bool mine = has_w && owner == bi;
+        if (!__any_sync(0xffffffffu, mine)) continue;
+        const double v0 = warp_sum(mine ? aw0 : 0.0), v1 = warp_sum(mine ? aw1 : 0.0), v2 = warp_sum(mine ? aw2 : 0.0);
+        if (lane == 0) {
+          s_acc[warp][bi * 3 + 0] += v0;
+          s_acc[warp][bi * 3 + 1] += v1;
+          s_acc[warp][bi * 3 + 2] += v2;
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, has_u)) {
+      const double v0 = warp_sum(au0), v1 = warp_sum(au1), v2 = warp_sum(au2);
+      if (lane == 0) {
+        s_acc[warp][nb * 3 + 0] += v0;
+        s_acc[warp][nb * 3 + 1] += v1;
+        s_acc[warp][nb * 3 + 2] += v2;
+      }
+    }
+  }
+  __syncthreads();
+  __shared__ double blk[NC];
+  if ((int)threadIdx.x < ncomp) {
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w) s += s_acc[w][threadIdx.x];
+    blk[threadIdx.x] = s;
+  }
+  __syncthreads();
+  grid_reduce(blk, ncomp, p.partials, p.ticket, p.acc_out);
+}
+
+// Initial-state term of dJ/d u_in when f^{n0} = f^eq(rho0, u_in) everywhere:
+// sum over cells and populations not taken from a ghost plane of
+// lambda^{n0}_i d f^eq_i(rho0, u_in) / d u_in (= d g_i / d u_in).
+template <int Q, class T>
+__global__ void __launch_bounds__(PSM_THREADS) k_adjoint_init(const __grid_constant__ AdjParams p) {
+  const T* lam = static_cast<const T*>(p.lam_in);
+  const long long N = p.g.ncell;
+  double a[3] = {0, 0, 0};
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int z = (int)(idx / ((long long)p.g.nx * p.g.ny));
+    const bool zlo = p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && z == 0;
+    const bool zhi = p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && z == p.g.nz - 1;
+    for (int i = 0; i < Q; ++i) {
+      const int cz = lat_cz(i);
+      if ((cz > 0 && zlo) || (cz < 0 && zhi)) continue;
+      const double l = (double)lam[(long long)i * N + idx];
+      for (int k = 0; k < 3; ++k) a[k] += l * p.dghost[i][k];
+    }
+  }
+  __shared__ double s_w[PSM_THREADS / 32][3];
+  __shared__ double blk[3];
+  for (int k = 0; k < 3; ++k) {
+    const double v = warp_sum(a[k]);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < PSM_THREADS / 32; ++w) s += s_w[w][threadIdx.x];
+    blk[threadIdx.x] = s;
+  }
+  __syncthreads();
+  grid_reduce(blk, 3, p.partials, p.ticket, p.acc_out);
+}
+
+template <class S, int Q>
+cudaError_t launch_adjoint_q(int trt, const AdjParams& p, cudaStream_t st) {
+  static int blocks_bgk = persistent_blocks(k_adjoint<S, Q, 0>, 1ll << 40);
+  static int blocks_trt = persistent_blocks(k_adjoint<S, Q, 1>, 1ll << 40);
+  const int b = trt ? blocks_trt : blocks_bgk;
+  const int grid = (int)(p.t.ntiles < b ? p.t.ntiles : b);
+  if (trt) k_adjoint<S, Q, 1><<<grid, PSM_THREADS, 0, st>>>(p);
+  else k_adjoint<S, Q, 0><<<grid, PSM_THREADS, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <class S, int Q>
+cudaError_t launch_adjoint_init_q(const AdjParams& p, int blocks, cudaStream_t st) {
+  using T = typename Store<S>::T;
+  k_adjoint_init<Q, T><<<blocks, PSM_THREADS, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace psm
+
+#define PSM_DEFINE_ADJOINT(NAME, S)                                                                      \
+  namespace psm {                                                                                        \
+  cudaError_t launch_adjoint_##NAME(int Q, int trt, const AdjParams& p, cudaStream_t st) {               \
+    return Q == 19 ? launch_adjoint_q<S, 19>(trt, p, st) : launch_adjoint_q<S, 27>(trt, p, st);          \
+  }                                                                                                      \
+  cudaError_t launch_adjoint_init_##NAME(int Q, const AdjParams& p, int blocks, cudaStream_t st) {       \
+    return Q == 19 ? launch_adjoint_init_q<S, 19>(p, blocks, st) : launch_adjoint_init_q<S, 27>(p, blocks, st); \
+  }                                                                                                      \
+  }

@@ -9,6 +9,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "psm_adjoint.cuh"
 #include "psm_kernels.cuh"
 
 namespace {
@@ -109,6 +110,12 @@ struct psm_solver {
   int variant = PSM_KERNEL_AUTO;
   psm::Tiling tma_tiling;
   psm::TmaMaps maps[2];
+  // trajectory recording for psm_backward: checkpoints every rec_K steps from rec_n0
+  bool recording = false;
+  int rec_K = 0;
+  int rec_flags = 0;
+  int64_t rec_n0 = 0;
+  std::vector<void*> ckpt;
 };
 
 namespace psm {
@@ -397,6 +404,46 @@ int check_err(psm_solver* h) {
   return PSM_OK;
 }
 
+size_t state_bytes(const psm_solver* h) {
+  return (size_t)h->Q * (size_t)h->g.ncell * storage_bytes(h->lat.storage);
+}
+
+// copy the current natural-layout state into a new checkpoint (stream ordered)
+int take_checkpoint(psm_solver* h) {
+  void* c = nullptr;
+  PSM_CUDA(cudaMallocAsync(&c, state_bytes(h), h->stream), "checkpoint allocation");
+  const void* src = h->lat.streaming == PSM_STREAM_TWO_GRID ? h->buf[h->cur] : h->buf[0];
+  cudaError_t e = cudaMemcpyAsync(c, src, state_bytes(h), cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(c, h->stream);
+    return cuda_fail(e, "checkpoint copy");
+  }
+  h->ckpt.push_back(c);
+  return PSM_OK;
+}
+
+void drop_checkpoints(psm_solver* h) {
+  for (void* c : h->ckpt) cudaFreeAsync(c, h->stream);
+  h->ckpt.clear();
+}
+
+cudaError_t launch_adjoint(int storage, int Q, int trt, const psm::AdjParams& p, cudaStream_t st) {
+  switch (storage) {
+    case PSM_FP64: return psm::launch_adjoint_fp64(Q, trt, p, st);
+    case PSM_FP32: return psm::launch_adjoint_fp32(Q, trt, p, st);
+    case PSM_FP16_SHIFTED: return psm::launch_adjoint_fp16(Q, trt, p, st);
+    default: return psm::launch_adjoint_bf16(Q, trt, p, st);
+  }
+}
+cudaError_t launch_adjoint_init(int storage, int Q, const psm::AdjParams& p, int blocks, cudaStream_t st) {
+  switch (storage) {
+    case PSM_FP64: return psm::launch_adjoint_init_fp64(Q, p, blocks, st);
+    case PSM_FP32: return psm::launch_adjoint_init_fp32(Q, p, blocks, st);
+    case PSM_FP16_SHIFTED: return psm::launch_adjoint_init_fp16(Q, p, blocks, st);
+    default: return psm::launch_adjoint_init_bf16(Q, p, blocks, st);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -507,6 +554,7 @@ int psm_destroy(psm_handle h) {
   cudaFree(h->d_sum);
   cudaFree(h->d_delta);
   cudaFree(h->d_err);
+  for (void* c : h->ckpt) cudaFree(c);
   delete h;
   return PSM_OK;
 }
@@ -697,6 +745,11 @@ int psm_step(psm_handle h, int n) {
   p.ticket = h->d_ticket;
   p.err = h->d_err;
   for (int k = 0; k < n; ++k) {
+    if (h->recording && (h->step - h->rec_n0) % h->rec_K == 0 &&
+        (int64_t)h->ckpt.size() == (h->step - h->rec_n0) / h->rec_K) {
+      const int rc = take_checkpoint(h);
+      if (rc != PSM_OK) return rc;
+    }
     for (int b = 0; b < h->nbodies; ++b) p.body[b] = dev_body(h, b, h->step);
     p.ft_out = h->d_series + (size_t)(h->step % h->cap) * PSM_MAX_BODIES * 6;
     int mode, src;
@@ -717,6 +770,188 @@ int psm_step(psm_handle h, int n) {
     if (h->lat.streaming == PSM_STREAM_TWO_GRID) h->cur ^= 1;
     h->step++;
   }
+  return PSM_OK;
+}
+
+int psm_set_eps_delta(psm_handle h, const float* delta) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_set_eps_delta: NULL handle");
+  PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  if (!delta) {
+    cudaFree(h->d_delta);
+    h->d_delta = nullptr;
+    return PSM_OK;
+  }
+  if (!h->d_delta) PSM_CUDA(cudaMalloc(&h->d_delta, sizeof(float) * (size_t)h->g.ncell), "delta allocation");
+  PSM_CUDA(cudaMemcpy(h->d_delta, delta, sizeof(float) * (size_t)h->g.ncell, cudaMemcpyDefault), "delta upload");
+  return PSM_OK;
+}
+
+int psm_record(psm_handle h, int K, int flags) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_record: NULL handle");
+  drop_checkpoints(h);
+  h->recording = false;
+  if (K == 0) return PSM_OK;
+  if (K < 1) return fail(PSM_ERR_ARG, "checkpoint interval K must be >= 1 (0 stops recording)");
+  if (h->lat.streaming == PSM_STREAM_AA && ((K & 1) || (h->step & 1)))
+    return fail(PSM_ERR_ARG, "AA streaming: record from an even step with an even K (checkpoints need the "
+                             "natural layout)");
+  if (flags & ~PSM_RECORD_INIT_FROM_INFLOW) return fail(PSM_ERR_ARG, "unknown record flags");
+  h->rec_K = K;
+  h->rec_flags = flags;
+  h->rec_n0 = h->step;
+  h->recording = true;
+  return take_checkpoint(h);
+}
+
+int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* grad_omega, double* grad_uin) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_backward: NULL handle");
+  if (!h->recording) return fail(PSM_ERR_STATE, "psm_backward needs a forward run recorded with psm_record");
+  const int64_t N = h->step - h->rec_n0;
+  if (N < 1) return fail(PSM_ERR_STATE, "no step recorded since psm_record");
+  const int K = h->rec_K;
+  const int64_t M = (N + K - 1) / K;
+  if ((int64_t)h->ckpt.size() < M) return fail(PSM_ERR_STATE, "checkpoints missing");
+  const int nb = h->nbodies;
+  const int ncomp = nb * 3 + 3;
+  const size_t ncell = (size_t)h->g.ncell;
+  const size_t tb = h->lat.storage == PSM_FP64 ? 8 : 4;
+  const size_t sbytes = state_bytes(h);
+  cudaStream_t st = h->stream;
+  // weights of J on the force/torque series
+  std::vector<double> w((size_t)N * nb * 6, 0.0);
+  if (dJ_dFT) {
+    PSM_CUDA(cudaMemcpy(w.data(), dJ_dFT, sizeof(double) * w.size(), cudaMemcpyDefault), "weights upload");
+  } else {
+    if (nb < 1) return fail(PSM_ERR_STATE, "default functional (mean torque) needs a body");
+    for (int64_t n = 0; n < N; ++n) w[(size_t)n * nb * 6 + 5] = 1.0 / (double)N;
+  }
+  // scratch (stream ordered): K - 1 recompute slots, two adjoint fields, accumulators
+  std::vector<void*> slots((size_t)K, nullptr);
+  void *lam0 = nullptr, *lam1 = nullptr;
+  double *grad = nullptr, *wdev = nullptr, *acc = nullptr, *ftscratch = nullptr;
+  cudaError_t e = cudaSuccess;
+  for (int k = 1; k < K && e == cudaSuccess; ++k) e = cudaMallocAsync(&slots[k], sbytes, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&lam0, (size_t)h->Q * ncell * tb, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&lam1, (size_t)h->Q * ncell * tb, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&grad, ncell * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&wdev, sizeof(double) * w.size(), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&acc, sizeof(double) * (size_t)(N + 1) * ncomp, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ftscratch, sizeof(double) * PSM_MAX_BODIES * 6, st);
+  auto release = [&]() {
+    for (void* s : slots)
+      if (s) cudaFreeAsync(s, st);
+    cudaFreeAsync(lam0, st);
+    cudaFreeAsync(lam1, st);
+    cudaFreeAsync(grad, st);
+    cudaFreeAsync(wdev, st);
+    cudaFreeAsync(acc, st);
+    cudaFreeAsync(ftscratch, st);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "backward scratch allocation");
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(wdev, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lam0, 0, (size_t)h->Q * ncell * tb, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, ncell * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)(N + 1) * ncomp, st);
+
+  // step parameters for the recompute (two-grid, plain loads) and the adjoint
+  StepParams sp;
+  std::memset(&sp, 0, sizeof sp);
+  sp.g = h->g;
+  sp.t = h->tiling;
+  fill_consts<float>(h, sp.cf);
+  fill_consts<double>(h, sp.cd);
+  sp.trt = h->col.fluid == PSM_TRT ? 1 : 0;
+  sp.solid = h->col.solid;
+  sp.weighting = h->col.weighting;
+  sp.nbodies = nb;
+  sp.delta = h->d_delta;
+  sp.partials = h->d_partials;
+  sp.ticket = h->d_ticket;
+  sp.ft_out = ftscratch;
+  sp.err = h->d_err;
+  psm::AdjParams ap;
+  std::memset(&ap, 0, sizeof ap);
+  ap.g = h->g;
+  ap.t = h->tiling;
+  ap.grad = grad;
+  ap.trt = sp.trt;
+  ap.solid = sp.solid;
+  ap.weighting = sp.weighting;
+  ap.nbodies = nb;
+  ap.delta = h->d_delta;
+  ap.partials = h->d_partials;
+  ap.ticket = h->d_ticket;
+  ap.cf = sp.cf;
+  ap.cd = sp.cd;
+  {
+    // d g_i / d u_in = w_i rho0 (3 c_i + 9 (c_i . u_in) c_i - 3 u_in)
+    const double* u = h->grid.u_in;
+    for (int i = 0; i < h->Q; ++i) {
+      const double wi = h->Q == 19 ? psm::lat_w<19>(i) : psm::lat_w<27>(i);
+      const double c[3] = {(double)psm::lat_cx(i), (double)psm::lat_cy(i), (double)psm::lat_cz(i)};
+      const double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+      for (int k = 0; k < 3; ++k) ap.dghost[i][k] = wi * h->grid.rho0 * (3.0 * c[k] + 9.0 * cu * c[k] - 3.0 * u[k]);
+    }
+  }
+  void* la = lam0;  // lambda^{n+1}
+  void* lb = lam1;  // lambda^n
+  for (int64_t m = M - 1; m >= 0 && e == cudaSuccess; --m) {
+    const int64_t ns = h->rec_n0 + m * K;
+    const int64_t ne = std::min<int64_t>(ns + K, h->step);
+    slots[0] = h->ckpt[(size_t)m];
+    // recompute f^{ns+1} .. f^{ne-1} into the slots
+    for (int64_t n = ns; n + 1 < ne && e == cudaSuccess; ++n) {
+      for (int b = 0; b < nb; ++b) sp.body[b] = dev_body(h, b, n);
+      sp.f = slots[(size_t)(n - ns)];
+      sp.f_dst = slots[(size_t)(n - ns + 1)];
+      e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, sp, st);
+    }
+    // adjoint steps ne-1 .. ns
+    for (int64_t n = ne - 1; n >= ns && e == cudaSuccess; --n) {
+      for (int b = 0; b < nb; ++b) ap.body[b] = dev_body(h, b, n);
+      ap.f = slots[(size_t)(n - ns)];
+      ap.lam_in = la;
+      ap.lam_out = lb;
+      ap.w = wdev + (size_t)(n - h->rec_n0) * nb * 6;
+      ap.acc_out = acc + (size_t)(n - h->rec_n0) * ncomp;
+      e = launch_adjoint(h->lat.storage, h->Q, ap.trt, ap, st);
+      std::swap(la, lb);
+    }
+  }
+  slots[0] = nullptr;  // checkpoints stay owned by the handle
+  if (e == cudaSuccess && (h->rec_flags & PSM_RECORD_INIT_FROM_INFLOW)) {
+    ap.lam_in = la;  // lambda^{n0}
+    ap.acc_out = acc + (size_t)N * ncomp + nb * 3;
+    e = launch_adjoint_init(h->lat.storage, h->Q, ap, h->max_blocks, st);
+  }
+  std::vector<double> acc_h((size_t)(N + 1) * ncomp);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(acc_h.data(), acc, sizeof(double) * acc_h.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && grad_eps)
+    e = cudaMemcpyAsync(grad_eps, grad, sizeof(double) * ncell, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release();
+  if (e != cudaSuccess) return cuda_fail(e, "backward pass");
+  {
+    const int rc = check_err(h);
+    if (rc != PSM_OK) return rc;
+  }
+  // scalar gradients: sum the per-step FP64 partials in step order
+  std::vector<double> gw((size_t)nb * 3, 0.0), gu(3, 0.0);
+  bool finite = true;
+  for (int64_t n = 0; n <= N; ++n) {
+    const double* a = acc_h.data() + (size_t)n * ncomp;
+    for (int k = 0; k < nb * 3; ++k) gw[k] += a[k];
+    for (int k = 0; k < 3; ++k) gu[k] += a[nb * 3 + k];
+  }
+  for (double v : gw) finite = finite && std::isfinite(v);
+  for (double v : gu) finite = finite && std::isfinite(v);
+  if (grad_omega) std::memcpy(grad_omega, gw.data(), sizeof(double) * gw.size());
+  if (grad_uin) std::memcpy(grad_uin, gu.data(), sizeof(double) * 3);
+  if (!finite) return fail(PSM_ERR_NONFINITE, "gradient holds NaN or Inf");
   return PSM_OK;
 }
 

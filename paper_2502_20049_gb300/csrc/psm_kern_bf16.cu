@@ -2,3 +2,6 @@
 #include "psm_kernels.cuh"
 
 PSM_DEFINE_STORAGE(bf16, __nv_bfloat16)
+#include "psm_adjoint.cuh"
+
+PSM_DEFINE_ADJOINT(bf16, __nv_bfloat16)

@@ -2,3 +2,6 @@
 #include "psm_kernels.cuh"
 
 PSM_DEFINE_STORAGE(fp16, __half)
+#include "psm_adjoint.cuh"
+
+PSM_DEFINE_ADJOINT(fp16, __half)

@@ -2,3 +2,6 @@
 #include "psm_kernels.cuh"
 
 PSM_DEFINE_STORAGE(fp32, float)
+#include "psm_adjoint.cuh"
+
+PSM_DEFINE_ADJOINT(fp32, float)

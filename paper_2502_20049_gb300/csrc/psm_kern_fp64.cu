@@ -2,3 +2,6 @@
 #include "psm_kernels.cuh"
 
 PSM_DEFINE_STORAGE(fp64, double)
+#include "psm_adjoint.cuh"
+
+PSM_DEFINE_ADJOINT(fp64, double)

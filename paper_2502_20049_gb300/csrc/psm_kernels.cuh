@@ -619,6 +619,10 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   __syncthreads();
 
   // producer: stage the pre-collision rows of tile `tile` into stage `s`
+  // producer: all 32 lanes of warp 0 stage the pre-collision rows of tile
+  // `tile` into stage `s`, one copy job per lane (one row box of all slots per
+  // tile row in the own-cell modes; one row of slot opp(i) plus its 16-byte
+  // x-edge chunk per tile row and direction in the AA odd step)
   auto produce = [&](int tile, int s) {
     int tx0, y0, z;
     {
@@ -632,41 +636,43 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     unsigned char* st = stages + (long long)s * SB;
     unsigned long long* bar = &bars[s];
     fence_proxy_async();
-    for (int r = 0; r < TY; ++r) {
-      const int y = y0 + r;
+    const int njobs = (MODE == MODE_AA_ODD) ? TY * Q : TY;
+    for (int job = lane; job < njobs; job += 32) {
       if (MODE != MODE_AA_ODD) {
+        const int r = job;
         mbar_expect_tx(bar, (unsigned)(Q * TX * (int)sizeof(S)));
-        tma_load_4d(st + r * BB, map_rows, tx0, y, z, 0, bar);
+        tma_load_4d(st + r * BB, map_rows, tx0, y0 + r, z, 0, bar);
       } else {
-#pragma unroll 1
-        for (int i = 0; i < Q; ++i) {
-          const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
-          int zs = z - cz;
-          if (zs < 0 || zs >= p.g.nz) {
-            if (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET) continue;  // ghost populations: no load
-            zs = zs < 0 ? zs + p.g.nz : zs - p.g.nz;
-          }
-          int ys = y - cy;
-          ys = ys < 0 ? ys + p.g.ny : (ys >= p.g.ny ? ys - p.g.ny : ys);
-          const int slot = lat_opp(i);
-          mbar_expect_tx(bar, (unsigned)(TX * (int)sizeof(S)));
-          tma_load_4d(st + (r * Q + i) * RB, map_rows, tx0, ys, zs, slot, bar);
-          if (cx != 0) {
-            // cx = +1 reads x0 - 1 (left chunk), cx = -1 reads x0 + TX (right chunk), wrapped in x
-            const int xe = cx > 0 ? (tx0 == 0 ? p.g.nx - EP : tx0 - EP) : (tx0 + TX == p.g.nx ? 0 : tx0 + TX);
-            const S* src = buf + (long long)slot * N + ((long long)zs * p.g.ny + ys) * p.g.nx + xe;
-            unsigned char* e = st + MB + ((r * Q + i) * 2 + (cx > 0 ? 0 : 1)) * 16;
-            mbar_expect_tx(bar, 16u);
-            bulk_load_16(e, src, bar);
-          }
+        const int r = job / Q, i = job % Q;
+        const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+        int zs = z - cz;
+        if (zs < 0 || zs >= p.g.nz) {
+          if (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET) continue;  // ghost populations: no load
+          zs = zs < 0 ? zs + p.g.nz : zs - p.g.nz;
+        }
+        int ys = y0 + r - cy;
+        ys = ys < 0 ? ys + p.g.ny : (ys >= p.g.ny ? ys - p.g.ny : ys);
+        const int slot = lat_opp(i);
+        mbar_expect_tx(bar, (unsigned)(TX * (int)sizeof(S)));
+        tma_load_4d(st + (r * Q + i) * RB, map_rows, tx0, ys, zs, slot, bar);
+        if (cx != 0) {
+          // cx = +1 reads x0 - 1 (left chunk), cx = -1 reads x0 + TX (right chunk), wrapped in x
+          const int xe = cx > 0 ? (tx0 == 0 ? p.g.nx - EP : tx0 - EP) : (tx0 + TX == p.g.nx ? 0 : tx0 + TX);
+          const S* src = buf + (long long)slot * N + ((long long)zs * p.g.ny + ys) * p.g.nx + xe;
+          unsigned char* e = st + MB + ((r * Q + i) * 2 + (cx > 0 ? 0 : 1)) * 16;
+          mbar_expect_tx(bar, 16u);
+          bulk_load_16(e, src, bar);
         }
       }
     }
-    mbar_arrive(bar);
-    s_issued[s] += 1;
+    __syncwarp();  // every lane's expected bytes are registered before the arrival
+    if (lane == 0) {
+      mbar_arrive(bar);
+      s_issued[s] += 1;
+    }
   };
 
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     for (int k = 0; k < NST; ++k) {
       const int tile = blockIdx.x + k * gridDim.x;
       if (tile < ntiles) produce(tile, k);
@@ -736,8 +742,8 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         }
       }
     }
-    __syncthreads();  // stage s fully read: thread 0 may refill it
-    if (threadIdx.x == 0) {
+    __syncthreads();  // stage s fully read: warp 0 may refill it
+    if (warp == 0) {
       const int next = tile + NST * gridDim.x;
       if (next < ntiles) produce(next, s);
     }

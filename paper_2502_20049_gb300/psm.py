@@ -104,6 +104,9 @@ def lib() -> ctypes.CDLL:
                 "psm_mass": (i, [H, P(d)]),
                 "psm_synchronize": (i, [H]),
                 "psm_set_kernel_variant": (i, [H, i]),
+                "psm_set_eps_delta": (i, [H, vp]),
+                "psm_record": (i, [H, i, i]),
+                "psm_backward": (i, [H, vp, vp, vp, vp]),
                 "psm_kernel_variant": (i, [H, P(i)]),
             }
             for name, (res, args) in sig.items():
@@ -376,6 +379,43 @@ class Solver:
 
     def synchronize(self):
         check(lib().psm_synchronize(self._h))
+
+    def set_eps_delta(self, delta):
+        """Per-cell additive eps perturbation (float32 [nz, ny, nx], numpy or torch); None removes it."""
+        if delta is None:
+            check(lib().psm_set_eps_delta(self._h, None))
+            return
+        if hasattr(delta, "data_ptr"):
+            d = delta.detach().to(dtype=__import__("torch").float32).contiguous()
+            p, keep = _ptr(d, np.float32, self.ncell)
+        else:
+            d = np.ascontiguousarray(delta, dtype=np.float32)
+            p, keep = _ptr(d, np.float32, self.ncell)
+        check(lib().psm_set_eps_delta(self._h, p))
+
+    def record(self, K: int, init_from_inflow: bool = False):
+        """Checkpoint the trajectory every K steps from now on (K = 0 stops)."""
+        check(lib().psm_record(self._h, int(K), 1 if init_from_inflow else 0))
+
+    def backward(self, dJ_dFT=None, grad_eps=None):
+        """Adjoint gradients of J = sum w * FT over the recorded steps.
+
+        Returns (grad_eps [nz, ny, nx] (or the given buffer), grad_omega
+        [nbodies, 3], grad_uin [3]).  dJ_dFT None = mean torque about z on body 0.
+        """
+        c = self.cfg
+        nb = self.num_bodies
+        w = None
+        if dJ_dFT is not None:
+            w = np.ascontiguousarray(dJ_dFT, dtype=np.float64)
+        if grad_eps is None:
+            grad_eps = np.zeros((c.nz, c.ny, c.nx))
+        gp, keep = _ptr(grad_eps, np.float64, self.ncell)
+        gw = np.zeros((max(nb, 1), 3))
+        gu = np.zeros(3)
+        check(lib().psm_backward(self._h, None if w is None else ctypes.c_void_p(w.ctypes.data), gp,
+                                 ctypes.c_void_p(gw.ctypes.data), ctypes.c_void_p(gu.ctypes.data)))
+        return grad_eps, gw[:nb], gu
 
     KERNELS = {"auto": 0, "plain": 1, "tma": 2}
 

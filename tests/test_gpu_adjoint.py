@@ -1,0 +1,153 @@
+"""GPU discrete adjoint (psm_record / psm_backward, through the C ABI) against
+the oracle's tangent-linear model and against central finite differences.
+
+J = mean torque about z on body 0 over the recorded steps.  The tangent-linear
+model is the oracle's own FP64 step on dual numbers (pinned against FP64
+finite differences in test_oracle_tangent.py); a directional derivative there
+must equal the inner product of the GPU gradient with the same direction.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2502_20049_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+
+    g.build()
+
+
+def small_case(storage="fp64", fluid="trt", solid=1, weighting=1, streaming="aa", steps=24, bc_z=1):
+    return W.Case("adj_small", 12, 12, 16, Q=19, storage=storage, streaming=streaming, fluid=fluid, tau=0.62,
+                  solid=solid, weighting=weighting, bc_z=bc_z, u_in=(0.0, 0.0, 0.03), steps=steps,
+                  bodies=[W.BodyCase(W.ELLIPSOID, (4.0, 2.2, 1.8), 2, (6.0, 6.2, 8.0), omega=(0.0, 0.0, 0.04))])
+
+
+def gpu_grad(case, K=4):
+    from paper_2502_20049_gb300 import psm
+
+    sol = psm.Solver.from_case(case)
+    sol.record(K, init_from_inflow=True)
+    sol.step(case.steps)
+    ge, gw, gu = sol.backward()
+    J = sol.force_torque(0)[:, 5].mean()
+    return J, ge, gw, gu
+
+
+def oracle_tl(case, d_delta=None, d_omega=(0, 0, 0), d_u=(0, 0, 0)):
+    import oracle
+
+    cfg = oracle.Config(nx=case.nx, ny=case.ny, nz=case.nz, Q=case.Q, bc_z=case.bc_z, rho0=case.rho0,
+                        u_in=tuple(case.u_in), fluid={"bgk": 0, "trt": 1}[case.fluid], tau=case.tau,
+                        trt_lambda=case.trt_lambda, solid=case.solid, weighting=case.weighting)
+    sim = oracle.TangentSim(cfg, d_u_in=d_u)
+    b = case.bodies[0]
+    sub, lo = oracle.voxelize(b.kind, b.params, b.s)
+    sim.add_body(oracle.BodySpec(sub=sub, s=b.s, lo=lo, R0=b.R0, Q0=np.array(b.Q0), omega=b.omega, v=b.v),
+                 d_omega=d_omega)
+    sim.init_eq(case.rho0, case.u_in, du=d_u)
+    sim.set_delta(None, d_delta)
+    sim.step(case.steps)
+    v, t = sim.force_torque()
+    return v[:, 0, 5].mean(), t[:, 0, 5].mean()
+
+
+CASES = [dict(), dict(fluid="bgk"), dict(solid=2), dict(solid=3), dict(weighting=0), dict(streaming="twogrid"),
+         dict(bc_z=0)]
+
+
+@pytest.mark.parametrize("kw", CASES)
+def test_adjoint_fp64_matches_tangent_linear(kw):
+    case = small_case(**kw)
+    J, ge, gw, gu = gpu_grad(case)
+    v = W.random_unit((case.nz, case.ny, case.nx), seed=W.SEED + 5)
+    J_or, dv = oracle_tl(case, d_delta=v)
+    assert abs(J - J_or) <= 1e-12 * abs(J_or)
+    ip = float((ge * v).sum())
+    print(f"{kw}: <grad, v> {ip:.12e} vs tangent {dv:.12e}")
+    assert abs(ip - dv) <= 1e-9 * abs(dv)
+    _, dw = oracle_tl(case, d_omega=(0.0, 0.0, 1.0))
+    assert abs(gw[0, 2] - dw) <= 1e-9 * abs(dw)
+    _, dwx = oracle_tl(case, d_omega=(1.0, 0.0, 0.0))
+    assert abs(gw[0, 0] - dwx) <= 1e-9 * max(abs(dwx), 1e-3 * abs(dw))
+    _, du = oracle_tl(case, d_u=(0.0, 0.0, 1.0))
+    assert abs(gu[2] - du) <= 1e-9 * abs(du)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-3), ("fp16", 2e-2)])
+def test_adjoint_reduced_precision_matches_tangent_linear(storage, tol):
+    case = small_case(storage=storage)
+    J, ge, gw, gu = gpu_grad(case)
+    v = W.random_unit((case.nz, case.ny, case.nx), seed=W.SEED + 6)
+    _, dv = oracle_tl(case, d_delta=v)
+    _, dw = oracle_tl(case, d_omega=(0.0, 0.0, 1.0))
+    _, du = oracle_tl(case, d_u=(0.0, 0.0, 1.0))
+    ip = float((ge * v).sum())
+    errs = (abs(ip - dv) / abs(dv), abs(gw[0, 2] - dw) / abs(dw), abs(gu[2] - du) / abs(du))
+    print(f"{storage} adjoint relative errors (delta, omega, u_in): {errs}")
+    assert max(errs) <= tol
+
+
+def test_adjoint_fp64_vs_central_fd_16_cells():
+    """GPU FP64 adjoint vs FP64 central differences of the GPU forward on 16
+    seeded cells of the body's swept region (h = 1e-4 absolute)."""
+    from paper_2502_20049_gb300 import psm
+
+    case = W.c4_adjoint(n=32, steps=48).with_(storage="fp64")
+    case.bodies[0].omega = (0.0, 0.0, 0.01)
+    J, ge, _, _ = gpu_grad(case, K=8)
+    mask = np.zeros((case.nz, case.ny, case.nx), bool)
+    sol = psm.Solver.from_case(case)
+    for n in range(0, case.steps, 8):
+        mask |= sol.eps() > 0
+        sol.step(8)
+    cells = W.pick_cells(mask, 16)
+    h = 1e-4
+
+    def J_of(delta):
+        s = psm.Solver.from_case(case)
+        s.set_eps_delta(delta)
+        s.step(case.steps)
+        return s.force_torque(0)[:, 5].mean()
+
+    scale = np.abs(ge).max()
+    for c in cells:
+        d = np.zeros(case.cells, np.float32)
+        d[c] = h
+        fd = (J_of(d) - J_of(-d)) / (2 * h)
+        g = ge.reshape(-1)[c]
+        assert abs(g - fd) <= 1e-6 * scale + 1e-6 * abs(fd), (c, g, fd)
+
+
+def test_autograd_function_fp64():
+    import torch
+
+    from paper_2502_20049_gb300.autograd import PSMTorque
+
+    case = small_case()
+    eps_delta = torch.zeros((case.nz, case.ny, case.nx), dtype=torch.float64, device="cuda", requires_grad=True)
+    omega = torch.tensor(case.bodies[0].omega, dtype=torch.float64, requires_grad=True)
+    u_in = torch.tensor(case.u_in, dtype=torch.float64, requires_grad=True)
+    J = PSMTorque.apply(eps_delta, omega, u_in, case, case.steps, 4)
+    J.backward()
+    v = W.random_unit((case.nz, case.ny, case.nx), seed=W.SEED + 7)
+    J_or, dv = oracle_tl(case, d_delta=v)
+    _, dw = oracle_tl(case, d_omega=(0.0, 0.0, 1.0))
+    assert abs(float(J) - J_or) <= 1e-12 * abs(J_or)
+    assert abs(float((eps_delta.grad.cpu().numpy() * v).sum()) - dv) <= 1e-9 * abs(dv)
+    assert abs(float(omega.grad[2]) - dw) <= 1e-9 * abs(dw)
+
+
+def test_backward_without_record_is_state_error():
+    from paper_2502_20049_gb300 import psm
+
+    sol = psm.Solver.from_case(small_case())
+    sol.step(2)
+    with pytest.raises(psm.PSMError) as ei:
+        sol.backward()
+    assert ei.value.code == -5
