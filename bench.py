@@ -145,13 +145,6 @@ class Clocks:
                 "reasons": reasons, "samples": len(loaded)}
 
 
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
 def cpu_baseline(name: str, steps: int = 3):
     """The oracle as it stands on this host's cores: `steps` steps of the full workload."""
     from oracle.cases import sim_from_case as oracle_sim
@@ -169,7 +162,9 @@ def cpu_baseline(name: str, steps: int = 3):
 
 
 def run_reference(args):
-    rank, world, _ = dist_env()
+    from paper_2502_20049_gb300 import replicas
+
+    rank, world, _ = replicas.env()
     if rank != 0:
         return
     from oracle.cases import sim_from_case as oracle_sim
@@ -182,7 +177,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     mlups = case.cells * args.steps / dt / 1e6
     _, desc = workload(args.workload, args.streaming)
-    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "sample_cells": case.cells},
@@ -193,49 +188,97 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(sol, steps: int, stream) -> float:
+    """Device time (s) of `steps` psm_step launches, CUDA events on the solver's stream."""
+    import torch
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sol.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sol.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def variant_mlups(name, streaming, storage, kernel, steps, warmup, stream):
+    """MLUPS of one storage / streaming variant of the workload (same timing rules)."""
+    from paper_2502_20049_gb300 import psm
+
+    case, _ = workload(name, streaming)
+    case = case.with_(storage=storage)
+    sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
+    if kernel != "auto":
+        sol.set_kernel_variant(kernel)
+    sol.step(warmup)
+    t = time_steps(sol, steps, stream)
+    v = sol.kernel_variant
+    sol.close()
+    return {"mlups": round(case.cells * steps / t / 1e6, 1), "kernel": v,
+            "hbm_gbs": round(2 * case.Q * psm.STORAGE_BYTES[storage] * case.cells * steps / t / 1e9, 1)}
+
+
+def adjoint_cost(stream, steps: int = 512, K: int = 64):
+    """Adjoint workload: 128^3 D3Q19 TRT FP32, rotating ellipsoid, checkpoint every
+    K steps.  Returns forward and backward time per step and their ratio (backward
+    includes the recompute of every segment)."""
+    import time as _t
+
+    from paper_2502_20049_gb300 import psm
+    from paper_2502_20049_gb300 import workloads as W
+
+    case = W.c4_adjoint(steps=steps)
+    sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
+    sol.step(4)
+    t_fwd = time_steps(sol, steps, stream)
+    sol2 = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
+    sol2.record(K, init_from_inflow=True)
+    t_rec = time_steps(sol2, steps, stream)
+    t0 = _t.perf_counter()
+    sol2.backward()
+    t_bwd = _t.perf_counter() - t0
+    sol.close()
+    sol2.close()
+    return {"workload": f"D3Q19 TRT FP32 128^3, rotating ellipsoid 20/10/4, {steps} steps, checkpoint every {K}",
+            "forward_ms_per_step": round(t_fwd / steps * 1e3, 4),
+            "recorded_forward_ms_per_step": round(t_rec / steps * 1e3, 4),
+            "backward_ms_per_step": round(t_bwd / steps * 1e3, 4),
+            "ratio": round(t_bwd / t_fwd, 3)}
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     import __graft_entry__ as G
+    from paper_2502_20049_gb300 import replicas
 
-    rank, world, local = dist_env()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    rank, world, local = replicas.env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
     torch.cuda.set_device(local)
+    dist = replicas.init()
     G.build()
     from paper_2502_20049_gb300 import psm
 
     case, desc = workload(args.workload, args.streaming)
+    if args.storage:
+        case = case.with_(storage=args.storage)
+        desc = desc.replace("FP32", args.storage.upper()).replace("FP16-shifted", args.storage.upper())
     stream = torch.cuda.current_stream()
     sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
+    if args.kernel != "auto":
+        sol.set_kernel_variant(args.kernel)
     cells = case.cells
     sol.step(args.warmup)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
-        ev0.record(stream)
-        sol.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t = ev0.elapsed_time(ev1) / 1e3
-    t_max = t
-    if dist:
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = cells * args.steps * world / t_max / 1e6
+        t = time_steps(sol, args.steps, stream)
+    replicas.barrier(dist)
+    t_max = replicas.max_over_ranks(dist, t, device="cuda")
+    value = replicas.aggregate_rate(cells * args.steps, world, t_max) / 1e6
     ms = t_max / args.steps * 1e3
 
     # roofline of the step kernel (the only kernel in the step): algorithmic
@@ -243,12 +286,12 @@ def run_ours(args):
     bpc = sol.bytes_per_cell_update()
     achieved = bpc * cells / (t / args.steps) / 1e9
     peak, peak_kind = peaks()
-    key = f"{args.workload}/{args.streaming}"
+    key = f"{args.workload}/{case.streaming}/{case.storage}/{sol.kernel_variant}"
     traffic = NCU_BYTES_PER_CELL.get(key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"hbm_gbs of {peak_kind}",
                 "traffic": None if traffic is None else round(traffic * cells),
-                "algorithmic_bytes_per_cell": bpc}
+                "algorithmic_bytes_per_cell": bpc, "kernel": f"k_step ({sol.kernel_variant} loads)"}
 
     # end to end through the public API: every step one psm_step call (the
     # pose rides in the launch parameters) and a synchronous read of that
@@ -256,26 +299,22 @@ def run_ours(args):
     nb = len(case.bodies)
     out = torch.empty((1, 6), dtype=torch.float64, pin_memory=True)
     sol.synchronize()
-    e2e_steps = args.steps
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(args.steps):
         sol.step(1)
         for b in range(nb):
             sol.force_torque(b, sol.step_count - 1, 1, out=out)
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": round(cells * e2e_steps * world / t_e2e / 1e6, 1), "unit": "MLUPS", "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": 48 * nb,
+    t_e2e = replicas.max_over_ranks(dist, time.perf_counter() - t0, device="cuda")
+    e2e = {"value": round(replicas.aggregate_rate(cells * args.steps, world, t_e2e) / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 48 * nb,
            "note": "per step: psm_step(h, 1) with the body poses as launch parameters, then psm_force_torque "
                    "into pinned host memory (synchronising)"}
+    sol.close()
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp64": "f64"}.get(case.storage, "f32"), "data": "synthetic",
-            "config": {"workload": desc, "cells": cells, "streaming": args.streaming, "storage": case.storage,
+            "config": {"workload": desc, "cells": cells, "streaming": case.streaming, "storage": case.storage,
                        "stencil": f"D3Q{case.Q}", "parallelism": f"replicas x{world}",
                        "l2": f"PDF working set {cells * case.Q * psm.STORAGE_BYTES[case.storage] / 1e9:.2f} GB "
                              f"> 129 MB L2, no flush"},
@@ -283,11 +322,19 @@ def run_ours(args):
     ck = clk.summary()
     if ck:
         line["clocks"] = ck
+    if not args.no_extras:
+        vs = {}
+        for streaming, storage in (("twogrid", "fp16"), ("twogrid", "bf16"), ("aa", "fp32"), ("aa", "fp16")):
+            if streaming == case.streaming and storage == case.storage:
+                continue
+            vs[f"{storage}/{streaming}"] = variant_mlups(args.workload, streaming, storage, "auto", 300, 5, stream)
+        line["variants"] = vs
+        line["adjoint"] = adjoint_cost(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
+    if dist is not None:
         dist.destroy_process_group()
 
 
@@ -298,8 +345,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2", choices=["c2", "c5", "c3_fp32", "c3_fp16", "c3_bf16"])
-    ap.add_argument("--streaming", default="aa", choices=["aa", "twogrid"])
+    ap.add_argument("--streaming", default="twogrid", choices=["aa", "twogrid"])
+    ap.add_argument("--storage", default=None, choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the variant and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

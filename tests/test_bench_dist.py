@@ -1,0 +1,58 @@
+"""The multi-rank timing logic of bench.py (replicas: barrier + max over ranks),
+run as two gloo ranks on the CPU."""
+
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    from paper_2502_20049_gb300 import replicas
+
+    dist = replicas.init("gloo")
+    r, w, lr = replicas.env()
+    replicas.barrier(dist)
+    t = 1.0 + r  # rank 1 is the slow one
+    t_max = replicas.max_over_ranks(dist, t)
+    rate = replicas.aggregate_rate(100.0, w, t_max)
+    out.put((r, w, lr, t_max, rate))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_time_and_rate():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[0] for r in res] == [0, 1]
+    for r, w, lr, t_max, rate in res:
+        assert w == 2 and lr == r
+        assert t_max == 2.0
+        assert rate == pytest.approx(100.0 * 2 / 2.0)
+
+
+def test_single_rank_defaults(monkeypatch):
+    from paper_2502_20049_gb300 import replicas
+
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    assert replicas.env() == (0, 1, 0)
+    assert replicas.init() is None
+    assert replicas.max_over_ranks(None, 3.5) == 3.5
