@@ -158,6 +158,7 @@ def test_adjoint_c4_full_fp32_vs_fp64_fd():
     for c in cells:
         fd = fd_richardson(J_of, case.cells, c, 1e-4)
         g = ge.reshape(-1)[c]
+        print(f"cell {c}: adjoint {g:.9e} fd {fd:.9e} rel {abs(g - fd) / max(abs(fd), 1e-300):.3e} (max |grad| {scale:.3e})")
         worst = max(worst, abs(g - fd) / max(abs(fd), 1e-3 * scale))
     print(f"C4 128^3 FP32 adjoint vs FP64 FD, 16 cells: worst relative error {worst:.3e}")
     assert worst <= 1e-2
