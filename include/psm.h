@@ -285,6 +285,32 @@ int psm_record(psm_handle h, int K, int flags);
  * PSM_ERR_STATE without a recorded forward. */
 int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* grad_omega, double* grad_uin);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free reduction (no counterpart in the paper)                   */
+/* ------------------------------------------------------------------------ */
+
+/* Total mass sum_x sum_i f_i of a caller-owned PDF field, for callers that
+ * must not allocate device memory (an application that routes every device
+ * allocation through its own pool, or a loop that cannot afford the implicit
+ * device synchronisation of cudaMalloc).  It allocates nothing: its scratch
+ * (block partial sums, a ticket counter, the result) is a file-scope
+ * __device__ array of about 128 KB that every GPU loading the library holds
+ * until the process exits.
+ *   f:       device pointer, [Q][ncell] values in the storage precision
+ *            `storage` (PSM_FP64 ... PSM_BF16_SHIFTED), stored as
+ *            f_i - w_i rho0 (pass rho0 = 0 for unshifted values);
+ *   stencil: PSM_D3Q19 or PSM_D3Q27;  ncell: 1 .. 2^30 (PSM_ERR_ARG beyond:
+ *            the scratch holds 16384 partial sums of 65536 cells each);
+ *   stream:  cudaStream_t (NULL = legacy default stream);
+ *   out:     one double, host or device; the call synchronises the stream.
+ * The summation order is fixed (deterministic).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) for that
+ * device; make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+int psm_mass_noalloc(const void* f, int storage, int stencil, int64_t ncell, double rho0, void* stream,
+                     double* out);
+
 #define PSM_KERNEL_AUTO 0
 #define PSM_KERNEL_PLAIN 1
 #define PSM_KERNEL_TMA 2
