@@ -200,6 +200,12 @@ int psm_init_equilibrium(psm_handle h, double rho, const double u[3]);
 int psm_set_state(psm_handle h, const double* f);
 int psm_get_state(psm_handle h, double* f);
 
+/* Natural, unshifted FP64 PDFs of n listed cells (flat indices
+ * (z * ny + y) * nx + x, host or device): f[n][Q] in the library's direction
+ * order.  PSM_ERR_ARG for an index out of range.  For sampled checks of grids
+ * too large to export whole. */
+int psm_get_cells(psm_handle h, const int64_t* cells, int64_t n, double* f);
+
 /* Density and velocity u = j / rho per cell: rho[nz][ny][nx], u[nz][ny][nx][3] (FP64). */
 int psm_get_macroscopic(psm_handle h, double* rho, double* u);
 

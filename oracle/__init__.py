@@ -93,6 +93,7 @@ def _lib():
                 "or_eps": (i, [vp, l, dp, ip]),
                 "or_macroscopic": (i, [vp, dp, dp]),
                 "or_update_cells": (i, [vp, P(ctypes.c_long), l, dp]),
+                "or_collide_at": (i, [vp, l, i, i, i, dp, dp, dp, dp]),
                 "ort_create": (vp, [vp, dp]),
                 "ort_destroy": (None, [vp]),
                 "ort_set_threads": (i, [vp, i]),
@@ -349,6 +350,17 @@ class Sim:
         if rc != 0:
             raise IndexError("cell index out of range")
         return out
+
+    def collide_at(self, n: int, x: int, y: int, z: int, f_in):
+        """(post[Q], g[3], eps) of cell (x, y, z) at the pose of step n from given
+        pre-collision PDFs f_in[Q] (oracle direction order)."""
+        f_in = np.ascontiguousarray(f_in, dtype=np.float64).reshape(self.cfg.Q)
+        post = np.zeros(self.cfg.Q)
+        g = np.zeros(3)
+        e = np.zeros(1)
+        if _lib().or_collide_at(self._h, int(n), int(x), int(y), int(z), _dp(f_in), _dp(post), _dp(g), _dp(e)) != 0:
+            raise IndexError((x, y, z))
+        return post, g, float(e[0])
 
     def macroscopic(self):
         """(rho[nz,ny,nx], u[nz,ny,nx,3]) with u = j / rho."""

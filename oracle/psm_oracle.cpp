@@ -248,6 +248,15 @@ struct Sim {
 
   long cell(int x, int y, int z) const { return ((long)z * cfg.ny + y) * cfg.nx + x; }
 
+  // The state arrays are allocated on first use, so that a simulation used
+  // only for one-cell collisions (collide_at) of a huge grid stays small.
+  void ensure_state() {
+    if (f.empty()) {
+      f.assign((size_t)L.Q * ncell, T(0.0));
+      post.assign((size_t)L.Q * ncell, T(0.0));
+    }
+  }
+
   // Ghost-plane populations: f^eq_i(rho0, u_in) (reading of the unstated
   // inflow/outflow condition: equilibrium planes at z=-1 and z=nz).
   T ghost(int i) const { return feq<T>(L, i, T(cfg.rho0), u_in); }
@@ -260,6 +269,7 @@ struct Sim {
   }
 
   void init_eq(T rho, const T u[3]) {
+    ensure_state();
     for (int i = 0; i < L.Q; ++i)
       for (int z = 0; z < cfg.nz; ++z)
         for (int y = 0; y < cfg.ny; ++y)
@@ -320,13 +330,22 @@ struct Sim {
   // force density g = B sum_i Omega^S_i c_i.
   void collide_cell(int x, int y, int z, double eps_c, int owner_c, const std::vector<Pose>& poses, T* post,
                     T* g) const {
+    const long c = cell(x, y, z);
+    T fl[27];
+    for (int i = 0; i < L.Q; ++i) fl[i] = f[i * ncell + c];
+    collide_given(x, y, z, eps_c, owner_c, poses, fl, post, g);
+  }
+
+  // The same collision from explicitly given pre-collision PDFs fl[Q] of cell
+  // (x, y, z) (the per-cell delta still applies).
+  void collide_given(int x, int y, int z, double eps_c, int owner_c, const std::vector<Pose>& poses, const T* fl,
+                     T* post, T* g) const {
     const int Q = L.Q;
     const double tau = cfg.tau;
     const double cs2 = 1.0 / 3.0;
     const double om_p = omega_plus(), om_m = omega_minus();
     const long c = cell(x, y, z);
-    T fl[27], E[27], G[27], OF[27], OS[27];
-    for (int i = 0; i < Q; ++i) fl[i] = f[i * ncell + c];
+    T E[27], G[27], OF[27], OS[27];
     // moments of the pre-collision PDFs
     T rho(0.0), j[3] = {T(0.0), T(0.0), T(0.0)};
     for (int i = 0; i < Q; ++i) {
@@ -438,6 +457,7 @@ struct Sim {
   }
 
   void do_step() {
+    ensure_state();
     const int Q = L.Q;
     const int nx = cfg.nx, ny = cfg.ny, nz = cfg.nz;
     const double tau = cfg.tau;
@@ -528,8 +548,6 @@ Sim<T>* make_sim(const or_config* cfg) {
   S->cfg = *cfg;
   S->L = make_lattice(cfg->Q);
   S->ncell = (long)cfg->nx * cfg->ny * cfg->nz;
-  S->f.assign((size_t)S->L.Q * S->ncell, T(0.0));
-  S->post.assign((size_t)S->L.Q * S->ncell, T(0.0));
   for (int k = 0; k < 3; ++k) S->u_in[k] = T(cfg->u_in[k]);
 #ifdef _OPENMP
   S->nthreads = omp_get_max_threads();
@@ -715,11 +733,13 @@ int or_init_eq(void* h, double rho, const double* u) {
 }
 int or_set_f(void* h, const double* f) {
   auto* S = static_cast<Sim<double>*>(h);
+  S->ensure_state();
   std::memcpy(S->f.data(), f, sizeof(double) * S->f.size());
   return 0;
 }
 int or_get_f(void* h, double* f) {
   auto* S = static_cast<Sim<double>*>(h);
+  S->ensure_state();
   std::memcpy(f, S->f.data(), sizeof(double) * S->f.size());
   return 0;
 }
@@ -753,14 +773,33 @@ int or_eps(void* h, long n, double* eps, int* owner) {
 // out[k * Q + i] in the oracle's direction order.
 int or_update_cells(void* h, const long* cells, long n, double* out) {
   auto* S = static_cast<Sim<double>*>(h);
+  S->ensure_state();
   for (long k = 0; k < n; ++k)
     if (cells[k] < 0 || cells[k] >= S->ncell) return -1;
   S->update_cells(cells, n, out);
   return 0;
 }
+// One cell's collision at the pose of step n from given pre-collision PDFs
+// f_in[Q] (oracle order): post_out[Q] and g_out[3] = B sum_i Omega^S_i c_i;
+// eps and owner are computed by the remap (Sec. 3).
+int or_collide_at(void* h, long n, int x, int y, int z, const double* f_in, double* post_out, double* g_out,
+                  double* eps_out) {
+  auto* S = static_cast<Sim<double>*>(h);
+  if (x < 0 || y < 0 || z < 0 || x >= S->cfg.nx || y >= S->cfg.ny || z >= S->cfg.nz) return -1;
+  const std::vector<Pose> poses = S->poses_at(n);
+  double e;
+  int o;
+  S->remap_one(poses, x, y, z, e, o);
+  double g[3];
+  S->collide_given(x, y, z, e, o, poses, f_in, post_out, g);
+  if (g_out) for (int k = 0; k < 3; ++k) g_out[k] = g[k];
+  if (eps_out) *eps_out = e;
+  return 0;
+}
 // rho and u = j/rho (no forcing shift) per cell
 int or_macroscopic(void* h, double* rho, double* u) {
   auto* S = static_cast<Sim<double>*>(h);
+  S->ensure_state();
   for (long c = 0; c < S->ncell; ++c) {
     double r = 0, j[3] = {0, 0, 0};
     for (int i = 0; i < S->L.Q; ++i) {
@@ -822,6 +861,7 @@ int ort_ft(void* h, double* vals, double* tans) {
 }
 int ort_get_f(void* h, double* vals, double* tans) {
   auto* S = static_cast<Sim<Dual>*>(h);
+  S->ensure_state();
   for (size_t k = 0; k < S->f.size(); ++k) {
     vals[k] = S->f[k].v;
     if (tans) tans[k] = S->f[k].d;

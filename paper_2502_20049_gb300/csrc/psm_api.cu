@@ -45,6 +45,12 @@ size_t storage_bytes(int st) {
   }
 }
 
+// Tensor maps of one PDF buffer (x, y, z, slot): box (TX, 1, 1, Q) and (TX, 1, 1, 1).
+struct BufMaps {
+  CUtensorMap rowq;
+  CUtensorMap row1;
+};
+
 struct HostBody {
   unsigned long long* d_bricks = nullptr;
   int64_t gx = 0, gy = 0, gz = 0;
@@ -109,7 +115,7 @@ struct psm_solver {
   bool tma_ok = false;
   int variant = PSM_KERNEL_AUTO;
   psm::Tiling tma_tiling;
-  psm::TmaMaps maps[2];
+  BufMaps maps[2];
   // trajectory recording for psm_backward: checkpoints every rec_K steps from rec_n0
   bool recording = false;
   int rec_K = 0;
@@ -285,7 +291,7 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
 }
 
 int layout_of(const psm_solver* h) {
-  if (h->lat.streaming == PSM_STREAM_TWO_GRID) return psm::LAYOUT_NATURAL;
+  if (h->lat.streaming == PSM_STREAM_TWO_GRID) return psm::LAYOUT_PULL;
   return (h->step & 1) ? psm::LAYOUT_SWAPPED : psm::LAYOUT_NATURAL;
 }
 
@@ -354,7 +360,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tensor maps of PDF buffer `buf` as a (x, y, z, slot) tensor.
-bool encode_maps(const psm_solver* h, void* buf, psm::TmaMaps& m) {
+bool encode_maps(const psm_solver* h, void* buf, BufMaps& m) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   CUtensorMapDataType dt = h->lat.storage == PSM_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -622,6 +628,38 @@ int psm_get_state(psm_handle h, double* f) {
   return rc;
 }
 
+int psm_get_cells(psm_handle h, const int64_t* cells, int64_t n, double* f) {
+  if (!valid_handle(h) || (n > 0 && (!cells || !f))) return fail(PSM_ERR_ARG, "psm_get_cells: NULL argument");
+  if (n < 0) return fail(PSM_ERR_ARG, "psm_get_cells: n must be >= 0");
+  if (n == 0) return PSM_OK;
+  std::vector<long long> hc((size_t)n);
+  PSM_CUDA(cudaMemcpy(hc.data(), cells, sizeof(long long) * (size_t)n, cudaMemcpyDefault), "cell list read");
+  for (long long c : hc)
+    if (c < 0 || c >= h->g.ncell) return fail(PSM_ERR_ARG, "psm_get_cells: cell index %lld out of range", c);
+  long long* dc = nullptr;
+  double* dout = nullptr;
+  PSM_CUDA(cudaMalloc(&dc, sizeof(long long) * (size_t)n), "cell list allocation");
+  cudaError_t e = cudaMalloc(&dout, sizeof(double) * (size_t)n * h->Q);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dc, hc.data(), sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    IoParams p;
+    io_base(h, p);
+    switch (h->lat.storage) {
+      case PSM_FP64: e = psm::launch_get_cells_fp64(h->Q, p, dc, n, dout, h->stream); break;
+      case PSM_FP32: e = psm::launch_get_cells_fp32(h->Q, p, dc, n, dout, h->stream); break;
+      case PSM_FP16_SHIFTED: e = psm::launch_get_cells_fp16(h->Q, p, dc, n, dout, h->stream); break;
+      default: e = psm::launch_get_cells_bf16(h->Q, p, dc, n, dout, h->stream); break;
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(f, dout, sizeof(double) * (size_t)n * h->Q, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(dc);
+  cudaFree(dout);
+  if (e != cudaSuccess) return cuda_fail(e, "psm_get_cells");
+  return PSM_OK;
+}
+
 int psm_get_macroscopic(psm_handle h, double* rho, double* u) {
   if (!valid_handle(h) || !rho || !u) return fail(PSM_ERR_ARG, "psm_get_macroscopic: NULL argument");
   const int planes = chunk_planes(h, sizeof(double) * 4);
@@ -764,7 +802,14 @@ int psm_step(psm_handle h, int n) {
       p.f = h->buf[0];
       p.f_dst = nullptr;
     }
-    cudaError_t e = use_tma ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, h->maps[src], h->stream)
+    psm::TmaMaps tm;
+    if (use_tma) {
+      const int dsti = h->lat.streaming == PSM_STREAM_TWO_GRID ? (src ^ 1) : 0;
+      tm.rowq = h->maps[src].rowq;
+      tm.row1 = h->maps[src].row1;
+      tm.dstq = h->maps[dsti].rowq;
+    }
+    cudaError_t e = use_tma ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, tm, h->stream)
                             : psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     if (h->lat.streaming == PSM_STREAM_TWO_GRID) h->cur ^= 1;
@@ -907,12 +952,15 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
       for (int b = 0; b < nb; ++b) sp.body[b] = dev_body(h, b, n);
       sp.f = slots[(size_t)(n - ns)];
       sp.f_dst = slots[(size_t)(n - ns + 1)];
-      e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, sp, st);
+      // slot 0 holds the checkpoint: natural layout (AA, even step) or pull layout (two grids)
+      const int mode = (n == ns && h->lat.streaming == PSM_STREAM_AA) ? psm::MODE_NAT2PULL : psm::MODE_TG;
+      e = psm::launch_step(h->lat.storage, h->Q, mode, sp, st);
     }
     // adjoint steps ne-1 .. ns
     for (int64_t n = ne - 1; n >= ns && e == cudaSuccess; --n) {
       for (int b = 0; b < nb; ++b) ap.body[b] = dev_body(h, b, n);
       ap.f = slots[(size_t)(n - ns)];
+      ap.f_layout = (n == ns && h->lat.streaming == PSM_STREAM_AA) ? psm::LAYOUT_NATURAL : psm::LAYOUT_PULL;
       ap.lam_in = la;
       ap.lam_out = lb;
       ap.w = wdev + (size_t)(n - h->rec_n0) * nb * 6;

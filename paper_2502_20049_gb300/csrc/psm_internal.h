@@ -13,15 +13,22 @@ namespace psm {
 enum Storage { ST_FP64 = PSM_FP64, ST_FP32 = PSM_FP32, ST_FP16 = PSM_FP16_SHIFTED, ST_BF16 = PSM_BF16_SHIFTED };
 
 // Access pattern of one step kernel.
-//   MODE_TG      : read own cell slot i (natural), write slot i of x + c_i in
-//                  the second buffer (two grids, push);
-//   MODE_AA_EVEN : read own slot i (natural), write own slot opp(i) (swapped);
-//   MODE_AA_ODD  : read slot opp(i) of x - c_i (swapped), write slot i of
-//                  x + c_i (natural).
-enum Mode { MODE_TG = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
+//   MODE_TG       : two grids, pull: read slot i of x - c_i (pull layout),
+//                   write own slot i of the other buffer (pull layout);
+//   MODE_AA_EVEN  : read own slot i (natural), write own slot opp(i) (swapped);
+//   MODE_AA_ODD   : read slot opp(i) of x - c_i (swapped), write slot i of
+//                   x + c_i (natural);
+//   MODE_NAT2PULL : read own slot i (natural), write own slot i of the other
+//                   buffer (pull layout) -- restarts a two-grid sequence from
+//                   a natural-layout checkpoint.
+enum Mode { MODE_TG = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2, MODE_NAT2PULL = 3 };
 
-// Layout a state is stored in, for import / export kernels.
-enum Layout { LAYOUT_NATURAL = 0, LAYOUT_SWAPPED = 1 };
+// Layout a state is stored in.  Pre-collision f_i(x) sits at
+//   NATURAL: slot i of x;  SWAPPED: slot opp(i) of x - c_i;
+//   PULL:    slot i of x - c_i  (post-collision values not yet streamed).
+// Populations whose upstream cell x - c_i lies in a ghost plane are not
+// stored in any layout: they take the ghost value.
+enum Layout { LAYOUT_NATURAL = 0, LAYOUT_SWAPPED = 1, LAYOUT_PULL = 2 };
 
 // One body as the kernels see it at one step.
 struct DevBody {
@@ -86,11 +93,12 @@ struct StepParams {
   ConstT<double> cd;     // constants for FP64 arithmetic
 };
 
-// Tensor maps of one PDF buffer viewed as a 4-D tensor (x, y, z, slot):
-// rowq = box (TX, 1, 1, Q) (a tile row of every slot), row1 = box (TX, 1, 1, 1).
+// Tensor maps of the PDF buffers viewed as 4-D tensors (x, y, z, slot) for one
+// launch of the TMA step kernel.
 struct TmaMaps {
-  CUtensorMap rowq;
-  CUtensorMap row1;
+  CUtensorMap rowq;  // source buffer, box (TX, 1, 1, Q)
+  CUtensorMap row1;  // source buffer, box (TX, 1, 1, 1)
+  CUtensorMap dstq;  // destination buffer (TMA stores), box (TX, 1, 1, Q)
 };
 
 // Parameters of the import / export / reduction kernels.
@@ -154,7 +162,9 @@ cudaError_t launch_remap(const RemapParams& p, cudaStream_t st);
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_macro_##NAME(int Q, const IoParams& p, cudaStream_t st);             \
-  cudaError_t launch_mass_##NAME(int Q, const IoParams& p, int blocks, cudaStream_t st);
+  cudaError_t launch_mass_##NAME(int Q, const IoParams& p, int blocks, cudaStream_t st);  \
+  cudaError_t launch_get_cells_##NAME(int Q, const IoParams& p, const long long* cells, long long n, double* out, \
+                                      cudaStream_t st);
 
 PSM_DECLARE_STORAGE(fp64)
 PSM_DECLARE_STORAGE(fp32)

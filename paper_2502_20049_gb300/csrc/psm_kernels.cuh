@@ -316,21 +316,36 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int 
   solid_cell = Bw != T(0);
   if (!solid_cell) {
     // ---- pure fluid: f* = f + Omega^F ----
+    // Per opposite pair (i, j), c_j = -c_i, the shifted equilibrium splits into
+    //   even = w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)) = A_w + K_w (c.u)^2,
+    //   odd  = 3 w rho (c.u),  f^eq_i = even + odd,  f^eq_j = even - odd,
+    // with A_w, K_w, C_w = 3 w rho computed once per weight class.
+    const T omp = om_a + om_b, omm = om_a - om_b;  // omega+ and omega- (BGK: both 1/tau)
+    const T base = drho - T(1.5) * rho * uu;
     {
-      const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
-      f[0] = f[0] - (om_a + om_b) * n0;
+      const T n0 = f[0] - T(lat_w<Q>(0)) * base;
+      f[0] = f[0] - omp * n0;
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
       const int j = i + 1;
-      const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
-      const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
+      const T w = T(lat_w<Q>(i));
+      T cu = 0;
+      if (lat_cx(i)) cu += T(lat_cx(i)) * ux;
+      if (lat_cy(i)) cu += T(lat_cy(i)) * uy;
+      if (lat_cz(i)) cu += T(lat_cz(i)) * uz;
+      const T even = w * base + (T(4.5) * w * rho) * (cu * cu);
+      const T odd = (T(3) * w * rho) * cu;
       if (TRT) {
-        f[i] = f[i] - om_a * ni - om_b * nj;
-        f[j] = f[j] - om_a * nj - om_b * ni;
+        // f* = f - omega+ (f+ - even) - omega- (f- - odd)
+        const T np = T(0.5) * (f[i] + f[j]) - even;
+        const T nm = T(0.5) * (f[i] - f[j]) - odd;
+        const T a = omp * np, b = omm * nm;
+        f[i] = f[i] - a - b;
+        f[j] = f[j] - a + b;
       } else {
-        f[i] = f[i] - om_a * ni;
-        f[j] = f[j] - om_a * nj;
+        f[i] = f[i] + om_a * ((even + odd) - f[i]);
+        f[j] = f[j] + om_a * ((even - odd) - f[j]);
       }
     }
     return;
@@ -412,7 +427,11 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int 
   }
 }
 
-// Streamed store (Eq. 1) of one cell's post-collision PDFs.
+// Store of one cell's post-collision PDFs (Eq. 1 with the streaming split
+// between this store and the next step's load):
+//   AA even        own cell, slot opp(i);
+//   AA odd         cell x + c_i, slot i (dropped where x + c_i is outside);
+//   TG / NAT2PULL  own cell, slot i of the other buffer (the next step pulls).
 template <class S, int Q, int MODE, class T>
 __device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Nbr& nbr, unsigned cell, const T (&f)[Q]) {
 #pragma unroll
@@ -420,9 +439,10 @@ __device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Nbr
     const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
     if (MODE == MODE_AA_EVEN) {
       Store<S>::st(buf + (long long)lat_opp(i) * N + cell, f[i]);
-    } else if (!nbr.to_ghost(cz)) {
-      S* base = (MODE == MODE_TG) ? dst : buf;
-      Store<S>::st(base + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
+    } else if (MODE == MODE_AA_ODD) {
+      if (!nbr.to_ghost(cz)) Store<S>::st(buf + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
+    } else {
+      Store<S>::st(dst + (long long)i * N + cell, f[i]);
     }
   }
 }
@@ -493,8 +513,10 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
         if (nbr.from_ghost(cz)) {
           f[i] = cst<T>(p).ghost[i];
-        } else if (MODE == MODE_AA_ODD) {
-          f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
+        } else if (MODE == MODE_AA_ODD || MODE == MODE_TG) {
+          // pull: population i of x was stored by x - c_i (slot opp(i) in the AA odd step)
+          const int slot = MODE == MODE_AA_ODD ? lat_opp(i) : i;
+          f[i] = Store<S>::ld(buf + (long long)slot * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
         } else {
           f[i] = Store<S>::ld(buf + (long long)i * N + cell);
         }
@@ -560,52 +582,93 @@ __device__ __forceinline__ void bulk_load_16(void* dst, const void* src, unsigne
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// Shared-memory layout of one stage (bytes), 128-byte aligned row boxes.
+__device__ __forceinline__ void tma_store_4d(const void* map, int c0, int c1, int c2, int c3, const void* src) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+#ifndef PSM_TMA_OUT_BUFS
+#define PSM_TMA_OUT_BUFS 2
+#endif
+// 1: the two-grid and AA even steps write their tiles back with TMA tensor stores
+#ifndef PSM_TMA_STORE
+#define PSM_TMA_STORE 1
+#endif
+
+// Shared-memory layout of the TMA step kernel (bytes; every box 128-byte aligned):
+// [barriers 128 B] [PSM_TMA_STAGES input stages] [PSM_TMA_OUT_BUFS output tiles].
+//   input, own-row modes (AA even): per tile row one [Q][TX] box of all slots;
+//   input, pull modes (TG, AA odd): per tile row and direction one [TX] row plus
+//     two 16-byte x-edge chunks;
+//   output (TG, AA even): per tile row one [Q][TX] box, written back by one TMA
+//     tensor store.
 template <class S, int Q, int MODE>
 struct TmaLayout {
+  static constexpr bool LOAD_OWN = MODE == MODE_AA_EVEN;
+  static constexpr bool STORE_TMA = PSM_TMA_STORE && (MODE == MODE_AA_EVEN || MODE == MODE_TG);
   static constexpr int EP = 16 / (int)sizeof(S);  // elements per 16-byte edge chunk
-  __host__ __device__ static int row_bytes(int tx) { return ((tx * (int)sizeof(S) + 127) / 128) * 128; }
-  // own-row modes: one [Q][TX] box per tile row; odd step: one [TX] box per row and direction
-  __host__ __device__ static int box_bytes(int tx) {
-    return MODE == MODE_AA_ODD ? row_bytes(tx) : ((Q * tx * (int)sizeof(S) + 127) / 128) * 128;
-  }
+  __host__ __device__ static int r128(int b) { return ((b + 127) / 128) * 128; }
+  __host__ __device__ static int row_bytes(int tx) { return r128(tx * (int)sizeof(S)); }
+  __host__ __device__ static int box_bytes(int tx) { return r128(Q * tx * (int)sizeof(S)); }
   __host__ __device__ static int main_bytes(int tx, int ty) {
-    return MODE == MODE_AA_ODD ? ty * Q * row_bytes(tx) : ty * box_bytes(tx);
+    return LOAD_OWN ? ty * box_bytes(tx) : ty * Q * row_bytes(tx);
   }
-  __host__ __device__ static int edge_bytes(int ty) { return MODE == MODE_AA_ODD ? ty * Q * 2 * 16 : 0; }
-  __host__ __device__ static int stage_bytes(int tx, int ty) {
-    return ((main_bytes(tx, ty) + edge_bytes(ty) + 127) / 128) * 128;
-  }
+  __host__ __device__ static int edge_bytes(int ty) { return LOAD_OWN ? 0 : ty * Q * 2 * 16; }
+  __host__ __device__ static int stage_bytes(int tx, int ty) { return r128(main_bytes(tx, ty) + edge_bytes(ty)); }
+  __host__ __device__ static int out_bytes(int tx, int ty) { return STORE_TMA ? ty * box_bytes(tx) : 0; }
   // + 128 B of barriers, + 128 B of alignment slack
-  __host__ __device__ static int smem_bytes(int tx, int ty) { return 256 + PSM_TMA_STAGES * stage_bytes(tx, ty); }
+  __host__ __device__ static int smem_bytes(int tx, int ty) {
+    return 256 + PSM_TMA_STAGES * stage_bytes(tx, ty) + PSM_TMA_OUT_BUFS * out_bytes(tx, ty);
+  }
 };
 
+// ---------------------------------------------------------------------------
+// TMA-staged step kernel.  Shapes: nx % TX == 0 with TX = min(256, nx) (and
+// 256 % nx == 0 when nx < 256), TY = 256 / TX rows per tile, ny % TY == 0, and
+// TX * sizeof(S) a multiple of 16 bytes.  Persistent blocks stride over tiles.
+// Warp 0 keeps PSM_TMA_STAGES tiles of pre-collision rows in flight in shared
+// memory (cp.async.bulk.tensor row boxes; in the pull modes one row per
+// direction plus 16-byte cp.async.bulk edge chunks for x - c_x) while all
+// threads collide the oldest staged tile from shared memory.  In the two-grid
+// and AA even steps the post-collision tile is written to shared memory and
+// back to global memory by one TMA tensor store per tile row; the AA odd step
+// stores to x + c_i with st.global.
+// ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int TRT>
 __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
     k_step_tma(const __grid_constant__ StepParams p, const __grid_constant__ TmaMaps maps) {
   using T = typename Store<S>::T;
   using L = TmaLayout<S, Q, MODE>;
   constexpr int NST = PSM_TMA_STAGES;
+  constexpr int NOUT = PSM_TMA_OUT_BUFS;
   constexpr int EP = L::EP;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
   __shared__ int s_abort;
-  __shared__ int s_issued[NST];  // loads issued per stage (thread 0 only)
+  __shared__ int s_issued[NST];  // loads issued per stage (warp 0, lane 0)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // dynamic shared memory is only guaranteed 16-byte alignment: align by hand
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(base);  // NST barriers in the first 128 B
-  unsigned char* stages = base + 128;
-
   const int nb = p.nbodies;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
   const int TX = p.t.tx, TY = p.t.ty;
   const int SB = L::stage_bytes(TX, TY);
   const int RB = L::row_bytes(TX), BB = L::box_bytes(TX), MB = L::main_bytes(TX, TY);
+  unsigned char* stages = base + 128;
+  unsigned char* outs = stages + NST * SB;
+  const int OB = L::out_bytes(TX, TY);
   const long long N = p.g.ncell;
   S* __restrict__ buf = static_cast<S*>(p.f);
   S* __restrict__ dst = static_cast<S*>(p.f_dst);
-  const void* map_rows = (MODE == MODE_AA_ODD) ? (const void*)&maps.row1 : (const void*)&maps.rowq;
+  const void* map_in = L::LOAD_OWN ? (const void*)&maps.rowq : (const void*)&maps.row1;
   const int ntiles = (int)p.t.ntiles;
 
   if (threadIdx.x == 0) {
@@ -618,11 +681,8 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   }
   __syncthreads();
 
-  // producer: stage the pre-collision rows of tile `tile` into stage `s`
-  // producer: all 32 lanes of warp 0 stage the pre-collision rows of tile
-  // `tile` into stage `s`, one copy job per lane (one row box of all slots per
-  // tile row in the own-cell modes; one row of slot opp(i) plus its 16-byte
-  // x-edge chunk per tile row and direction in the AA odd step)
+  // producer: the 32 lanes of warp 0 stage the pre-collision rows of tile
+  // `tile` into stage `s`, one copy job per lane
   auto produce = [&](int tile, int s) {
     int tx0, y0, z;
     {
@@ -636,12 +696,12 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     unsigned char* st = stages + (long long)s * SB;
     unsigned long long* bar = &bars[s];
     fence_proxy_async();
-    const int njobs = (MODE == MODE_AA_ODD) ? TY * Q : TY;
+    const int njobs = L::LOAD_OWN ? TY : TY * Q;
     for (int job = lane; job < njobs; job += 32) {
-      if (MODE != MODE_AA_ODD) {
+      if (L::LOAD_OWN) {
         const int r = job;
         mbar_expect_tx(bar, (unsigned)(Q * TX * (int)sizeof(S)));
-        tma_load_4d(st + r * BB, map_rows, tx0, y0 + r, z, 0, bar);
+        tma_load_4d(st + r * BB, map_in, tx0, y0 + r, z, 0, bar);
       } else {
         const int r = job / Q, i = job % Q;
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
@@ -652,9 +712,9 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         }
         int ys = y0 + r - cy;
         ys = ys < 0 ? ys + p.g.ny : (ys >= p.g.ny ? ys - p.g.ny : ys);
-        const int slot = lat_opp(i);
+        const int slot = MODE == MODE_AA_ODD ? lat_opp(i) : i;
         mbar_expect_tx(bar, (unsigned)(TX * (int)sizeof(S)));
-        tma_load_4d(st + (r * Q + i) * RB, map_rows, tx0, ys, zs, slot, bar);
+        tma_load_4d(st + (r * Q + i) * RB, map_in, tx0, ys, zs, slot, bar);
         if (cx != 0) {
           // cx = +1 reads x0 - 1 (left chunk), cx = -1 reads x0 + TX (right chunk), wrapped in x
           const int xe = cx > 0 ? (tx0 == 0 ? p.g.nx - EP : tx0 - EP) : (tx0 + TX == p.g.nx ? 0 : tx0 + TX);
@@ -698,26 +758,28 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     if (s_abort) {
       if (threadIdx.x == 0) {
         if (p.err) atomicExch(p.err, 1);
-        // let the copies already issued land before the block's shared memory is released
+        // let the copies already issued finish before the block's shared memory is released
         for (int s2 = 0; s2 < NST; ++s2) {
           if (s_issued[s2] == 0) continue;
           const unsigned last = (unsigned)((s_issued[s2] - 1) & 1);
           for (unsigned it = 0; it < (1u << 20) && !mbar_try_wait(&bars[s2], last); ++it) {
           }
         }
+        if (L::STORE_TMA) bulk_wait_all();
       }
       __syncthreads();
       return;
     }
-    int x, y, z;
+    int tx0, y0, z;
     {
       const int tx = tile % p.t.ntx;
       const int r = tile / p.t.ntx;
       const int ty = r % p.t.nty;
       z = r / p.t.nty;
-      x = tx * TX + lx;
-      y = ty * TY + ly;
+      tx0 = tx * TX;
+      y0 = ty * TY;
     }
+    const int x = tx0 + lx, y = y0 + ly;
     const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
     Nbr nbr;
     nbr.init(p.g, x, y, z);
@@ -728,7 +790,7 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
       const int cx = lat_cx(i), cz = lat_cz(i);
       if (nbr.from_ghost(cz)) {
         f[i] = cst<T>(p).ghost[i];
-      } else if (MODE != MODE_AA_ODD) {
+      } else if (L::LOAD_OWN) {
         f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + ly * BB) + i * TX + lx);
       } else {
         const S* row = reinterpret_cast<const S*>(st + (ly * Q + i) * RB);
@@ -742,7 +804,10 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         }
       }
     }
-    __syncthreads();  // stage s fully read: warp 0 may refill it
+    // the output tile about to be written was last handed to a TMA store NOUT
+    // tiles ago: wait until that store has read it
+    if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_read<NOUT - 1>();
+    __syncthreads();  // stage s fully read (warp 0 may refill it); output tile free
     if (warp == 0) {
       const int next = tile + NST * gridDim.x;
       if (next < ntiles) produce(next, s);
@@ -751,9 +816,26 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     bool solid_cell = false;
     double ft[6] = {0, 0, 0, 0, 0, 0};
     psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
-    psm_store<S, Q, MODE>(buf, dst, N, nbr, cell, f);
+    if (L::STORE_TMA) {
+      unsigned char* ob = outs + (long long)(k % NOUT) * OB;
+      S* orow = reinterpret_cast<S*>(ob + ly * BB);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int slot = MODE == MODE_AA_EVEN ? lat_opp(i) : i;
+        Store<S>::st(orow + slot * TX + lx, f[i]);
+      }
+      fence_proxy_async();  // the generic-proxy writes above become visible to the TMA store
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int r = 0; r < TY; ++r) tma_store_4d(&maps.dstq, tx0, y0 + r, z, 0, ob + r * BB);
+        bulk_commit();
+      }
+    } else {
+      psm_store<S, Q, MODE>(buf, dst, N, nbr, cell, f);
+    }
     warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
   }
+  if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_all();
   if (nb == 0) return;
   block_ft_finish(s_ft, p);
 }
@@ -784,8 +866,9 @@ __device__ __forceinline__ void read_state(const IoParams& p, const S* buf, cons
   for (int i = 0; i < Q; ++i) {
     if (nbr.from_ghost(lat_cz(i))) {
       f[i] = T(p.ghost[i]);
-    } else if (p.layout == LAYOUT_SWAPPED) {
-      f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N +
+    } else if (p.layout != LAYOUT_NATURAL) {
+      const int slot = p.layout == LAYOUT_SWAPPED ? lat_opp(i) : i;
+      f[i] = Store<S>::ld(buf + (long long)slot * N +
                           (unsigned)((unsigned)cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i))));
     } else {
       f[i] = Store<S>::ld(buf + (long long)i * N + cell);
@@ -817,8 +900,8 @@ __global__ void k_import(const __grid_constant__ IoParams p) {
       if (nbr.from_ghost(lat_cz(i))) continue;  // such populations always read the ghost value
       long long dstc;
       int slot;
-      if (p.layout == LAYOUT_SWAPPED) {
-        slot = lat_opp(i);
+      if (p.layout != LAYOUT_NATURAL) {
+        slot = p.layout == LAYOUT_SWAPPED ? lat_opp(i) : i;
         dstc = (unsigned)((unsigned)cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i)));
       } else {
         slot = i;
@@ -844,6 +927,26 @@ __global__ void k_export(const __grid_constant__ IoParams p) {
     T f[Q];
     read_state<S, Q>(p, buf, nbr, cell, f);
     for (int i = 0; i < Q; ++i) p.f_out[(long long)i * nchunk + idx] = (double)f[i] + lat_w<Q>(i) * p.rho0;
+  }
+}
+
+// Natural, unshifted FP64 PDFs of listed cells: out[k][Q].
+template <class S, int Q>
+__global__ void k_get_cells(const __grid_constant__ IoParams p, const long long* cells, long long n, double* out) {
+  using T = typename Store<S>::T;
+  const S* buf = static_cast<const S*>(p.f);
+  const long long plane = (long long)p.g.nx * p.g.ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long cell = cells[k];
+    if (cell < 0 || cell >= p.g.ncell) continue;  // the host validates; never read out of bounds
+    const int z = (int)(cell / plane);
+    const long long r = cell % plane;
+    const int y = (int)(r / p.g.nx), x = (int)(r % p.g.nx);
+    Nbr nbr;
+    nbr.init(p.g, x, y, z);
+    T f[Q];
+    read_state<S, Q>(p, buf, nbr, cell, f);
+    for (int i = 0; i < Q; ++i) out[k * Q + i] = (double)f[i] + lat_w<Q>(i) * p.rho0;
   }
 }
 
@@ -974,6 +1077,8 @@ int step_blocks_t() {
 template <class S, int Q>
 cudaError_t launch_step_q(int mode, int trt, const StepParams& p, cudaStream_t st) {
   if (mode == MODE_TG) return trt ? launch_step_t<S, Q, MODE_TG, 1>(p, st) : launch_step_t<S, Q, MODE_TG, 0>(p, st);
+  if (mode == MODE_NAT2PULL)
+    return trt ? launch_step_t<S, Q, MODE_NAT2PULL, 1>(p, st) : launch_step_t<S, Q, MODE_NAT2PULL, 0>(p, st);
   if (mode == MODE_AA_EVEN)
     return trt ? launch_step_t<S, Q, MODE_AA_EVEN, 1>(p, st) : launch_step_t<S, Q, MODE_AA_EVEN, 0>(p, st);
   return trt ? launch_step_t<S, Q, MODE_AA_ODD, 1>(p, st) : launch_step_t<S, Q, MODE_AA_ODD, 0>(p, st);
@@ -1024,6 +1129,13 @@ inline int io_grid(const IoParams& p) {
   cudaError_t launch_macro_##NAME(int Q, const IoParams& p, cudaStream_t st) {                          \
     if (Q == 19) k_macro<S, 19><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                                 \
     else k_macro<S, 27><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                                         \
+    return cudaGetLastError();                                                                          \
+  }                                                                                                     \
+  cudaError_t launch_get_cells_##NAME(int Q, const IoParams& p, const long long* cells, long long n,     \
+                                      double* out, cudaStream_t st) {                                  \
+    const int b = (int)((n + PSM_THREADS - 1) / PSM_THREADS < 1024 ? (n + PSM_THREADS - 1) / PSM_THREADS : 1024); \
+    if (Q == 19) k_get_cells<S, 19><<<b < 1 ? 1 : b, PSM_THREADS, 0, st>>>(p, cells, n, out);         \
+    else k_get_cells<S, 27><<<b < 1 ? 1 : b, PSM_THREADS, 0, st>>>(p, cells, n, out);                 \
     return cudaGetLastError();                                                                          \
   }                                                                                                     \
   cudaError_t launch_mass_##NAME(int Q, const IoParams& p, int blocks, cudaStream_t st) {               \

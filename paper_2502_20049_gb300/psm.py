@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
                 "psm_set_state": (i, [H, vp]),
                 "psm_get_state": (i, [H, vp]),
                 "psm_get_macroscopic": (i, [H, vp, vp]),
+                "psm_get_cells": (i, [H, vp, i64, vp]),
                 "psm_get_eps": (i, [H, vp]),
                 "psm_set_geometry": (i, [H, i, P(GeomField), P(d), P(d), P(d), P(d)]),
                 "psm_num_bodies": (i, [H, P(i)]),
@@ -363,6 +364,14 @@ class Solver:
             f = np.ascontiguousarray(f, dtype=np.float64)
             p, keep = _ptr(f, np.float64, int(np.prod(self.shape)))
         check(lib().psm_set_state(self._h, p))
+
+    def get_cells(self, cells):
+        """[len(cells), Q] natural FP64 PDFs of flat cell indices (library order)."""
+        cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+        out = np.zeros((cells.size, self.cfg.Q))
+        check(lib().psm_get_cells(self._h, ctypes.c_void_p(cells.ctypes.data), cells.size,
+                                  ctypes.c_void_p(out.ctypes.data)))
+        return out
 
     def macroscopic(self):
         c = self.cfg
