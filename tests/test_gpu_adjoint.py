@@ -95,9 +95,12 @@ def test_adjoint_reduced_precision_matches_tangent_linear(storage, tol):
 
 def fd_richardson(J_of, n, c, h):
     """Central difference at h and h/2 combined by Richardson extrapolation
-    (truncation error O(h^4)): the solid fraction enters through B(eps) with
-    B' up to (1 + t) / t for t = tau - 1/2, so plain O(h^2) differences at
-    h = 1e-4 are visibly biased at fully solid cells."""
+    (truncation error O(h^4)).  The solid fraction enters through B(eps) with
+    B' = (1 + t) / t at eps = 1 (t = tau - 1/2: 21 at tau = 0.55), and B > 1
+    makes a fully solid cell anti-dissipative, so J(delta) is strongly curved
+    there: at h = 1e-4 even Richardson differences are biased by ~1 % and at
+    h = 1e-3 the perturbed run can blow up.  The checks use h = 1e-6 in FP64
+    (the differences converge to the adjoint as h shrinks)."""
     def D(hh):
         d = np.zeros(n, np.float32)
         d[c] = hh
@@ -132,7 +135,7 @@ def J_fp64(case):
 
 
 def test_adjoint_fp64_vs_central_fd_16_cells():
-    """GPU FP64 adjoint vs FP64 central differences (h = 1e-4, Richardson) of
+    """GPU FP64 adjoint vs FP64 central differences (h = 1e-6, Richardson) of
     the GPU forward on 16 seeded cells of the body's swept region."""
     case = W.c4_adjoint(n=32, steps=48).with_(storage="fp64")
     case.bodies[0].omega = (0.0, 0.0, 0.01)
@@ -140,7 +143,7 @@ def test_adjoint_fp64_vs_central_fd_16_cells():
     J_of = J_fp64(case)
     scale = np.abs(ge).max()
     for c in swept_cells(case):
-        fd = fd_richardson(J_of, case.cells, c, 1e-4)
+        fd = fd_richardson(J_of, case.cells, c, 1e-6)
         g = ge.reshape(-1)[c]
         assert abs(g - fd) <= 1e-5 * abs(fd) + 1e-7 * scale, (c, g, fd)
 
@@ -148,12 +151,11 @@ def test_adjoint_fp64_vs_central_fd_16_cells():
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 def test_adjoint_c4_full_vs_fp64_fd(storage):
     """The adjoint workload at full size: 128^3, 512 steps, checkpoint every 64
-    steps, TRT tau 0.55, against FP64 central differences (h = 1e-4,
+    steps, TRT tau 0.55, against FP64 central differences (h = 1e-6,
     Richardson) of the GPU forward on 16 seeded cells of the swept region.
-    FP64 adjoint: 1e-5 relative per cell.  FP32 forward and adjoint: the
-    gradient is taken on the FP32 trajectory, which drifts from the FP64 one
-    over 512 steps of this weakly damped flow; the bar is 1e-2 of the largest
-    gradient component (the relative error of each cell is printed)."""
+    FP64 adjoint: 1e-5 relative per cell.  FP32 forward and adjoint (the
+    gradient of the FP32 trajectory): 1e-2 relative per cell (the relative
+    error of each cell is printed)."""
     case = W.c4_adjoint().with_(storage=storage)
     J, ge, gw, gu = gpu_grad(case, K=64)
     cells = swept_cells(case, every=64)
@@ -161,7 +163,7 @@ def test_adjoint_c4_full_vs_fp64_fd(storage):
     scale = np.abs(ge).max()
     worst_rel, worst_scaled = 0.0, 0.0
     for c in cells:
-        fd = fd_richardson(J_of, case.cells, c, 1e-4)
+        fd = fd_richardson(J_of, case.cells, c, 1e-6)
         g = ge.reshape(-1)[c]
         rel = abs(g - fd) / max(abs(fd), 1e-300)
         print(f"{storage} cell {c}: adjoint {g:.9e} fd {fd:.9e} rel {rel:.3e} (max |grad| {scale:.3e})")
@@ -172,7 +174,7 @@ def test_adjoint_c4_full_vs_fp64_fd(storage):
     if storage == "fp64":
         assert worst_rel <= 1e-5 and worst_scaled <= 1e-6
     else:
-        assert worst_scaled <= 1e-2
+        assert worst_rel <= 1e-2 and worst_scaled <= 1e-3
 
 
 def test_autograd_function_fp64():
