@@ -27,8 +27,7 @@ namespace psm {
 struct AdjParams {
   Grid3 g;
   Tiling t;
-  const void* f;        // f^n, storage S, shifted, in layout f_layout
-  int f_layout;         // LAYOUT_NATURAL or LAYOUT_PULL
+  const void* f;        // f^n, natural layout, storage S, shifted
   const void* lam_in;   // lambda^{n+1}, [Q][ncell] in T
   void* lam_out;        // lambda^n
   double* grad;         // [ncell]: += dJ/d delta (FP64 accumulator)
@@ -99,7 +98,6 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
       for (int i = 0; i < Q; ++i) {
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
         if (nbr.from_ghost(cz)) f[i] = C.ghost[i];
-        else if (p.f_layout == LAYOUT_PULL) f[i] = Store<S>::ld(fb + (long long)i * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
         else f[i] = Store<S>::ld(fb + (long long)i * N + cell);
         mu[i] = nbr.to_ghost(cz) ? T(0) : lin[(long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz))];
       }

@@ -291,7 +291,7 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
 }
 
 int layout_of(const psm_solver* h) {
-  if (h->lat.streaming == PSM_STREAM_TWO_GRID) return psm::LAYOUT_PULL;
+  if (h->lat.streaming == PSM_STREAM_TWO_GRID) return psm::LAYOUT_NATURAL;
   return (h->step & 1) ? psm::LAYOUT_SWAPPED : psm::LAYOUT_NATURAL;
 }
 
@@ -327,6 +327,12 @@ int import_uniform(psm_solver* h, double rho, const double u[3]) {
 }
 
 bool valid_handle(psm_handle h) { return h != nullptr; }
+
+// 1: the AA odd step (per-direction rows) uses plain global loads even where
+// the TMA-staged kernel is selected.
+#ifndef PSM_AA_ODD_PLAIN
+#define PSM_AA_ODD_PLAIN 0
+#endif
 
 // TMA shape rules (see k_step_tma): TX = min(256, nx), nx % TX == 0,
 // 256 % nx == 0 if nx < 256, TY = 256 / TX divides ny, rows of 16-byte
@@ -802,14 +808,17 @@ int psm_step(psm_handle h, int n) {
       p.f = h->buf[0];
       p.f_dst = nullptr;
     }
+    // the AA odd step may run with plain loads while the other steps use TMA staging
+    const bool tma_now = use_tma && !(PSM_AA_ODD_PLAIN && mode == psm::MODE_AA_ODD);
+    p.t = tma_now ? h->tma_tiling : h->tiling;
     psm::TmaMaps tm;
-    if (use_tma) {
+    if (tma_now) {
       const int dsti = h->lat.streaming == PSM_STREAM_TWO_GRID ? (src ^ 1) : 0;
       tm.rowq = h->maps[src].rowq;
       tm.row1 = h->maps[src].row1;
       tm.dstq = h->maps[dsti].rowq;
     }
-    cudaError_t e = use_tma ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, tm, h->stream)
+    cudaError_t e = tma_now ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, tm, h->stream)
                             : psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     if (h->lat.streaming == PSM_STREAM_TWO_GRID) h->cur ^= 1;
@@ -952,15 +961,12 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
       for (int b = 0; b < nb; ++b) sp.body[b] = dev_body(h, b, n);
       sp.f = slots[(size_t)(n - ns)];
       sp.f_dst = slots[(size_t)(n - ns + 1)];
-      // slot 0 holds the checkpoint: natural layout (AA, even step) or pull layout (two grids)
-      const int mode = (n == ns && h->lat.streaming == PSM_STREAM_AA) ? psm::MODE_NAT2PULL : psm::MODE_TG;
-      e = psm::launch_step(h->lat.storage, h->Q, mode, sp, st);
+      e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, sp, st);
     }
     // adjoint steps ne-1 .. ns
     for (int64_t n = ne - 1; n >= ns && e == cudaSuccess; --n) {
       for (int b = 0; b < nb; ++b) ap.body[b] = dev_body(h, b, n);
       ap.f = slots[(size_t)(n - ns)];
-      ap.f_layout = (n == ns && h->lat.streaming == PSM_STREAM_AA) ? psm::LAYOUT_NATURAL : psm::LAYOUT_PULL;
       ap.lam_in = la;
       ap.lam_out = lb;
       ap.w = wdev + (size_t)(n - h->rec_n0) * nb * 6;

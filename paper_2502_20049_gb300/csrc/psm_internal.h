@@ -13,22 +13,18 @@ namespace psm {
 enum Storage { ST_FP64 = PSM_FP64, ST_FP32 = PSM_FP32, ST_FP16 = PSM_FP16_SHIFTED, ST_BF16 = PSM_BF16_SHIFTED };
 
 // Access pattern of one step kernel.
-//   MODE_TG       : two grids, pull: read slot i of x - c_i (pull layout),
-//                   write own slot i of the other buffer (pull layout);
-//   MODE_AA_EVEN  : read own slot i (natural), write own slot opp(i) (swapped);
-//   MODE_AA_ODD   : read slot opp(i) of x - c_i (swapped), write slot i of
-//                   x + c_i (natural);
-//   MODE_NAT2PULL : read own slot i (natural), write own slot i of the other
-//                   buffer (pull layout) -- restarts a two-grid sequence from
-//                   a natural-layout checkpoint.
-enum Mode { MODE_TG = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2, MODE_NAT2PULL = 3 };
+//   MODE_TG      : two grids, push: read own slot i (natural), write slot i of
+//                  x + c_i in the other buffer (natural);
+//   MODE_AA_EVEN : read own slot i (natural), write own slot opp(i) (swapped);
+//   MODE_AA_ODD  : read slot opp(i) of x - c_i (swapped), write slot i of
+//                  x + c_i (natural).
+enum Mode { MODE_TG = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 
 // Layout a state is stored in.  Pre-collision f_i(x) sits at
-//   NATURAL: slot i of x;  SWAPPED: slot opp(i) of x - c_i;
-//   PULL:    slot i of x - c_i  (post-collision values not yet streamed).
+//   NATURAL: slot i of x;  SWAPPED: slot opp(i) of x - c_i.
 // Populations whose upstream cell x - c_i lies in a ghost plane are not
-// stored in any layout: they take the ghost value.
-enum Layout { LAYOUT_NATURAL = 0, LAYOUT_SWAPPED = 1, LAYOUT_PULL = 2 };
+// stored in either layout: they take the ghost value.
+enum Layout { LAYOUT_NATURAL = 0, LAYOUT_SWAPPED = 1 };
 
 // One body as the kernels see it at one step.
 struct DevBody {
@@ -98,7 +94,7 @@ struct StepParams {
 struct TmaMaps {
   CUtensorMap rowq;  // source buffer, box (TX, 1, 1, Q)
   CUtensorMap row1;  // source buffer, box (TX, 1, 1, 1)
-  CUtensorMap dstq;  // destination buffer (TMA stores), box (TX, 1, 1, Q)
+  CUtensorMap dstq;  // destination of the AA even step's TMA stores, box (TX, 1, 1, Q)
 };
 
 // Parameters of the import / export / reduction kernels.

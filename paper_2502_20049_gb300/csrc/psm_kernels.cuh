@@ -427,11 +427,11 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int 
   }
 }
 
-// Store of one cell's post-collision PDFs (Eq. 1 with the streaming split
-// between this store and the next step's load):
-//   AA even        own cell, slot opp(i);
-//   AA odd         cell x + c_i, slot i (dropped where x + c_i is outside);
-//   TG / NAT2PULL  own cell, slot i of the other buffer (the next step pulls).
+// Streamed store (Eq. 1) of one cell's post-collision PDFs:
+//   AA even  own cell, slot opp(i);
+//   AA odd   cell x + c_i, slot i;
+//   TG       cell x + c_i, slot i of the other buffer;
+// populations that leave the domain through a ghost plane are dropped.
 template <class S, int Q, int MODE, class T>
 __device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Nbr& nbr, unsigned cell, const T (&f)[Q]) {
 #pragma unroll
@@ -439,10 +439,9 @@ __device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Nbr
     const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
     if (MODE == MODE_AA_EVEN) {
       Store<S>::st(buf + (long long)lat_opp(i) * N + cell, f[i]);
-    } else if (MODE == MODE_AA_ODD) {
-      if (!nbr.to_ghost(cz)) Store<S>::st(buf + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
-    } else {
-      Store<S>::st(dst + (long long)i * N + cell, f[i]);
+    } else if (!nbr.to_ghost(cz)) {
+      S* base = (MODE == MODE_TG) ? dst : buf;
+      Store<S>::st(base + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
     }
   }
 }
@@ -513,10 +512,9 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
         if (nbr.from_ghost(cz)) {
           f[i] = cst<T>(p).ghost[i];
-        } else if (MODE == MODE_AA_ODD || MODE == MODE_TG) {
-          // pull: population i of x was stored by x - c_i (slot opp(i) in the AA odd step)
-          const int slot = MODE == MODE_AA_ODD ? lat_opp(i) : i;
-          f[i] = Store<S>::ld(buf + (long long)slot * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
+        } else if (MODE == MODE_AA_ODD) {
+          // population i of x was stored by x - c_i in slot opp(i) (AA even step)
+          f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
         } else {
           f[i] = Store<S>::ld(buf + (long long)i * N + cell);
         }
@@ -611,8 +609,8 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 //     tensor store.
 template <class S, int Q, int MODE>
 struct TmaLayout {
-  static constexpr bool LOAD_OWN = MODE == MODE_AA_EVEN;
-  static constexpr bool STORE_TMA = PSM_TMA_STORE && (MODE == MODE_AA_EVEN || MODE == MODE_TG);
+  static constexpr bool LOAD_OWN = MODE != MODE_AA_ODD;
+  static constexpr bool STORE_TMA = PSM_TMA_STORE && MODE == MODE_AA_EVEN;
   static constexpr int EP = 16 / (int)sizeof(S);  // elements per 16-byte edge chunk
   __host__ __device__ static int r128(int b) { return ((b + 127) / 128) * 128; }
   __host__ __device__ static int row_bytes(int tx) { return r128(tx * (int)sizeof(S)); }
@@ -712,7 +710,7 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         }
         int ys = y0 + r - cy;
         ys = ys < 0 ? ys + p.g.ny : (ys >= p.g.ny ? ys - p.g.ny : ys);
-        const int slot = MODE == MODE_AA_ODD ? lat_opp(i) : i;
+        const int slot = lat_opp(i);
         mbar_expect_tx(bar, (unsigned)(TX * (int)sizeof(S)));
         tma_load_4d(st + (r * Q + i) * RB, map_in, tx0, ys, zs, slot, bar);
         if (cx != 0) {
@@ -866,9 +864,8 @@ __device__ __forceinline__ void read_state(const IoParams& p, const S* buf, cons
   for (int i = 0; i < Q; ++i) {
     if (nbr.from_ghost(lat_cz(i))) {
       f[i] = T(p.ghost[i]);
-    } else if (p.layout != LAYOUT_NATURAL) {
-      const int slot = p.layout == LAYOUT_SWAPPED ? lat_opp(i) : i;
-      f[i] = Store<S>::ld(buf + (long long)slot * N +
+    } else if (p.layout == LAYOUT_SWAPPED) {
+      f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N +
                           (unsigned)((unsigned)cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i))));
     } else {
       f[i] = Store<S>::ld(buf + (long long)i * N + cell);
@@ -900,8 +897,8 @@ __global__ void k_import(const __grid_constant__ IoParams p) {
       if (nbr.from_ghost(lat_cz(i))) continue;  // such populations always read the ghost value
       long long dstc;
       int slot;
-      if (p.layout != LAYOUT_NATURAL) {
-        slot = p.layout == LAYOUT_SWAPPED ? lat_opp(i) : i;
+      if (p.layout == LAYOUT_SWAPPED) {
+        slot = lat_opp(i);
         dstc = (unsigned)((unsigned)cell + nbr.off(-lat_cx(i), -lat_cy(i), -lat_cz(i)));
       } else {
         slot = i;
@@ -1077,8 +1074,6 @@ int step_blocks_t() {
 template <class S, int Q>
 cudaError_t launch_step_q(int mode, int trt, const StepParams& p, cudaStream_t st) {
   if (mode == MODE_TG) return trt ? launch_step_t<S, Q, MODE_TG, 1>(p, st) : launch_step_t<S, Q, MODE_TG, 0>(p, st);
-  if (mode == MODE_NAT2PULL)
-    return trt ? launch_step_t<S, Q, MODE_NAT2PULL, 1>(p, st) : launch_step_t<S, Q, MODE_NAT2PULL, 0>(p, st);
   if (mode == MODE_AA_EVEN)
     return trt ? launch_step_t<S, Q, MODE_AA_EVEN, 1>(p, st) : launch_step_t<S, Q, MODE_AA_EVEN, 0>(p, st);
   return trt ? launch_step_t<S, Q, MODE_AA_ODD, 1>(p, st) : launch_step_t<S, Q, MODE_AA_ODD, 0>(p, st);
