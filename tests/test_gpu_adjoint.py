@@ -153,7 +153,8 @@ def test_adjoint_c4_full_vs_fp64_fd(storage):
     """The adjoint workload at full size: 128^3, 512 steps, checkpoint every 64
     steps, TRT tau 0.55, against FP64 central differences (h = 1e-6,
     Richardson) of the GPU forward on 16 seeded cells of the swept region.
-    FP64 adjoint: 1e-5 relative per cell.  FP32 forward and adjoint (the
+    FP64 adjoint: 1e-5 relative per cell plus 1e-7 of max|grad| (the
+    difference's round-off floor).  FP32 forward and adjoint (the
     gradient of the FP32 trajectory): 1e-2 relative per cell (the relative
     error of each cell is printed)."""
     case = W.c4_adjoint().with_(storage=storage)
@@ -161,7 +162,7 @@ def test_adjoint_c4_full_vs_fp64_fd(storage):
     cells = swept_cells(case, every=64)
     J_of = J_fp64(case)
     scale = np.abs(ge).max()
-    worst_rel, worst_scaled = 0.0, 0.0
+    worst_rel, worst_scaled, fp64_ok = 0.0, 0.0, True
     for c in cells:
         fd = fd_richardson(J_of, case.cells, c, 1e-6)
         g = ge.reshape(-1)[c]
@@ -169,10 +170,14 @@ def test_adjoint_c4_full_vs_fp64_fd(storage):
         print(f"{storage} cell {c}: adjoint {g:.9e} fd {fd:.9e} rel {rel:.3e} (max |grad| {scale:.3e})")
         worst_rel = max(worst_rel, rel if abs(fd) > 1e-3 * scale else 0.0)
         worst_scaled = max(worst_scaled, abs(g - fd) / scale)
+        # FP64: 1e-5 relative per cell plus 1e-7 of max|grad|, the round-off floor of a
+        # central difference at h = 1e-6 (about eps_mach |J| / h), which dominates for
+        # cells whose derivative is ~1e-3 of the largest
+        fp64_ok = fp64_ok and abs(g - fd) <= 1e-5 * abs(fd) + 1e-7 * scale
     print(f"C4 128^3 {storage} adjoint vs FP64 FD, 16 cells: worst relative {worst_rel:.3e}, "
           f"worst / max|grad| {worst_scaled:.3e}")
     if storage == "fp64":
-        assert worst_rel <= 1e-5 and worst_scaled <= 1e-6
+        assert fp64_ok and worst_scaled <= 1e-6
     else:
         assert worst_rel <= 1e-2 and worst_scaled <= 1e-3
 
