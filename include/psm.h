@@ -250,12 +250,14 @@ int psm_mass(psm_handle h, double* out);
 int psm_synchronize(psm_handle h);
 
 /* Step-kernel variant: PSM_KERNEL_AUTO (default) uses the TMA-staged kernel
- * when the shape allows it, else plain global loads; PSM_KERNEL_PLAIN forces
- * plain loads; PSM_KERNEL_TMA forces TMA staging (PSM_ERR_UNSUPPORTED if the
- * shape does not allow it).  TMA shapes: with TX = min(256, nx):
- * nx % TX == 0, 256 % nx == 0 when nx < 256, TX >= 32, ny % (256 / TX) == 0,
- * nx * sizeof(PDF) a multiple of 16 bytes.  Both variants compute the same
- * results. */
+ * when the shape allows it, else plain global loads, and runs the AA odd step
+ * with whichever of the two measured faster on GB300 (plain loads);
+ * PSM_KERNEL_PLAIN forces plain loads; PSM_KERNEL_TMA forces TMA staging for
+ * every step the shape allows (PSM_ERR_UNSUPPORTED if it allows none).  TMA
+ * shapes: with TX = min(256, nx): nx % TX == 0, 256 % nx == 0 when nx < 256,
+ * TX >= 32, ny % (256 / TX) == 0, nx * sizeof(PDF) a multiple of 16 bytes,
+ * staging buffers within the per-block shared memory; the AA odd step also
+ * needs TX = 256.  All variants compute the same results, bit for bit. */
 /* ------------------------------------------------------------------------ */
 /* Differentiation (not in the paper): discrete adjoint of the step          */
 /* ------------------------------------------------------------------------ */

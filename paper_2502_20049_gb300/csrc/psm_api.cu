@@ -45,9 +45,9 @@ size_t storage_bytes(int st) {
   }
 }
 
-// Tensor maps of one PDF buffer (x, y, z, slot): box (TX, 1, 1, Q) and (TX, 1, 1, 1).
+// Tensor maps of one PDF buffer (x, y, z, slot): box (TX, TY, 1, Q) and (TX, 1, 1, 1).
 struct BufMaps {
-  CUtensorMap rowq;
+  CUtensorMap tile;
   CUtensorMap row1;
 };
 
@@ -113,6 +113,7 @@ struct psm_solver {
   int* d_err = nullptr;
   // TMA-staged step kernel: eligibility, its tiling and the tensor maps per buffer
   bool tma_ok = false;
+  bool tma_odd_ok = false;  // the AA odd step has its TMA variant too (full 256-cell rows)
   int variant = PSM_KERNEL_AUTO;
   psm::Tiling tma_tiling;
   BufMaps maps[2];
@@ -156,12 +157,12 @@ cudaError_t launch_step_tma(int storage, int Q, int mode, const StepParams& p, c
     default: return launch_step_tma_bf16(Q, mode, p.trt, p, m, st);
   }
 }
-int tma_smem_bytes(int storage, int Q, int mode, int tx, int ty) {
+int tma_smem_bytes(int storage, int Q, int mode) {
   switch (storage) {
-    case PSM_FP64: return tma_smem_bytes_fp64(Q, mode, tx, ty);
-    case PSM_FP32: return tma_smem_bytes_fp32(Q, mode, tx, ty);
-    case PSM_FP16_SHIFTED: return tma_smem_bytes_fp16(Q, mode, tx, ty);
-    default: return tma_smem_bytes_bf16(Q, mode, tx, ty);
+    case PSM_FP64: return tma_smem_bytes_fp64(Q, mode);
+    case PSM_FP32: return tma_smem_bytes_fp32(Q, mode);
+    case PSM_FP16_SHIFTED: return tma_smem_bytes_fp16(Q, mode);
+    default: return tma_smem_bytes_bf16(Q, mode);
   }
 }
 int step_grid_blocks(int storage, int Q, int mode, int trt) {
@@ -328,15 +329,16 @@ int import_uniform(psm_solver* h, double rho, const double u[3]) {
 
 bool valid_handle(psm_handle h) { return h != nullptr; }
 
-// 1: the AA odd step (per-direction rows) uses plain global loads even where
-// the TMA-staged kernel is selected.
+// 1: under PSM_KERNEL_AUTO the AA odd step (per-direction rows) uses plain
+// global loads even where its TMA-staged variant applies.
 #ifndef PSM_AA_ODD_PLAIN
-#define PSM_AA_ODD_PLAIN 0
+#define PSM_AA_ODD_PLAIN 1
 #endif
 
 // TMA shape rules (see k_step_tma): TX = min(256, nx), nx % TX == 0,
 // 256 % nx == 0 if nx < 256, TY = 256 / TX divides ny, rows of 16-byte
-// multiples, at least 32 cells per row segment.
+// multiples, at least 32 cells per row segment, and the staging buffers of
+// the modes used fit the shared memory a block may have.
 bool tma_shape(const psm_solver* h, psm::Tiling& t) {
   const int64_t nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
   const int64_t b = (int64_t)storage_bytes(h->lat.storage);
@@ -344,6 +346,12 @@ bool tma_shape(const psm_solver* h, psm::Tiling& t) {
   if (TX < 32 || nx % TX != 0 || (nx < 256 && 256 % nx != 0)) return false;
   const int64_t TY = 256 / TX;
   if (ny % TY != 0 || (TX * b) % 16 != 0 || (nx * b) % 16 != 0) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  const int mode = h->lat.streaming == PSM_STREAM_TWO_GRID ? psm::MODE_TG : psm::MODE_AA_EVEN;
+  if (psm::tma_smem_bytes(h->lat.storage, h->Q, mode) > optin) return false;
   t.tx = (int)TX;
   t.ty = (int)TY;
   t.ntx = (int)(nx / TX);
@@ -378,9 +386,9 @@ bool encode_maps(const psm_solver* h, void* buf, BufMaps& m) {
                               (cuuint64_t)h->Q};
   const cuuint64_t strides[3] = {dims[0] * b, dims[0] * dims[1] * b, dims[0] * dims[1] * dims[2] * b};
   const cuuint32_t elem[4] = {1, 1, 1, 1};
-  const cuuint32_t box_q[4] = {(cuuint32_t)h->tma_tiling.tx, 1, 1, (cuuint32_t)h->Q};
+  const cuuint32_t box_q[4] = {(cuuint32_t)h->tma_tiling.tx, (cuuint32_t)h->tma_tiling.ty, 1, (cuuint32_t)h->Q};
   const cuuint32_t box_1[4] = {(cuuint32_t)h->tma_tiling.tx, 1, 1, 1};
-  CUresult r1 = enc(&m.rowq, dt, 4, buf, dims, strides, box_q, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  CUresult r1 = enc(&m.tile, dt, 4, buf, dims, strides, box_q, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   CUresult r2 = enc(&m.row1, dt, 4, buf, dims, strides, box_1, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -544,6 +552,11 @@ int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_colli
   if (tma_shape(h, h->tma_tiling)) {
     h->tma_ok = true;
     for (int b = 0; b < nbuf; ++b) h->tma_ok = h->tma_ok && encode_maps(h, h->buf[b], h->maps[b]);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    h->tma_odd_ok = h->tma_ok && h->tma_tiling.tx == psm::PSM_THREADS &&
+                    psm::tma_smem_bytes(h->lat.storage, h->Q, psm::MODE_AA_ODD) <= optin;
   }
   e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), h->stream);
   if (e == cudaSuccess)
@@ -808,15 +821,16 @@ int psm_step(psm_handle h, int n) {
       p.f = h->buf[0];
       p.f_dst = nullptr;
     }
-    // the AA odd step may run with plain loads while the other steps use TMA staging
-    const bool tma_now = use_tma && !(PSM_AA_ODD_PLAIN && mode == psm::MODE_AA_ODD);
+    // the AA odd step runs with plain loads unless its TMA variant applies
+    const bool tma_now = use_tma && (mode != psm::MODE_AA_ODD ||
+                                     (h->tma_odd_ok && (h->variant == PSM_KERNEL_TMA || !PSM_AA_ODD_PLAIN)));
     p.t = tma_now ? h->tma_tiling : h->tiling;
     psm::TmaMaps tm;
     if (tma_now) {
       const int dsti = h->lat.streaming == PSM_STREAM_TWO_GRID ? (src ^ 1) : 0;
-      tm.rowq = h->maps[src].rowq;
+      tm.tile = h->maps[src].tile;
       tm.row1 = h->maps[src].row1;
-      tm.dstq = h->maps[dsti].rowq;
+      tm.dst = h->maps[dsti].tile;
     }
     cudaError_t e = tma_now ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, tm, h->stream)
                             : psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);

@@ -92,9 +92,9 @@ struct StepParams {
 // Tensor maps of the PDF buffers viewed as 4-D tensors (x, y, z, slot) for one
 // launch of the TMA step kernel.
 struct TmaMaps {
-  CUtensorMap rowq;  // source buffer, box (TX, 1, 1, Q)
-  CUtensorMap row1;  // source buffer, box (TX, 1, 1, 1)
-  CUtensorMap dstq;  // destination of the AA even step's TMA stores, box (TX, 1, 1, Q)
+  CUtensorMap tile;  // source buffer, box (TX, TY, 1, Q): all slots of one tile
+  CUtensorMap row1;  // source buffer, box (TX, 1, 1, 1): one slot of one row
+  CUtensorMap dst;   // destination of the AA even step's TMA stores, box (TX, TY, 1, Q)
 };
 
 // Parameters of the import / export / reduction kernels.
@@ -140,8 +140,8 @@ Tiling make_tiling(int nx, int ny, int nz);
 cudaError_t launch_step(int storage, int Q, int mode, const StepParams& p, cudaStream_t st);
 // TMA-staged variant (shape rules at k_step_tma); p.t must be the TMA tiling.
 cudaError_t launch_step_tma(int storage, int Q, int mode, const StepParams& p, const TmaMaps& m, cudaStream_t st);
-// dynamic shared memory bytes the TMA variant needs for a TX x TY tile
-int tma_smem_bytes(int storage, int Q, int mode, int tx, int ty);
+// dynamic shared memory bytes of the TMA variant for one mode
+int tma_smem_bytes(int storage, int Q, int mode);
 int step_grid_blocks(int storage, int Q, int mode, int trt);
 cudaError_t launch_import(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_export(int storage, int Q, const IoParams& p, cudaStream_t st);
@@ -153,7 +153,7 @@ cudaError_t launch_remap(const RemapParams& p, cudaStream_t st);
   cudaError_t launch_step_##NAME(int Q, int mode, int trt, const StepParams& p, cudaStream_t st); \
   cudaError_t launch_step_tma_##NAME(int Q, int mode, int trt, const StepParams& p, const TmaMaps& m, \
                                      cudaStream_t st);                                    \
-  int tma_smem_bytes_##NAME(int Q, int mode, int tx, int ty);                             \
+  int tma_smem_bytes_##NAME(int Q, int mode);                                             \
   int step_grid_blocks_##NAME(int Q, int mode, int trt);                                  \
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st);            \

@@ -279,16 +279,86 @@ __device__ __forceinline__ const ConstT<T>& cst(const StepParams& p) {
   else return p.cd;
 }
 
+// 1 / r: FP32 by rcp.approx refined with one Newton-Raphson step
+// (a' = a + a (1 - r a)), within 1 ulp for the densities here (r near 1); FP64
+// by IEEE division.
+template <class T>
+__device__ __forceinline__ T recip(T r) {
+  if constexpr (sizeof(T) == 4) {
+    float a;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(a) : "f"(r));
+    return fmaf(a, fmaf(-r, a, 1.0f), a);
+  } else {
+    return T(1) / r;
+  }
+}
+
+// Density deviation, density and velocity of one cell from its shifted PDFs.
+template <class T, int Q>
+__device__ __forceinline__ void moments(const T (&f)[Q], T rho0, T& drho, T& rho, T& ux, T& uy, T& uz, T& uu) {
+  T d = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    d += f[i];
+    if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
+    if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
+    if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
+  }
+  drho = d;
+  rho = rho0 + d;
+  const T inv_rho = recip(rho);
+  ux = jx * inv_rho;
+  uy = jy * inv_rho;
+  uz = jz * inv_rho;
+  uu = ux * ux + uy * uy + uz * uz;
+}
+
+// Pure fluid cell: f* = f + Omega^F (Eq. 2, or TRT).  Per opposite pair (i, j),
+// c_j = -c_i, the shifted equilibrium splits into
+//   even = w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)),  odd = 3 w rho (c.u),
+//   f^eq_i - w rho0 = even + odd,  f^eq_j - w rho0 = even - odd.
+template <class T, int Q, int TRT>
+__device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drho, T rho, T ux, T uy, T uz, T uu) {
+  const T omp = C.om_a + C.om_b, omm = C.om_a - C.om_b;  // omega+ and omega- (BGK: both 1/tau)
+  const T base = drho - T(1.5) * rho * uu;
+  {
+    const T n0 = f[0] - T(lat_w<Q>(0)) * base;
+    f[0] = f[0] - omp * n0;
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int j = i + 1;
+    const T w = T(lat_w<Q>(i));
+    T cu = 0;
+    if (lat_cx(i)) cu += T(lat_cx(i)) * ux;
+    if (lat_cy(i)) cu += T(lat_cy(i)) * uy;
+    if (lat_cz(i)) cu += T(lat_cz(i)) * uz;
+    const T even = w * base + (T(4.5) * w * rho) * (cu * cu);
+    const T odd = (T(3) * w * rho) * cu;
+    if (TRT) {
+      // f* = f - omega+ (f+ - even) - omega- (f- - odd)
+      const T np = T(0.5) * (f[i] + f[j]) - even;
+      const T nm = T(0.5) * (f[i] - f[j]) - odd;
+      const T a = omp * np, b = omm * nm;
+      f[i] = f[i] - a - b;
+      f[j] = f[j] - a + b;
+    } else {
+      f[i] = f[i] + C.om_a * ((even + odd) - f[i]);
+      f[j] = f[j] + C.om_a * ((even - odd) - f[j]);
+    }
+  }
+}
+
 // One cell's PSM update in registers, from its pre-collision (shifted) PDFs f:
 // remap (Sec. 3), B (Eq. 5/6), moments, u_s = omega x r + v, Omega^F (Eq. 2 /
 // TRT), Omega^S (Eq. 7/8/9), blend (Eq. 4).  f becomes the post-collision
 // state.  For a cell in contact with a body (B > 0) ft receives the force and
-// torque on the body (minus Eq. 10 / 11 per cell, about R_n).
+// torque on the body (minus Eq. 10 / 11 per cell, about R_n).  A cell with
+// B = 0 takes exactly the arithmetic of fluid_relax.
 template <class T, int Q, int TRT>
 __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int x, int y, int z, unsigned cell,
                                             int& owner, bool& solid_cell, double (&ft)[6]) {
   const ConstT<T>& C = cst<T>(p);
-  const T rho0 = C.rho0;
   const T om_a = C.om_a, om_b = C.om_b;
   const T inv_tau = C.inv_tau;
   // ---- remap (Sec. 3) and weighting (Eq. 5/6) ----
@@ -300,54 +370,11 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int 
     const T t = C.tmh;
     Bw = eps * t / ((T(1) - eps) + t);
   }
-  // ---- moments ----
-  T drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    drho += f[i];
-    if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
-    if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
-    if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
-  }
-  const T rho = rho0 + drho;
-  const T inv_rho = T(1) / rho;
-  const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-  const T uu = ux * ux + uy * uy + uz * uz;
+  T drho, rho, ux, uy, uz, uu;
+  moments<T, Q>(f, C.rho0, drho, rho, ux, uy, uz, uu);
   solid_cell = Bw != T(0);
   if (!solid_cell) {
-    // ---- pure fluid: f* = f + Omega^F ----
-    // Per opposite pair (i, j), c_j = -c_i, the shifted equilibrium splits into
-    //   even = w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)) = A_w + K_w (c.u)^2,
-    //   odd  = 3 w rho (c.u),  f^eq_i = even + odd,  f^eq_j = even - odd,
-    // with A_w, K_w, C_w = 3 w rho computed once per weight class.
-    const T omp = om_a + om_b, omm = om_a - om_b;  // omega+ and omega- (BGK: both 1/tau)
-    const T base = drho - T(1.5) * rho * uu;
-    {
-      const T n0 = f[0] - T(lat_w<Q>(0)) * base;
-      f[0] = f[0] - omp * n0;
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-      const int j = i + 1;
-      const T w = T(lat_w<Q>(i));
-      T cu = 0;
-      if (lat_cx(i)) cu += T(lat_cx(i)) * ux;
-      if (lat_cy(i)) cu += T(lat_cy(i)) * uy;
-      if (lat_cz(i)) cu += T(lat_cz(i)) * uz;
-      const T even = w * base + (T(4.5) * w * rho) * (cu * cu);
-      const T odd = (T(3) * w * rho) * cu;
-      if (TRT) {
-        // f* = f - omega+ (f+ - even) - omega- (f- - odd)
-        const T np = T(0.5) * (f[i] + f[j]) - even;
-        const T nm = T(0.5) * (f[i] - f[j]) - odd;
-        const T a = omp * np, b = omm * nm;
-        f[i] = f[i] - a - b;
-        f[j] = f[j] - a + b;
-      } else {
-        f[i] = f[i] + om_a * ((even + odd) - f[i]);
-        f[j] = f[j] + om_a * ((even - odd) - f[j]);
-      }
-    }
+    fluid_relax<T, Q, TRT>(C, f, drho, rho, ux, uy, uz, uu);
     return;
   }
   // ---- PSM cell: f* = f + (1 - B) Omega^F + B Omega^S (Eq. 4) ----
@@ -427,25 +454,78 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int 
   }
 }
 
+// Streaming indices of one cell: the index of x + c for c in {-1, 0, 1}^3 is
+// zc[cz + 1] + dy[cy + 1] + dx[cx + 1] (mod 2^32; cell indices are < 2^32),
+// periodic in x and y, and in z (where z ends in ghost planes the callers
+// drop the populations that cross them).
+struct Stencil {
+  unsigned zc[3], dy[3], dx[3];
+  __device__ __forceinline__ void init(const Grid3& g, int x, int y, int z, unsigned cell) {
+    const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
+    dx[0] = (x == 0) ? nx - 1u : 0u - 1u;
+    dx[1] = 0u;
+    dx[2] = (x == g.nx - 1) ? 0u - (nx - 1u) : 1u;
+    dy[0] = (y == 0) ? (unsigned)(g.ny - 1) * nx : 0u - nx;
+    dy[1] = 0u;
+    dy[2] = (y == g.ny - 1) ? 0u - (unsigned)(g.ny - 1) * nx : nx;
+    zc[0] = cell + ((z == 0) ? (unsigned)(g.nz - 1) * plane : 0u - plane);
+    zc[1] = cell;
+    zc[2] = cell + ((z == g.nz - 1) ? 0u - (unsigned)(g.nz - 1) * plane : plane);
+  }
+  __device__ __forceinline__ unsigned at(int cx, int cy, int cz) const { return zc[cz + 1] + dy[cy + 1] + dx[cx + 1]; }
+};
+
+// Position of a z plane against the ghost planes (never set for periodic z).
+struct ZGhost {
+  bool lo, hi;  // z - 1 (resp. z + 1) lies in a ghost plane
+  __device__ __forceinline__ void init(const Grid3& g, int z) {
+    const bool ghost = g.bc_z == PSM_BC_EQ_INLET_OUTLET;
+    lo = ghost && z == 0;
+    hi = ghost && z == g.nz - 1;
+  }
+  // x - c_i lies in a ghost plane: population i enters from it
+  __device__ __forceinline__ bool from(int cz) const { return (cz > 0 && lo) || (cz < 0 && hi); }
+  // x + c_i lies in a ghost plane: population i leaves the domain
+  __device__ __forceinline__ bool to(int cz) const { return (cz > 0 && hi) || (cz < 0 && lo); }
+};
+
 // Streamed store (Eq. 1) of one cell's post-collision PDFs:
 //   AA even  own cell, slot opp(i);
 //   AA odd   cell x + c_i, slot i;
 //   TG       cell x + c_i, slot i of the other buffer;
-// populations that leave the domain through a ghost plane are dropped.
-template <class S, int Q, int MODE, class T>
-__device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Nbr& nbr, unsigned cell, const T (&f)[Q]) {
+// with GHOST, populations that leave the domain through a ghost plane are dropped.
+template <class S, int Q, int MODE, bool GHOST, class T>
+__device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Stencil& sn, const ZGhost& zg,
+                                          unsigned cell, const T (&f)[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
     if (MODE == MODE_AA_EVEN) {
       Store<S>::st(buf + (long long)lat_opp(i) * N + cell, f[i]);
-    } else if (!nbr.to_ghost(cz)) {
+    } else if (!GHOST || !zg.to(lat_cz(i))) {
       S* base = (MODE == MODE_TG) ? dst : buf;
-      Store<S>::st(base + (long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz)), f[i]);
+      Store<S>::st(base + (long long)i * N + sn.at(lat_cx(i), lat_cy(i), lat_cz(i)), f[i]);
     }
   }
 }
 
+// Pre-collision PDFs of one cell with plain global loads (AA odd: population i
+// of x was stored by x - c_i in slot opp(i); otherwise slot i of x); with
+// GHOST, populations entering from a ghost plane take the ghost value.
+template <class S, int Q, int MODE, bool GHOST, class T>
+__device__ __forceinline__ void psm_load(const StepParams& p, const S* buf, long long N, const Stencil& sn,
+                                         const ZGhost& zg, unsigned cell, T (&f)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+    if (GHOST && zg.from(cz)) {
+      f[i] = cst<T>(p).ghost[i];
+    } else if (MODE == MODE_AA_ODD) {
+      f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + sn.at(-cx, -cy, -cz));
+    } else {
+      f[i] = Store<S>::ld(buf + (long long)i * N + cell);
+    }
+  }
+}
 // Per-warp force/torque accumulation into s_ft[warp] (fixed order: warp
 // butterfly, then in tile order).  All 32 lanes must call it.
 __device__ __forceinline__ void warp_ft(double (*s_ft)[PSM_MAX_BODIES * 6], int nb, bool contributes, int owner,
@@ -478,9 +558,40 @@ __device__ __forceinline__ void block_ft_finish(double (*s_ft)[PSM_MAX_BODIES * 
   grid_reduce(blk, ncomp, p.partials, p.ticket, p.ft_out);
 }
 
+// A tile (TX x TY cells of one z plane) takes the fluid-only path when no
+// body's cell box meets it, no eps perturbation is set and its plane is not
+// next to a ghost plane: every cell of such a tile has B = 0, and no
+// population of it enters or leaves through a ghost plane.
+__device__ __forceinline__ bool tile_general(const StepParams& p, int x0, int y0, int z, int TX, int TY) {
+  bool gen = p.delta != nullptr || (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && (z == 0 || z == p.g.nz - 1));
+#pragma unroll
+  for (int bi = 0; bi < PSM_MAX_BODIES; ++bi) {
+    if (bi < p.nbodies) {
+      const DevBody& b = p.body[bi];
+      gen = gen || (x0 < b.x1 && x0 + TX > b.x0 && y0 < b.y1 && y0 + TY > b.y0 && z >= b.z0 && z < b.z1);
+    }
+  }
+  return gen;
+}
+
+template <bool B>
+struct BoolC {
+  static constexpr bool value = B;
+};
+
+// One cell of a fluid-only tile: moments and Omega^F (the arithmetic psm_collide
+// takes for B = 0).
+template <class T, int Q, int TRT>
+__device__ __forceinline__ void fluid_collide(const StepParams& p, T (&f)[Q]) {
+  const ConstT<T>& C = cst<T>(p);
+  T drho, rho, ux, uy, uz, uu;
+  moments<T, Q>(f, C.rho0, drho, rho, ux, uy, uz, uu);
+  fluid_relax<T, Q, TRT>(C, f, drho, rho, ux, uy, uz, uu);
+}
+
 // ---------------------------------------------------------------------------
 // The fused step kernel with plain global loads (any grid shape; persistent:
-// blocks stride over row tiles).
+// blocks stride over tiles of TX x TY cells of one z plane).
 // ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int TRT>
 __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
@@ -495,48 +606,42 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   S* __restrict__ dst = static_cast<S*>(p.f_dst);
   const long long N = p.g.ncell;
   const int ntiles = (int)p.t.ntiles;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int x, y, z;
-    tile_coords(p.t, tile, x, y, z);
+  const int lx = (int)threadIdx.x % p.t.tx, ly = (int)threadIdx.x / p.t.tx;
+
+  auto cell_body = [&](auto gen_c, int x, int y, int z) {
+    constexpr bool GEN = decltype(gen_c)::value;
     const bool active = x < p.g.nx && y < p.g.ny;
     int owner = -1;
     bool solid_cell = false;
     double ft[6] = {0, 0, 0, 0, 0, 0};
     if (active) {
       const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
-      Nbr nbr;
-      nbr.init(p.g, x, y, z);
+      Stencil sn;
+      sn.init(p.g, x, y, z, cell);
+      ZGhost zg;
+      zg.init(p.g, z);
       T f[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
-        if (nbr.from_ghost(cz)) {
-          f[i] = cst<T>(p).ghost[i];
-        } else if (MODE == MODE_AA_ODD) {
-          // population i of x was stored by x - c_i in slot opp(i) (AA even step)
-          f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + (unsigned)(cell + nbr.off(-cx, -cy, -cz)));
-        } else {
-          f[i] = Store<S>::ld(buf + (long long)i * N + cell);
-        }
-      }
-      psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
-      psm_store<S, Q, MODE>(buf, dst, N, nbr, cell, f);
+      psm_load<S, Q, MODE, GEN>(p, buf, N, sn, zg, cell, f);
+      if (GEN) psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
+      else fluid_collide<T, Q, TRT>(p, f);
+      psm_store<S, Q, MODE, GEN>(buf, dst, N, sn, zg, cell, f);
     }
-    warp_ft(s_ft, nb, active && solid_cell && owner >= 0, owner, ft);
+    if (GEN) warp_ft(s_ft, nb, active && solid_cell && owner >= 0, owner, ft);
+  };
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int txi = tile % p.t.ntx;
+    const int r = tile / p.t.ntx;
+    const int tyi = r % p.t.nty;
+    const int z = r / p.t.nty;
+    const int x0 = txi * p.t.tx, y0 = tyi * p.t.ty;
+    if (tile_general(p, x0, y0, z, p.t.tx, p.t.ty)) cell_body(BoolC<true>{}, x0 + lx, y0 + ly, z);
+    else cell_body(BoolC<false>{}, x0 + lx, y0 + ly, z);
   }
   if (nb == 0) return;
   block_ft_finish(s_ft, p);
 }
 
-// ---------------------------------------------------------------------------
-// TMA-staged step kernel.  Shapes: nx % TX == 0 with TX = min(256, nx) (and
-// 256 % nx == 0 when nx < 256), TY = 256 / TX rows per tile, ny % TY == 0, and
-// TX * sizeof(S) a multiple of 16 bytes.  Persistent blocks stride over tiles;
-// thread 0 keeps PSM_TMA_STAGES tiles of pre-collision rows in flight in
-// shared memory (cp.async.bulk.tensor row boxes, plus 16-byte
-// cp.async.bulk edge chunks for the neighbours' x - c_x in the AA odd step)
-// while all threads collide the oldest staged tile from shared memory.
-// ---------------------------------------------------------------------------
 #ifndef PSM_TMA_STAGES
 #define PSM_TMA_STAGES 3
 #endif
@@ -595,49 +700,58 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 #ifndef PSM_TMA_OUT_BUFS
 #define PSM_TMA_OUT_BUFS 2
 #endif
-// 1: the two-grid and AA even steps write their tiles back with TMA tensor stores
+// 1: the AA even step writes its tiles back with TMA tensor stores
 #ifndef PSM_TMA_STORE
 #define PSM_TMA_STORE 1
 #endif
 
-// Shared-memory layout of the TMA step kernel (bytes; every box 128-byte aligned):
-// [barriers 128 B] [PSM_TMA_STAGES input stages] [PSM_TMA_OUT_BUFS output tiles].
-//   input, own-row modes (AA even): per tile row one [Q][TX] box of all slots;
-//   input, pull modes (TG, AA odd): per tile row and direction one [TX] row plus
-//     two 16-byte x-edge chunks;
-//   output (TG, AA even): per tile row one [Q][TX] box, written back by one TMA
-//     tensor store.
+// Lattice components for a run-time direction index (the producer's copy
+// jobs): c + 1 in two bits per direction.
+__host__ __device__ constexpr unsigned long long lat_bits(int axis) {
+  unsigned long long b = 0;
+  for (int i = 0; i < 27; ++i)
+    b |= (unsigned long long)((axis == 0 ? lat_cx(i) : (axis == 1 ? lat_cy(i) : lat_cz(i))) + 1) << (2 * i);
+  return b;
+}
+constexpr unsigned long long kLatCX = lat_bits(0), kLatCY = lat_bits(1), kLatCZ = lat_bits(2);
+__device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return (int)((bits >> (2 * i)) & 3ull) - 1; }
+
+// Shared-memory layout of the TMA step kernel (bytes; every box 128-byte
+// aligned): [barriers 128 B] [PSM_TMA_STAGES input stages] [PSM_TMA_OUT_BUFS
+// output tiles].
+//   input, own-cell modes (two-grid, AA even): one [Q][TY][TX] box per tile
+//     (TX TY = 256): slot i of thread t at element 256 i + t;
+//   input, AA odd (TX = 256, TY = 1): per direction i a record of ROW bytes
+//     holding, from byte 128, the 256 values of slot opp(i) at x - c_i for the
+//     tile's cells, preceded and followed by a 16-byte x-edge chunk, so that
+//     cell lx reads element lx - c_x of it with no branch;
+//   output (AA even): one [Q][TY][TX] box, written back by one TMA tensor store.
 template <class S, int Q, int MODE>
 struct TmaLayout {
   static constexpr bool LOAD_OWN = MODE != MODE_AA_ODD;
   static constexpr bool STORE_TMA = PSM_TMA_STORE && MODE == MODE_AA_EVEN;
   static constexpr int EP = 16 / (int)sizeof(S);  // elements per 16-byte edge chunk
-  __host__ __device__ static int r128(int b) { return ((b + 127) / 128) * 128; }
-  __host__ __device__ static int row_bytes(int tx) { return r128(tx * (int)sizeof(S)); }
-  __host__ __device__ static int box_bytes(int tx) { return r128(Q * tx * (int)sizeof(S)); }
-  __host__ __device__ static int main_bytes(int tx, int ty) {
-    return LOAD_OWN ? ty * box_bytes(tx) : ty * Q * row_bytes(tx);
-  }
-  __host__ __device__ static int edge_bytes(int ty) { return LOAD_OWN ? 0 : ty * Q * 2 * 16; }
-  __host__ __device__ static int stage_bytes(int tx, int ty) { return r128(main_bytes(tx, ty) + edge_bytes(ty)); }
-  __host__ __device__ static int out_bytes(int tx, int ty) { return STORE_TMA ? ty * box_bytes(tx) : 0; }
+  static constexpr int r128(int b) { return ((b + 127) / 128) * 128; }
+  static constexpr int BOX = r128(Q * PSM_THREADS * (int)sizeof(S));
+  static constexpr int ROW = r128(128 + PSM_THREADS * (int)sizeof(S) + 16);
+  static constexpr int STAGE = LOAD_OWN ? BOX : Q * ROW;
+  static constexpr int OUT = STORE_TMA ? BOX : 0;
   // + 128 B of barriers, + 128 B of alignment slack
-  __host__ __device__ static int smem_bytes(int tx, int ty) {
-    return 256 + PSM_TMA_STAGES * stage_bytes(tx, ty) + PSM_TMA_OUT_BUFS * out_bytes(tx, ty);
-  }
+  static constexpr int SMEM = 256 + PSM_TMA_STAGES * STAGE + PSM_TMA_OUT_BUFS * OUT;
 };
 
 // ---------------------------------------------------------------------------
-// TMA-staged step kernel.  Shapes: nx % TX == 0 with TX = min(256, nx) (and
-// 256 % nx == 0 when nx < 256), TY = 256 / TX rows per tile, ny % TY == 0, and
-// TX * sizeof(S) a multiple of 16 bytes.  Persistent blocks stride over tiles.
-// Warp 0 keeps PSM_TMA_STAGES tiles of pre-collision rows in flight in shared
-// memory (cp.async.bulk.tensor row boxes; in the pull modes one row per
-// direction plus 16-byte cp.async.bulk edge chunks for x - c_x) while all
-// threads collide the oldest staged tile from shared memory.  In the two-grid
-// and AA even steps the post-collision tile is written to shared memory and
-// back to global memory by one TMA tensor store per tile row; the AA odd step
-// stores to x + c_i with st.global.
+// TMA-staged step kernel.  Shapes: tiles of TX x TY = 256 cells of one z
+// plane with nx % TX == 0 and ny % TY == 0 (TX = min(256, nx)), TX * sizeof(S)
+// a multiple of 16 bytes; the AA odd step needs TX = 256.  Persistent blocks
+// stride over tiles.  Warp 0 keeps PSM_TMA_STAGES tiles of pre-collision PDFs
+// in flight in shared memory (two-grid and AA even: one cp.async.bulk.tensor
+// box per tile; AA odd: one row per direction plus 16-byte cp.async.bulk edge
+// chunks for x - c_x) while all threads collide the oldest staged tile from
+// shared memory.  The producer classifies each tile (tile_general) and the
+// block takes the fluid-only path or the general one for the whole tile.  The
+// two-grid and AA odd steps store to x + c_i with st.global; the AA even step
+// writes the tile to shared memory and back with one TMA tensor store.
 // ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int TRT>
 __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
@@ -650,6 +764,7 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
   __shared__ int s_abort;
   __shared__ int s_issued[NST];  // loads issued per stage (warp 0, lane 0)
+  __shared__ int4 s_hdr[NST];    // per stage: tile origin x0, y0, z and the general-path flag
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // dynamic shared memory is only guaranteed 16-byte alignment: align by hand
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -658,15 +773,11 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
   const int TX = p.t.tx, TY = p.t.ty;
-  const int SB = L::stage_bytes(TX, TY);
-  const int RB = L::row_bytes(TX), BB = L::box_bytes(TX), MB = L::main_bytes(TX, TY);
   unsigned char* stages = base + 128;
-  unsigned char* outs = stages + NST * SB;
-  const int OB = L::out_bytes(TX, TY);
+  unsigned char* outs = stages + NST * L::STAGE;
   const long long N = p.g.ncell;
   S* __restrict__ buf = static_cast<S*>(p.f);
   S* __restrict__ dst = static_cast<S*>(p.f_dst);
-  const void* map_in = L::LOAD_OWN ? (const void*)&maps.rowq : (const void*)&maps.row1;
   const int ntiles = (int)p.t.ntiles;
 
   if (threadIdx.x == 0) {
@@ -679,50 +790,47 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   }
   __syncthreads();
 
-  // producer: the 32 lanes of warp 0 stage the pre-collision rows of tile
+  // producer: the 32 lanes of warp 0 stage the pre-collision PDFs of tile
   // `tile` into stage `s`, one copy job per lane
   auto produce = [&](int tile, int s) {
-    int tx0, y0, z;
-    {
-      const int tx = tile % p.t.ntx;
-      const int r = tile / p.t.ntx;
-      const int ty = r % p.t.nty;
-      z = r / p.t.nty;
-      tx0 = tx * TX;
-      y0 = ty * TY;
-    }
-    unsigned char* st = stages + (long long)s * SB;
+    const int txi = tile % p.t.ntx;
+    const int r = tile / p.t.ntx;
+    const int tyi = r % p.t.nty;
+    const int z = r / p.t.nty;
+    const int x0 = txi * TX, y0 = tyi * TY;
+    unsigned char* st = stages + s * L::STAGE;
     unsigned long long* bar = &bars[s];
     fence_proxy_async();
-    const int njobs = L::LOAD_OWN ? TY : TY * Q;
-    for (int job = lane; job < njobs; job += 32) {
-      if (L::LOAD_OWN) {
-        const int r = job;
-        mbar_expect_tx(bar, (unsigned)(Q * TX * (int)sizeof(S)));
-        tma_load_4d(st + r * BB, map_in, tx0, y0 + r, z, 0, bar);
-      } else {
-        const int r = job / Q, i = job % Q;
-        const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+    if (L::LOAD_OWN) {
+      if (lane == 0) {
+        mbar_expect_tx(bar, (unsigned)(Q * PSM_THREADS * (int)sizeof(S)));
+        tma_load_4d(st, &maps.tile, x0, y0, z, 0, bar);
+      }
+    } else {
+      for (int i = lane; i < Q; i += 32) {
+        const int cx = lat_c_rt(kLatCX, i), cy = lat_c_rt(kLatCY, i), cz = lat_c_rt(kLatCZ, i);
         int zs = z - cz;
         if (zs < 0 || zs >= p.g.nz) {
           if (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET) continue;  // ghost populations: no load
           zs = zs < 0 ? zs + p.g.nz : zs - p.g.nz;
         }
-        int ys = y0 + r - cy;
+        int ys = y0 - cy;
         ys = ys < 0 ? ys + p.g.ny : (ys >= p.g.ny ? ys - p.g.ny : ys);
         const int slot = lat_opp(i);
-        mbar_expect_tx(bar, (unsigned)(TX * (int)sizeof(S)));
-        tma_load_4d(st + (r * Q + i) * RB, map_in, tx0, ys, zs, slot, bar);
+        unsigned char* row = st + i * L::ROW + 128;
+        mbar_expect_tx(bar, (unsigned)(PSM_THREADS * (int)sizeof(S)));
+        tma_load_4d(row, &maps.row1, x0, ys, zs, slot, bar);
         if (cx != 0) {
-          // cx = +1 reads x0 - 1 (left chunk), cx = -1 reads x0 + TX (right chunk), wrapped in x
-          const int xe = cx > 0 ? (tx0 == 0 ? p.g.nx - EP : tx0 - EP) : (tx0 + TX == p.g.nx ? 0 : tx0 + TX);
+          // cx = +1: cell x0 reads x0 - 1 (the chunk before the row, wrapped in x);
+          // cx = -1: cell x0 + 255 reads x0 + 256 (the chunk after it)
+          const int xe = cx > 0 ? (x0 == 0 ? p.g.nx - EP : x0 - EP) : (x0 + PSM_THREADS == p.g.nx ? 0 : x0 + PSM_THREADS);
           const S* src = buf + (long long)slot * N + ((long long)zs * p.g.ny + ys) * p.g.nx + xe;
-          unsigned char* e = st + MB + ((r * Q + i) * 2 + (cx > 0 ? 0 : 1)) * 16;
           mbar_expect_tx(bar, 16u);
-          bulk_load_16(e, src, bar);
+          bulk_load_16(cx > 0 ? row - 16 : row + PSM_THREADS * (int)sizeof(S), src, bar);
         }
       }
     }
+    if (lane == 0) s_hdr[s] = make_int4(x0, y0, z, tile_general(p, x0, y0, z, TX, TY) ? 1 : 0);
     __syncwarp();  // every lane's expected bytes are registered before the arrival
     if (lane == 0) {
       mbar_arrive(bar);
@@ -738,21 +846,32 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   }
 
   const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  int k = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-    const int s = k % NST;
-    const unsigned parity = (unsigned)((k / NST) & 1);
-    // bounded wait for the stage (2^22 polls); on time-out record an error and leave
-    if (!mbar_try_wait(&bars[s], parity)) {
-      unsigned it = 0;
-      while (!mbar_try_wait(&bars[s], parity)) {
-        if (++it > (1u << 22)) {
-          atomicExch(&s_abort, 1);
-          break;
-        }
+
+  // One staged tile.  Both instantiations (general / fluid-only) pass the same
+  // block barriers in the same order.  Returns true when the block must leave
+  // (a staged load timed out).
+  auto tile_body = [&](auto gen_c, int tile, int k, int s, const int4 hd) -> bool {
+    constexpr bool GEN = decltype(gen_c)::value;
+    const int x = hd.x + lx, y = hd.y + ly, z = hd.z;
+    const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
+    ZGhost zg;
+    zg.init(p.g, z);
+    const unsigned char* st = stages + s * L::STAGE;
+    T f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (GEN && zg.from(lat_cz(i))) {
+        f[i] = cst<T>(p).ghost[i];
+      } else if (L::LOAD_OWN) {
+        f[i] = Store<S>::ld(reinterpret_cast<const S*>(st) + i * PSM_THREADS + threadIdx.x);
+      } else {
+        f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + i * L::ROW + 128) + (lx - lat_cx(i)));
       }
     }
-    __syncthreads();
+    // the output tile about to be written was last handed to a TMA store NOUT
+    // tiles ago: wait until that store has read it
+    if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_read<NOUT - 1>();
+    __syncthreads();  // stage s read (warp 0 may refill it); output tile free; abort flag visible
     if (s_abort) {
       if (threadIdx.x == 0) {
         if (p.err) atomicExch(p.err, 1);
@@ -766,46 +885,8 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         if (L::STORE_TMA) bulk_wait_all();
       }
       __syncthreads();
-      return;
+      return true;
     }
-    int tx0, y0, z;
-    {
-      const int tx = tile % p.t.ntx;
-      const int r = tile / p.t.ntx;
-      const int ty = r % p.t.nty;
-      z = r / p.t.nty;
-      tx0 = tx * TX;
-      y0 = ty * TY;
-    }
-    const int x = tx0 + lx, y = y0 + ly;
-    const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
-    Nbr nbr;
-    nbr.init(p.g, x, y, z);
-    const unsigned char* st = stages + (long long)s * SB;
-    T f[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cx = lat_cx(i), cz = lat_cz(i);
-      if (nbr.from_ghost(cz)) {
-        f[i] = cst<T>(p).ghost[i];
-      } else if (L::LOAD_OWN) {
-        f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + ly * BB) + i * TX + lx);
-      } else {
-        const S* row = reinterpret_cast<const S*>(st + (ly * Q + i) * RB);
-        const int xs = lx - cx;
-        if (xs < 0) {
-          f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + MB + ((ly * Q + i) * 2 + 0) * 16) + (EP - 1));
-        } else if (xs >= TX) {
-          f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + MB + ((ly * Q + i) * 2 + 1) * 16));
-        } else {
-          f[i] = Store<S>::ld(row + xs);
-        }
-      }
-    }
-    // the output tile about to be written was last handed to a TMA store NOUT
-    // tiles ago: wait until that store has read it
-    if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_read<NOUT - 1>();
-    __syncthreads();  // stage s fully read (warp 0 may refill it); output tile free
     if (warp == 0) {
       const int next = tile + NST * gridDim.x;
       if (next < ntiles) produce(next, s);
@@ -813,25 +894,44 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     int owner = -1;
     bool solid_cell = false;
     double ft[6] = {0, 0, 0, 0, 0, 0};
-    psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
+    if (GEN) psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
+    else fluid_collide<T, Q, TRT>(p, f);
     if (L::STORE_TMA) {
-      unsigned char* ob = outs + (long long)(k % NOUT) * OB;
-      S* orow = reinterpret_cast<S*>(ob + ly * BB);
+      S* ot = reinterpret_cast<S*>(outs + (k % NOUT) * L::OUT);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int slot = MODE == MODE_AA_EVEN ? lat_opp(i) : i;
-        Store<S>::st(orow + slot * TX + lx, f[i]);
-      }
+      for (int i = 0; i < Q; ++i) Store<S>::st(ot + lat_opp(i) * PSM_THREADS + threadIdx.x, f[i]);
       fence_proxy_async();  // the generic-proxy writes above become visible to the TMA store
       __syncthreads();
       if (threadIdx.x == 0) {
-        for (int r = 0; r < TY; ++r) tma_store_4d(&maps.dstq, tx0, y0 + r, z, 0, ob + r * BB);
+        tma_store_4d(&maps.dst, hd.x, hd.y, z, 0, ot);
         bulk_commit();
       }
     } else {
-      psm_store<S, Q, MODE>(buf, dst, N, nbr, cell, f);
+      Stencil sn;
+      sn.init(p.g, x, y, z, cell);
+      psm_store<S, Q, MODE, GEN>(buf, dst, N, sn, zg, cell, f);
     }
-    warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
+    if (GEN) warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
+    return false;
+  };
+
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    const int s = k % NST;
+    const unsigned parity = (unsigned)((k / NST) & 1);
+    // bounded wait for the stage (2^22 polls); on time-out flag it (checked after the next block barrier)
+    if (!mbar_try_wait(&bars[s], parity)) {
+      unsigned it = 0;
+      while (!mbar_try_wait(&bars[s], parity)) {
+        if (++it > (1u << 22)) {
+          s_abort = 1;
+          break;
+        }
+      }
+    }
+    const int4 hd = s_hdr[s];
+    const bool stop = hd.w ? tile_body(BoolC<true>{}, tile, k, s, hd) : tile_body(BoolC<false>{}, tile, k, s, hd);
+    if (stop) return;
   }
   if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_all();
   if (nb == 0) return;
@@ -1030,22 +1130,21 @@ cudaError_t launch_step_t(const StepParams& p, cudaStream_t st) {
 template <class S, int Q, int MODE, int TRT>
 cudaError_t launch_step_tma_t(const StepParams& p, const TmaMaps& m, cudaStream_t st) {
   using L = TmaLayout<S, Q, MODE>;
-  const int smem = L::smem_bytes(p.t.tx, p.t.ty);
-  static int configured = -1;  // largest dynamic shared memory set so far
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, Q, MODE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<S, Q, MODE, TRT>, PSM_THREADS, smem);
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  long long blocks = (long long)sms * per_sm;
-  if (blocks > 8ll * sms) blocks = 8ll * sms;
-  if (p.t.ntiles < blocks) blocks = p.t.ntiles;
-  k_step_tma<S, Q, MODE, TRT><<<(int)blocks, PSM_THREADS, smem, st>>>(p, m);
+  // persistent grid: resident blocks per SM (registers and shared memory), at most 8 per SM
+  static const int blocks = [] {
+    if (cudaFuncSetAttribute(k_step_tma<S, Q, MODE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) !=
+        cudaSuccess)
+      return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<S, Q, MODE, TRT>, PSM_THREADS, L::SMEM);
+    if (per_sm > 8) per_sm = 8;
+    return sms * per_sm;
+  }();
+  if (blocks < 1) return cudaErrorInvalidConfiguration;
+  const long long grid = p.t.ntiles < blocks ? p.t.ntiles : blocks;
+  k_step_tma<S, Q, MODE, TRT><<<(int)grid, PSM_THREADS, L::SMEM, st>>>(p, m);
   return cudaGetLastError();
 }
 
@@ -1059,10 +1158,10 @@ cudaError_t launch_step_tma_q(int mode, int trt, const StepParams& p, const TmaM
 }
 
 template <class S, int Q>
-int tma_smem_q(int mode, int tx, int ty) {
-  if (mode == MODE_TG) return TmaLayout<S, Q, MODE_TG>::smem_bytes(tx, ty);
-  if (mode == MODE_AA_EVEN) return TmaLayout<S, Q, MODE_AA_EVEN>::smem_bytes(tx, ty);
-  return TmaLayout<S, Q, MODE_AA_ODD>::smem_bytes(tx, ty);
+int tma_smem_q(int mode) {
+  if (mode == MODE_TG) return TmaLayout<S, Q, MODE_TG>::SMEM;
+  if (mode == MODE_AA_EVEN) return TmaLayout<S, Q, MODE_AA_EVEN>::SMEM;
+  return TmaLayout<S, Q, MODE_AA_ODD>::SMEM;
 }
 
 template <class S, int Q, int MODE, int TRT>
@@ -1105,8 +1204,8 @@ inline int io_grid(const IoParams& p) {
                                      cudaStream_t st) {                                                 \
     return Q == 19 ? launch_step_tma_q<S, 19>(mode, trt, p, m, st) : launch_step_tma_q<S, 27>(mode, trt, p, m, st); \
   }                                                                                                     \
-  int tma_smem_bytes_##NAME(int Q, int mode, int tx, int ty) {                                          \
-    return Q == 19 ? tma_smem_q<S, 19>(mode, tx, ty) : tma_smem_q<S, 27>(mode, tx, ty);                 \
+  int tma_smem_bytes_##NAME(int Q, int mode) {                                                          \
+    return Q == 19 ? tma_smem_q<S, 19>(mode) : tma_smem_q<S, 27>(mode);                                 \
   }                                                                                                     \
   int step_grid_blocks_##NAME(int Q, int mode, int trt) {                                               \
     return Q == 19 ? step_blocks_q<S, 19>(mode, trt) : step_blocks_q<S, 27>(mode, trt);                 \

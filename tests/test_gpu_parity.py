@@ -181,6 +181,29 @@ def test_tma_staged_equals_plain_bitwise(storage, streaming):
     assert np.array_equal(a.force_torque(0), b.force_torque(0))
 
 
+@pytest.mark.parametrize("storage,Q", [("fp64", 19), ("fp32", 19), ("fp16", 19), ("bf16", 19), ("fp16", 27)])
+@pytest.mark.parametrize("streaming,bc_z", [("aa", 1), ("aa", 0), ("twogrid", 1)])
+def test_tma_full_rows_equal_plain_bitwise(storage, Q, streaming, bc_z):
+    """Tiles of one full 256-cell row, where every step (the AA odd step too)
+    has its TMA-staged variant: forced TMA staging and plain loads compute the
+    same bits.  A translating, rotating body crosses fluid-only and general
+    tiles; bc_z = 1 adds the ghost-plane tiles; 23 steps end on an odd AA step."""
+    from paper_2502_20049_gb300 import psm
+
+    case = W.Case("rows256_bits", 256, 8, 12, Q=Q, storage=storage, streaming=streaming, fluid="trt", tau=0.6,
+                  bc_z=bc_z, u_in=(0.02, 0.01, 0.03), steps=23,
+                  bodies=[W.BodyCase(W.ELLIPSOID, (7.0, 2.5, 2.0), 2, (100.0, 4.0, 6.0), omega=(0.01, 0.02, 0.05),
+                                     v=(0.1, 0.0, 0.0))])
+    a = psm.Solver.from_case(case)
+    b = psm.Solver.from_case(case)
+    a.set_kernel_variant("tma")
+    b.set_kernel_variant("plain")
+    a.step(case.steps)
+    b.step(case.steps)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.force_torque(0), b.force_torque(0))
+
+
 @pytest.mark.parametrize("streaming", ["aa", "twogrid"])
 def test_tma_full_rows_periodic_fp32(streaming):
     """TMA tiles of one full 256-cell row (the benchmark's tiling), periodic z,
