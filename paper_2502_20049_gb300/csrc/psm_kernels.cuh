@@ -624,7 +624,19 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
       psm_load<S, Q, MODE, GEN>(p, buf, N, sn, zg, cell, f);
       if (GEN) psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
       else fluid_collide<T, Q, TRT>(p, f);
-      psm_store<S, Q, MODE, GEN>(buf, dst, N, sn, zg, cell, f);
+      if (MODE == MODE_AA_ODD) {
+        // rebuild the stencil for the stores rather than keep it live through
+        // the collision (register pressure); the empty asm hides the equality
+        // of the inputs from common-subexpression elimination
+        int xs = x, ys = y, zs = z;
+        unsigned cs = cell;
+        asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs), "+r"(cs));
+        Stencil sn2;
+        sn2.init(p.g, xs, ys, zs, cs);
+        psm_store<S, Q, MODE, GEN>(buf, dst, N, sn2, zg, cs, f);
+      } else {
+        psm_store<S, Q, MODE, GEN>(buf, dst, N, sn, zg, cell, f);
+      }
     }
     if (GEN) warp_ft(s_ft, nb, active && solid_cell && owner >= 0, owner, ft);
   };
@@ -667,6 +679,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0u;
+}
+// mbar_try_wait polled at most 2^22 times; false if the phase did not complete
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 __device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int c0, int c1, int c2, int c3,
                                             unsigned long long* bar) {
@@ -768,7 +786,13 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // dynamic shared memory is only guaranteed 16-byte alignment: align by hand
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(base);  // NST barriers in the first 128 B
+  // barriers in the first 128 B: full[s] completes when stage s holds its tile
+  // (the producer's arrival plus the copied bytes); empty[s] when every warp has
+  // read it (one arrival per warp)
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(base);
+  unsigned long long* empty = full + NST;
+  static_assert(2 * NST * 8 <= 128, "stage barriers exceed their 128 bytes");
+  constexpr int NW = PSM_THREADS / 32;
   const int nb = p.nbodies;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
@@ -783,7 +807,8 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   if (threadIdx.x == 0) {
     s_abort = 0;
     for (int s = 0; s < NST; ++s) {
-      mbar_init(&bars[s], 1);
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NW);
       s_issued[s] = 0;
     }
     fence_mbar_init();
@@ -799,7 +824,7 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     const int z = r / p.t.nty;
     const int x0 = txi * TX, y0 = tyi * TY;
     unsigned char* st = stages + s * L::STAGE;
-    unsigned long long* bar = &bars[s];
+    unsigned long long* bar = &full[s];
     fence_proxy_async();
     if (L::LOAD_OWN) {
       if (lane == 0) {
@@ -847,10 +872,14 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
 
   const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
 
-  // One staged tile.  Both instantiations (general / fluid-only) pass the same
-  // block barriers in the same order.  Returns true when the block must leave
-  // (a staged load timed out).
-  auto tile_body = [&](auto gen_c, int tile, int k, int s, const int4 hd) -> bool {
+  // One staged tile, read from stage s after its full barrier.  Each warp
+  // signals empty[s] once it holds its cells' PDFs in registers; warp 0 then
+  // waits for all warps' signals before refilling the stage, so warps do not
+  // wait for one another otherwise.  The AA even step adds one block barrier
+  // per tile (the output tile complete before its TMA store).  A wait that
+  // times out sets s_abort; the block leaves the tile loop (the AA even step
+  // together, after its block barrier).
+  auto tile_body = [&](auto gen_c, int tile, int k, int s, const int4 hd) {
     constexpr bool GEN = decltype(gen_c)::value;
     const int x = hd.x + lx, y = hd.y + ly, z = hd.z;
     const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
@@ -868,28 +897,15 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
         f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + i * L::ROW + 128) + (lx - lat_cx(i)));
       }
     }
-    // the output tile about to be written was last handed to a TMA store NOUT
-    // tiles ago: wait until that store has read it
-    if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_read<NOUT - 1>();
-    __syncthreads();  // stage s read (warp 0 may refill it); output tile free; abort flag visible
-    if (s_abort) {
-      if (threadIdx.x == 0) {
-        if (p.err) atomicExch(p.err, 1);
-        // let the copies already issued finish before the block's shared memory is released
-        for (int s2 = 0; s2 < NST; ++s2) {
-          if (s_issued[s2] == 0) continue;
-          const unsigned last = (unsigned)((s_issued[s2] - 1) & 1);
-          for (unsigned it = 0; it < (1u << 20) && !mbar_try_wait(&bars[s2], last); ++it) {
-          }
-        }
-        if (L::STORE_TMA) bulk_wait_all();
-      }
-      __syncthreads();
-      return true;
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
     if (warp == 0) {
       const int next = tile + NST * gridDim.x;
-      if (next < ntiles) produce(next, s);
+      if (next < ntiles) {
+        // warp-uniform outcome (produce needs the whole warp)
+        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (unsigned)((k / NST) & 1)))) produce(next, s);
+        else s_abort = 1;
+      }
     }
     int owner = -1;
     bool solid_cell = false;
@@ -901,6 +917,9 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
 #pragma unroll
       for (int i = 0; i < Q; ++i) Store<S>::st(ot + lat_opp(i) * PSM_THREADS + threadIdx.x, f[i]);
       fence_proxy_async();  // the generic-proxy writes above become visible to the TMA store
+      // the stores issued so far have read their output tiles: after the block
+      // barrier below, tile k + 1 may write the buffer the store of tile k - 1 read
+      if (threadIdx.x == 0) bulk_wait_read<0>();
       __syncthreads();
       if (threadIdx.x == 0) {
         tma_store_4d(&maps.dst, hd.x, hd.y, z, 0, ot);
@@ -912,28 +931,34 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
       psm_store<S, Q, MODE, GEN>(buf, dst, N, sn, zg, cell, f);
     }
     if (GEN) warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
-    return false;
   };
 
   int k = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
     const int s = k % NST;
-    const unsigned parity = (unsigned)((k / NST) & 1);
-    // bounded wait for the stage (2^22 polls); on time-out flag it (checked after the next block barrier)
-    if (!mbar_try_wait(&bars[s], parity)) {
-      unsigned it = 0;
-      while (!mbar_try_wait(&bars[s], parity)) {
-        if (++it > (1u << 22)) {
-          s_abort = 1;
-          break;
-        }
-      }
+    // bounded wait for the stage, warp-uniform outcome (on time-out the block's
+    // results are invalid: s_abort)
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (unsigned)((k / NST) & 1)))) {
+      s_abort = 1;
+      if (!L::STORE_TMA) break;
     }
     const int4 hd = s_hdr[s];
-    const bool stop = hd.w ? tile_body(BoolC<true>{}, tile, k, s, hd) : tile_body(BoolC<false>{}, tile, k, s, hd);
-    if (stop) return;
+    if (hd.w) tile_body(BoolC<true>{}, tile, k, s, hd);
+    else tile_body(BoolC<false>{}, tile, k, s, hd);
+    // the AA even step leaves together: s_abort was set before its block barrier
+    if (L::STORE_TMA && s_abort) break;
   }
   if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_all();
+  __syncthreads();
+  if (s_abort) {
+    if (threadIdx.x == 0) {
+      if (p.err) atomicExch(p.err, 1);
+      // let the copies already issued finish before the block's shared memory is released
+      for (int s2 = 0; s2 < NST; ++s2)
+        if (s_issued[s2] > 0) mbar_wait_bounded(&full[s2], (unsigned)((s_issued[s2] - 1) & 1));
+    }
+    __syncthreads();
+  }
   if (nb == 0) return;
   block_ft_finish(s_ft, p);
 }
