@@ -45,10 +45,12 @@ size_t storage_bytes(int st) {
   }
 }
 
-// Tensor maps of one PDF buffer (x, y, z, slot): box (TX, TY, 1, Q) and (TX, 1, 1, 1).
+// Tensor maps of one PDF buffer (x, y, z, slot): boxes (TX, TY, 1, Q),
+// (TX, 1, 1, 1) and (32, 1, 1, Q).
 struct BufMaps {
   CUtensorMap tile;
   CUtensorMap row1;
+  CUtensorMap warpq;
 };
 
 struct HostBody {
@@ -392,7 +394,10 @@ bool encode_maps(const psm_solver* h, void* buf, BufMaps& m) {
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   CUresult r2 = enc(&m.row1, dt, 4, buf, dims, strides, box_1, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+  const cuuint32_t box_w[4] = {32, 1, 1, (cuuint32_t)h->Q};
+  CUresult r3 = enc(&m.warpq, dt, 4, buf, dims, strides, box_w, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS && r3 == CUDA_SUCCESS;
 }
 
 template <class T>
@@ -830,7 +835,7 @@ int psm_step(psm_handle h, int n) {
       const int dsti = h->lat.streaming == PSM_STREAM_TWO_GRID ? (src ^ 1) : 0;
       tm.tile = h->maps[src].tile;
       tm.row1 = h->maps[src].row1;
-      tm.dst = h->maps[dsti].tile;
+      tm.dstw = h->maps[dsti].warpq;
     }
     cudaError_t e = tma_now ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, tm, h->stream)
                             : psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);

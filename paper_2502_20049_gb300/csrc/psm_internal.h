@@ -94,7 +94,7 @@ struct StepParams {
 struct TmaMaps {
   CUtensorMap tile;  // source buffer, box (TX, TY, 1, Q): all slots of one tile
   CUtensorMap row1;  // source buffer, box (TX, 1, 1, 1): one slot of one row
-  CUtensorMap dst;   // destination of the AA even step's TMA stores, box (TX, TY, 1, Q)
+  CUtensorMap dstw;  // destination of the AA even step's per-warp TMA stores, box (32, 1, 1, Q)
 };
 
 // Parameters of the import / export / reduction kernels.

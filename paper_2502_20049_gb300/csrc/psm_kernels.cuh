@@ -272,6 +272,14 @@ __device__ __forceinline__ void grid_reduce(const double* blk, int ncomp, double
 #ifndef PSM_MIN_BLOCKS_Q27
 #define PSM_MIN_BLOCKS_Q27 2
 #endif
+// Resident blocks per SM of a step kernel for storage S and stencil Q: FP64
+// state needs twice the registers per PDF, so one block fewer (80 / 128 / 255
+// registers per thread at 3 / 2 / 1 blocks of 256 threads).
+template <class S, int Q>
+__host__ __device__ constexpr int step_min_blocks() {
+  return sizeof(S) == 8 ? (Q == 19 ? PSM_MIN_BLOCKS_Q19 - 1 : PSM_MIN_BLOCKS_Q27 - 1)
+                        : (Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27);
+}
 
 template <class T>
 __device__ __forceinline__ const ConstT<T>& cst(const StepParams& p) {
@@ -558,6 +566,33 @@ __device__ __forceinline__ void block_ft_finish(double (*s_ft)[PSM_MAX_BODIES * 
   grid_reduce(blk, ncomp, p.partials, p.ticket, p.ft_out);
 }
 
+// Tile walk of a persistent block: tile index t = (z nty + ty) ntx + tx,
+// advanced by the grid size without divisions after the first tile.
+struct TileWalk {
+  int tx, ty, z;       // current tile
+  int gx, gy, gz;      // the grid size, decomposed like a tile index
+  int ntx, nty;
+  __device__ __forceinline__ void init(const Tiling& t, int tile, int step) {
+    ntx = t.ntx;
+    nty = t.nty;
+    tx = tile % ntx;
+    ty = (tile / ntx) % nty;
+    z = tile / ntx / nty;
+    gx = step % ntx;
+    gy = (step / ntx) % nty;
+    gz = step / ntx / nty;
+  }
+  __device__ __forceinline__ void advance() {
+    tx += gx;
+    int c = tx >= ntx;
+    tx -= c ? ntx : 0;
+    ty += gy + c;
+    c = ty >= nty;
+    ty -= c ? nty : 0;
+    z += gz + c;
+  }
+};
+
 // A tile (TX x TY cells of one z plane) takes the fluid-only path when no
 // body's cell box meets it, no eps perturbation is set and its plane is not
 // next to a ghost plane: every cell of such a tile has B = 0, and no
@@ -594,7 +629,7 @@ __device__ __forceinline__ void fluid_collide(const StepParams& p, T (&f)[Q]) {
 // blocks stride over tiles of TX x TY cells of one z plane).
 // ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int TRT>
-__global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
+__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     k_step(const __grid_constant__ StepParams p) {
   using T = typename Store<S>::T;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
@@ -641,12 +676,10 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     if (GEN) warp_ft(s_ft, nb, active && solid_cell && owner >= 0, owner, ft);
   };
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int txi = tile % p.t.ntx;
-    const int r = tile / p.t.ntx;
-    const int tyi = r % p.t.nty;
-    const int z = r / p.t.nty;
-    const int x0 = txi * p.t.tx, y0 = tyi * p.t.ty;
+  TileWalk walk;
+  walk.init(p.t, blockIdx.x, gridDim.x);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, walk.advance()) {
+    const int x0 = walk.tx * p.t.tx, y0 = walk.ty * p.t.ty, z = walk.z;
     if (tile_general(p, x0, y0, z, p.t.tx, p.t.ty)) cell_body(BoolC<true>{}, x0 + lx, y0 + ly, z);
     else cell_body(BoolC<false>{}, x0 + lx, y0 + ly, z);
   }
@@ -654,8 +687,10 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   block_ft_finish(s_ft, p);
 }
 
-#ifndef PSM_TMA_STAGES
-#define PSM_TMA_STAGES 3
+// Most input stages of the TMA step kernel (the stage count follows from the
+// shared memory per SM, see TmaLayout).
+#ifndef PSM_TMA_MAX_STAGES
+#define PSM_TMA_MAX_STAGES 8
 #endif
 
 __device__ __forceinline__ unsigned smem_u32(const void* ptr) {
@@ -715,13 +750,16 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// output boxes per warp (AA even): 1, since a warp's previous store has long
+// read its box by the time the warp's next tile is collided
 #ifndef PSM_TMA_OUT_BUFS
-#define PSM_TMA_OUT_BUFS 2
+#define PSM_TMA_OUT_BUFS 1
 #endif
-// 1: the AA even step writes its tiles back with TMA tensor stores
+// 1: the AA even step writes its tiles back with TMA tensor stores (one per warp)
 #ifndef PSM_TMA_STORE
 #define PSM_TMA_STORE 1
 #endif
+
 
 // Lattice components for a run-time direction index (the producer's copy
 // jobs): c + 1 in two bits per direction.
@@ -735,15 +773,19 @@ constexpr unsigned long long kLatCX = lat_bits(0), kLatCY = lat_bits(1), kLatCZ 
 __device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return (int)((bits >> (2 * i)) & 3ull) - 1; }
 
 // Shared-memory layout of the TMA step kernel (bytes; every box 128-byte
-// aligned): [barriers 128 B] [PSM_TMA_STAGES input stages] [PSM_TMA_OUT_BUFS
-// output tiles].
+// aligned): [barriers 128 B] [NST input stages] [PSM_TMA_OUT_BUFS output tiles].
 //   input, own-cell modes (two-grid, AA even): one [Q][TY][TX] box per tile
 //     (TX TY = 256): slot i of thread t at element 256 i + t;
 //   input, AA odd (TX = 256, TY = 1): per direction i a record of ROW bytes
 //     holding, from byte 128, the 256 values of slot opp(i) at x - c_i for the
 //     tile's cells, preceded and followed by a 16-byte x-edge chunk, so that
 //     cell lx reads element lx - c_x of it with no branch;
-//   output (AA even): one [Q][TY][TX] box, written back by one TMA tensor store.
+//   output (AA even): per warp a [Q][32] box of its 32 cells (WBOX bytes),
+//     written back by the warp's own TMA tensor store.
+// The stage count NST fills the shared memory of the resident blocks the
+// launch bounds aim at (228 KB per SM, less 1 KB per block reserved and the
+// kernel's static shared memory), between 2 and PSM_TMA_MAX_STAGES: deeper
+// pipelines for the narrower storage types keep more bytes in flight.
 template <class S, int Q, int MODE>
 struct TmaLayout {
   static constexpr bool LOAD_OWN = MODE != MODE_AA_ODD;
@@ -753,30 +795,36 @@ struct TmaLayout {
   static constexpr int BOX = r128(Q * PSM_THREADS * (int)sizeof(S));
   static constexpr int ROW = r128(128 + PSM_THREADS * (int)sizeof(S) + 16);
   static constexpr int STAGE = LOAD_OWN ? BOX : Q * ROW;
-  static constexpr int OUT = STORE_TMA ? BOX : 0;
+  static constexpr int WBOX = r128(Q * 32 * (int)sizeof(S));
+  static constexpr int OUT = STORE_TMA ? (PSM_THREADS / 32) * WBOX : 0;
+  static constexpr int SM_SMEM = 233472;
+  static constexpr int BLOCKS = step_min_blocks<S, Q>();
+  static constexpr int BUDGET = (SM_SMEM - BLOCKS * (1024 + 4096)) / BLOCKS - 256 - PSM_TMA_OUT_BUFS * OUT;
+  static constexpr int NST = BUDGET / STAGE < 2 ? 2 : (BUDGET / STAGE > PSM_TMA_MAX_STAGES ? PSM_TMA_MAX_STAGES : BUDGET / STAGE);
   // + 128 B of barriers, + 128 B of alignment slack
-  static constexpr int SMEM = 256 + PSM_TMA_STAGES * STAGE + PSM_TMA_OUT_BUFS * OUT;
+  static constexpr int SMEM = 256 + NST * STAGE + PSM_TMA_OUT_BUFS * OUT;
 };
 
 // ---------------------------------------------------------------------------
 // TMA-staged step kernel.  Shapes: tiles of TX x TY = 256 cells of one z
 // plane with nx % TX == 0 and ny % TY == 0 (TX = min(256, nx)), TX * sizeof(S)
 // a multiple of 16 bytes; the AA odd step needs TX = 256.  Persistent blocks
-// stride over tiles.  Warp 0 keeps PSM_TMA_STAGES tiles of pre-collision PDFs
+// stride over tiles.  Warp 0 keeps NST tiles of pre-collision PDFs
 // in flight in shared memory (two-grid and AA even: one cp.async.bulk.tensor
 // box per tile; AA odd: one row per direction plus 16-byte cp.async.bulk edge
 // chunks for x - c_x) while all threads collide the oldest staged tile from
 // shared memory.  The producer classifies each tile (tile_general) and the
 // block takes the fluid-only path or the general one for the whole tile.  The
-// two-grid and AA odd steps store to x + c_i with st.global; the AA even step
-// writes the tile to shared memory and back with one TMA tensor store.
+// two-grid and AA odd steps store to x + c_i with st.global; in the AA even
+// step every warp writes its 32 cells to shared memory and back with one TMA
+// tensor store.  No block barrier inside the tile loop.
 // ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int TRT>
-__global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27)
+__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     k_step_tma(const __grid_constant__ StepParams p, const __grid_constant__ TmaMaps maps) {
   using T = typename Store<S>::T;
   using L = TmaLayout<S, Q, MODE>;
-  constexpr int NST = PSM_TMA_STAGES;
+  constexpr int NST = L::NST;
   constexpr int NOUT = PSM_TMA_OUT_BUFS;
   constexpr int EP = L::EP;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
@@ -815,14 +863,14 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   }
   __syncthreads();
 
-  // producer: the 32 lanes of warp 0 stage the pre-collision PDFs of tile
-  // `tile` into stage `s`, one copy job per lane
-  auto produce = [&](int tile, int s) {
-    const int txi = tile % p.t.ntx;
-    const int r = tile / p.t.ntx;
-    const int tyi = r % p.t.nty;
-    const int z = r / p.t.nty;
-    const int x0 = txi * TX, y0 = tyi * TY;
+  // producer: the 32 lanes of warp 0 stage the pre-collision PDFs of the
+  // walk's current tile into stage `s`, one copy job per lane, and advance it
+  TileWalk walk;
+  walk.init(p.t, blockIdx.x, gridDim.x);
+  auto produce = [&](int s) {
+    const int z = walk.z;
+    const int x0 = walk.tx * TX, y0 = walk.ty * TY;
+    walk.advance();
     unsigned char* st = stages + s * L::STAGE;
     unsigned long long* bar = &full[s];
     fence_proxy_async();
@@ -866,7 +914,7 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   if (warp == 0) {
     for (int k = 0; k < NST; ++k) {
       const int tile = blockIdx.x + k * gridDim.x;
-      if (tile < ntiles) produce(tile, k);
+      if (tile < ntiles) produce(k);
     }
   }
 
@@ -875,11 +923,10 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   // One staged tile, read from stage s after its full barrier.  Each warp
   // signals empty[s] once it holds its cells' PDFs in registers; warp 0 then
   // waits for all warps' signals before refilling the stage, so warps do not
-  // wait for one another otherwise.  The AA even step adds one block barrier
-  // per tile (the output tile complete before its TMA store).  A wait that
-  // times out sets s_abort; the block leaves the tile loop (the AA even step
-  // together, after its block barrier).
+  // wait for one another otherwise.  A wait that times out sets s_abort and
+  // the warp leaves the tile loop.
   auto tile_body = [&](auto gen_c, int tile, int k, int s, const int4 hd) {
+    (void)tile;
     constexpr bool GEN = decltype(gen_c)::value;
     const int x = hd.x + lx, y = hd.y + ly, z = hd.z;
     const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
@@ -903,7 +950,7 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
       const int next = tile + NST * gridDim.x;
       if (next < ntiles) {
         // warp-uniform outcome (produce needs the whole warp)
-        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (unsigned)((k / NST) & 1)))) produce(next, s);
+        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (unsigned)((k / NST) & 1)))) produce(s);
         else s_abort = 1;
       }
     }
@@ -913,16 +960,18 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
     if (GEN) psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
     else fluid_collide<T, Q, TRT>(p, f);
     if (L::STORE_TMA) {
-      S* ot = reinterpret_cast<S*>(outs + (k % NOUT) * L::OUT);
+      // this warp's output box of tile k; lane 0 issued (and committed) the
+      // warp's earlier stores: the one NOUT tiles back must have read it
+      S* ow = reinterpret_cast<S*>(outs + (k % NOUT) * L::OUT + warp * L::WBOX);
+      if (lane == 0) bulk_wait_read<NOUT - 1>();
+      __syncwarp();
 #pragma unroll
-      for (int i = 0; i < Q; ++i) Store<S>::st(ot + lat_opp(i) * PSM_THREADS + threadIdx.x, f[i]);
+      for (int i = 0; i < Q; ++i) Store<S>::st(ow + lat_opp(i) * 32 + lane, f[i]);
       fence_proxy_async();  // the generic-proxy writes above become visible to the TMA store
-      // the stores issued so far have read their output tiles: after the block
-      // barrier below, tile k + 1 may write the buffer the store of tile k - 1 read
-      if (threadIdx.x == 0) bulk_wait_read<0>();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        tma_store_4d(&maps.dst, hd.x, hd.y, z, 0, ot);
+      __syncwarp();
+      if (lane == 0) {
+        const int w0 = warp * 32;
+        tma_store_4d(&maps.dstw, hd.x + w0 % TX, hd.y + w0 / TX, z, 0, ow);
         bulk_commit();
       }
     } else {
@@ -937,18 +986,16 @@ __global__ void __launch_bounds__(PSM_THREADS, Q == 19 ? PSM_MIN_BLOCKS_Q19 : PS
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
     const int s = k % NST;
     // bounded wait for the stage, warp-uniform outcome (on time-out the block's
-    // results are invalid: s_abort)
+    // results are invalid: s_abort; the warp leaves the loop)
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (unsigned)((k / NST) & 1)))) {
       s_abort = 1;
-      if (!L::STORE_TMA) break;
+      break;
     }
     const int4 hd = s_hdr[s];
     if (hd.w) tile_body(BoolC<true>{}, tile, k, s, hd);
     else tile_body(BoolC<false>{}, tile, k, s, hd);
-    // the AA even step leaves together: s_abort was set before its block barrier
-    if (L::STORE_TMA && s_abort) break;
   }
-  if (L::STORE_TMA && threadIdx.x == 0) bulk_wait_all();
+  if (L::STORE_TMA && lane == 0) bulk_wait_all();
   __syncthreads();
   if (s_abort) {
     if (threadIdx.x == 0) {
