@@ -715,10 +715,32 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0u;
 }
-// mbar_try_wait polled at most 2^22 times; false if the phase did not complete
+// try_wait with a suspend-time hint: the thread may stop issuing until the
+// phase completes or about `ns` nanoseconds have passed
+__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long* bar, unsigned parity, unsigned ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 P, [%1], %2, %3;\n selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for a phase: one poll, then suspended polls until the phase
+// completes, 100 ms pass (global timer) or 2^22 polls were made; false if the
+// phase did not complete.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  for (unsigned it = 0; it < (1u << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+    if (globaltimer_ns() - t0 > 100000000ull) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int c0, int c1, int c2, int c3,
@@ -750,10 +772,9 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// output boxes per warp (AA even): 1, since a warp's previous store has long
-// read its box by the time the warp's next tile is collided
+// output boxes per warp (AA even), where the shared memory allows it
 #ifndef PSM_TMA_OUT_BUFS
-#define PSM_TMA_OUT_BUFS 1
+#define PSM_TMA_OUT_BUFS 2
 #endif
 // 1: the AA even step writes its tiles back with TMA tensor stores (one per warp)
 #ifndef PSM_TMA_STORE
@@ -773,7 +794,7 @@ constexpr unsigned long long kLatCX = lat_bits(0), kLatCY = lat_bits(1), kLatCZ 
 __device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return (int)((bits >> (2 * i)) & 3ull) - 1; }
 
 // Shared-memory layout of the TMA step kernel (bytes; every box 128-byte
-// aligned): [barriers 128 B] [NST input stages] [PSM_TMA_OUT_BUFS output tiles].
+// aligned): [barriers 128 B] [NST input stages] [NOUT output buffers].
 //   input, own-cell modes (two-grid, AA even): one [Q][TY][TX] box per tile
 //     (TX TY = 256): slot i of thread t at element 256 i + t;
 //   input, AA odd (TX = 256, TY = 1): per direction i a record of ROW bytes
@@ -799,10 +820,13 @@ struct TmaLayout {
   static constexpr int OUT = STORE_TMA ? (PSM_THREADS / 32) * WBOX : 0;
   static constexpr int SM_SMEM = 233472;
   static constexpr int BLOCKS = step_min_blocks<S, Q>();
-  static constexpr int BUDGET = (SM_SMEM - BLOCKS * (1024 + 4096)) / BLOCKS - 256 - PSM_TMA_OUT_BUFS * OUT;
-  static constexpr int NST = BUDGET / STAGE < 2 ? 2 : (BUDGET / STAGE > PSM_TMA_MAX_STAGES ? PSM_TMA_MAX_STAGES : BUDGET / STAGE);
+  static constexpr int BUDGET0 = (SM_SMEM - BLOCKS * (1024 + 4096)) / BLOCKS - 256;
+  static constexpr int clamp_st(int n) { return n < 2 ? 2 : (n > PSM_TMA_MAX_STAGES ? PSM_TMA_MAX_STAGES : n); }
+  // output boxes per warp: PSM_TMA_OUT_BUFS where that leaves at least 3 input stages, else 1
+  static constexpr int NOUT = (PSM_TMA_OUT_BUFS > 1 && (BUDGET0 - PSM_TMA_OUT_BUFS * OUT) / STAGE >= 3) ? PSM_TMA_OUT_BUFS : 1;
+  static constexpr int NST = clamp_st((BUDGET0 - NOUT * OUT) / STAGE);
   // + 128 B of barriers, + 128 B of alignment slack
-  static constexpr int SMEM = 256 + NST * STAGE + PSM_TMA_OUT_BUFS * OUT;
+  static constexpr int SMEM = 256 + NST * STAGE + NOUT * OUT;
 };
 
 // ---------------------------------------------------------------------------
@@ -825,7 +849,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   using T = typename Store<S>::T;
   using L = TmaLayout<S, Q, MODE>;
   constexpr int NST = L::NST;
-  constexpr int NOUT = PSM_TMA_OUT_BUFS;
+  constexpr int NOUT = L::NOUT;
   constexpr int EP = L::EP;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
   __shared__ int s_abort;
@@ -863,11 +887,14 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   }
   __syncthreads();
 
-  // producer: the 32 lanes of warp 0 stage the pre-collision PDFs of the
-  // walk's current tile into stage `s`, one copy job per lane, and advance it
+  // producer: the 32 lanes of one warp stage the pre-collision PDFs of the
+  // walk's current tile into stage `s`, one copy job per lane, and advance the
+  // walk.  Warp 0 stages the first NST tiles; afterwards warp w refills the
+  // stage of tile k when k = w (mod NW), so the producer work rotates over the
+  // warps (its walk: tiles w + NST, w + NST + NW, ... of this block).
   TileWalk walk;
-  walk.init(p.t, blockIdx.x, gridDim.x);
-  auto produce = [&](int s) {
+  walk.init(p.t, blockIdx.x + (warp + NST) * gridDim.x, NW * gridDim.x);
+  auto produce = [&](TileWalk& walk, int s) {
     const int z = walk.z;
     const int x0 = walk.tx * TX, y0 = walk.ty * TY;
     walk.advance();
@@ -912,9 +939,11 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   };
 
   if (warp == 0) {
+    TileWalk first;
+    first.init(p.t, blockIdx.x, gridDim.x);
     for (int k = 0; k < NST; ++k) {
       const int tile = blockIdx.x + k * gridDim.x;
-      if (tile < ntiles) produce(k);
+      if (tile < ntiles) produce(first, k);
     }
   }
 
@@ -946,11 +975,11 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
-    if (warp == 0) {
+    if (warp == k % NW) {
       const int next = tile + NST * gridDim.x;
       if (next < ntiles) {
         // warp-uniform outcome (produce needs the whole warp)
-        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (unsigned)((k / NST) & 1)))) produce(s);
+        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (unsigned)((k / NST) & 1)))) produce(walk, s);
         else s_abort = 1;
       }
     }
