@@ -776,9 +776,10 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 #ifndef PSM_TMA_OUT_BUFS
 #define PSM_TMA_OUT_BUFS 2
 #endif
-// 1: the AA even step writes its tiles back with TMA tensor stores (one per warp)
+// 1: the AA even step writes its tiles back with TMA tensor stores (one per
+// warp); 0 (default, measured faster on GB300): plain coalesced stores
 #ifndef PSM_TMA_STORE
-#define PSM_TMA_STORE 1
+#define PSM_TMA_STORE 0
 #endif
 
 
@@ -850,6 +851,13 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   using L = TmaLayout<S, Q, MODE>;
   constexpr int NST = L::NST;
   constexpr int NOUT = L::NOUT;
+  // refill lag in tiles: a stage is refilled LAG tiles after it was read, so the
+  // refilling warp seldom waits for the slowest warp; NST - LAG tiles stay ahead
+#ifdef PSM_TMA_REFILL_LAG
+  constexpr int LAG = PSM_TMA_REFILL_LAG < NST - 1 ? PSM_TMA_REFILL_LAG : NST - 2;
+#else
+  constexpr int LAG = NST >= 4 ? 2 : NST - 2;
+#endif
   constexpr int EP = L::EP;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
   __shared__ int s_abort;
@@ -890,7 +898,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   // producer: the 32 lanes of one warp stage the pre-collision PDFs of the
   // walk's current tile into stage `s`, one copy job per lane, and advance the
   // walk.  Warp 0 stages the first NST tiles; afterwards warp w refills the
-  // stage of tile k when k = w (mod NW), so the producer work rotates over the
+  // stage of tile j when j = w (mod NW), so the producer work rotates over the
   // warps (its walk: tiles w + NST, w + NST + NW, ... of this block).
   TileWalk walk;
   walk.init(p.t, blockIdx.x + (warp + NST) * gridDim.x, NW * gridDim.x);
@@ -975,11 +983,15 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
-    if (warp == k % NW) {
-      const int next = tile + NST * gridDim.x;
+    // refill the stage of tile j = k - LAG (read by every warp by now, as a rule)
+    // with tile j + NST; warp j mod NW does it
+    const int j = k - LAG;
+    if (j >= 0 && warp == j % NW) {
+      const int next = tile + (NST - LAG) * gridDim.x;
       if (next < ntiles) {
+        const int sj = j % NST;
         // warp-uniform outcome (produce needs the whole warp)
-        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (unsigned)((k / NST) & 1)))) produce(walk, s);
+        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[sj], (unsigned)((j / NST) & 1)))) produce(walk, sj);
         else s_abort = 1;
       }
     }
