@@ -415,6 +415,25 @@ void fill_consts(const psm_solver* h, psm::ConstT<T>& c) {
   c.inv_tau = (T)(1.0 / h->col.tau);
   c.tmh = (T)(h->col.tau - 0.5);
   for (int i = 0; i < 27; ++i) c.ghost[i] = (T)h->ghost[i];
+  double omp, omm;
+  if (h->col.fluid == PSM_TRT) {
+    omp = 1.0 / h->col.tau;
+    omm = 1.0 / (h->col.trt_lambda / (h->col.tau - 0.5) + 0.5);
+  } else {
+    omp = omm = 1.0 / h->col.tau;
+  }
+  c.omp1 = (T)(1.0 - omp);
+  c.hp1 = (T)(0.5 * (1.0 - omp));
+  c.hm1 = (T)(0.5 * (1.0 - omm));
+  // weight per class |c|^2 = 0..3 (D3Q19 has no corner directions)
+  const double w19[4] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0, 0.0};
+  const double w27[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+  for (int k = 0; k < 4; ++k) {
+    const double w = h->Q == 19 ? w19[k] : w27[k];
+    c.pw[k] = (T)(omp * w);
+    c.pk[k] = (T)(4.5 * omp * w);
+    c.pd[k] = (T)(3.0 * omm * w);
+  }
 }
 
 // A kernel gave up on a bounded wait: report it once.

@@ -67,6 +67,12 @@ struct ConstT {
   T inv_tau;     // 1 / tau (SC2)
   T tmh;         // tau - 1/2 (Eq. 6)
   T ghost[27];   // shifted ghost-plane populations f^eq_i(rho0, u_in) - w_i rho0
+  // fluid collision (fluid_relax): omega+ = om_a + om_b, omega- = om_a - om_b,
+  // and per weight class c = |c_i|^2 with weight w_c:
+  T omp1, hp1, hm1;  // 1 - omega+, (1 - omega+) / 2, (1 - omega-) / 2
+  T pw[4];        // omega+ w_c
+  T pk[4];        // 4.5 omega+ w_c
+  T pd[4];        // 3 omega- w_c
 };
 
 struct StepParams {

@@ -301,16 +301,24 @@ __device__ __forceinline__ T recip(T r) {
   }
 }
 
-// Density deviation, density and velocity of one cell from its shifted PDFs.
+// |c_i|^2: the weight class of direction i (0 rest, 1 axis, 2 face diagonal, 3 corner)
+__host__ __device__ __forceinline__ constexpr int lat_cls(int i) {
+  return lat_cx(i) * lat_cx(i) + lat_cy(i) * lat_cy(i) + lat_cz(i) * lat_cz(i);
+}
+
+// Density deviation, density and velocity of one cell from its shifted PDFs,
+// summed over opposite pairs (i, i + 1): drho = f_0 + sum (f_i + f_i+1),
+// j = sum c_i (f_i - f_i+1).  Sums start from -0 (x + -0 = x exactly).
 template <class T, int Q>
 __device__ __forceinline__ void moments(const T (&f)[Q], T rho0, T& drho, T& rho, T& ux, T& uy, T& uz, T& uu) {
-  T d = 0, jx = 0, jy = 0, jz = 0;
+  T d = f[0], jx = T(-0.0), jy = T(-0.0), jz = T(-0.0);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    d += f[i];
-    if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
-    if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
-    if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
+  for (int i = 1; i < Q; i += 2) {
+    const T sp = f[i] + f[i + 1], dm = f[i] - f[i + 1];
+    d += sp;
+    if (lat_cx(i)) jx += T(lat_cx(i)) * dm;
+    if (lat_cy(i)) jy += T(lat_cy(i)) * dm;
+    if (lat_cz(i)) jz += T(lat_cz(i)) * dm;
   }
   drho = d;
   rho = rho0 + d;
@@ -321,39 +329,40 @@ __device__ __forceinline__ void moments(const T (&f)[Q], T rho0, T& drho, T& rho
   uu = ux * ux + uy * uy + uz * uz;
 }
 
-// Pure fluid cell: f* = f + Omega^F (Eq. 2, or TRT).  Per opposite pair (i, j),
-// c_j = -c_i, the shifted equilibrium splits into
+// Pure fluid cell: f* = f + Omega^F (TRT; BGK is the case omega+ = omega- =
+// 1/tau).  Per opposite pair (i, j), c_j = -c_i, with s = f_i + f_j and
+// d = f_i - f_j the shifted equilibrium splits into
 //   even = w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)),  odd = 3 w rho (c.u),
-//   f^eq_i - w rho0 = even + odd,  f^eq_j - w rho0 = even - odd.
+//   f^eq_i - w rho0 = even + odd,  f^eq_j - w rho0 = even - odd,
+// and the relaxed pair is f*_i = p + m, f*_j = p - m with
+//   p = (1 - omega+) s / 2 + omega+ even,  m = (1 - omega-) d / 2 + omega- odd.
+// The products of omega+-, the weight and the numeric factors are host
+// constants per weight class (ConstT pw, pk, pd); f_i and f_j are not needed
+// once s and d are formed.
 template <class T, int Q, int TRT>
 __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drho, T rho, T ux, T uy, T uz, T uu) {
-  const T omp = C.om_a + C.om_b, omm = C.om_a - C.om_b;  // omega+ and omega- (BGK: both 1/tau)
   const T base = drho - T(1.5) * rho * uu;
-  {
-    const T n0 = f[0] - T(lat_w<Q>(0)) * base;
-    f[0] = f[0] - omp * n0;
+  constexpr int NC = Q == 27 ? 4 : 3;
+  T A[NC], K[NC], D[NC];  // per class: omega+ w base, 4.5 omega+ w rho, 3 omega- w rho
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    A[c] = C.pw[c] * base;
+    K[c] = C.pk[c] * rho;
+    D[c] = C.pd[c] * rho;
   }
+  f[0] = C.omp1 * f[0] + A[0];
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
-    const int j = i + 1;
-    const T w = T(lat_w<Q>(i));
-    T cu = 0;
+    const int j = i + 1, c = lat_cls(i);
+    T cu = T(-0.0);
     if (lat_cx(i)) cu += T(lat_cx(i)) * ux;
     if (lat_cy(i)) cu += T(lat_cy(i)) * uy;
     if (lat_cz(i)) cu += T(lat_cz(i)) * uz;
-    const T even = w * base + (T(4.5) * w * rho) * (cu * cu);
-    const T odd = (T(3) * w * rho) * cu;
-    if (TRT) {
-      // f* = f - omega+ (f+ - even) - omega- (f- - odd)
-      const T np = T(0.5) * (f[i] + f[j]) - even;
-      const T nm = T(0.5) * (f[i] - f[j]) - odd;
-      const T a = omp * np, b = omm * nm;
-      f[i] = f[i] - a - b;
-      f[j] = f[j] - a + b;
-    } else {
-      f[i] = f[i] + C.om_a * ((even + odd) - f[i]);
-      f[j] = f[j] + C.om_a * ((even - odd) - f[j]);
-    }
+    const T sp = f[i] + f[j], dm = f[i] - f[j];
+    const T pe = C.hp1 * sp + (K[c] * (cu * cu) + A[c]);
+    const T mo = C.hm1 * dm + D[c] * cu;
+    f[i] = pe + mo;
+    f[j] = pe - mo;
   }
 }
 
