@@ -306,27 +306,83 @@ __host__ __device__ __forceinline__ constexpr int lat_cls(int i) {
   return lat_cx(i) * lat_cx(i) + lat_cy(i) * lat_cy(i) + lat_cz(i) * lat_cz(i);
 }
 
+// Separately rounded operations (never contracted or reordered by the
+// compiler): the fluid collision computes the same bits in every kernel that
+// inlines it.
+template <class T>
+__device__ __forceinline__ T r_add(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fadd_rn(a, b);
+  else return __dadd_rn(a, b);
+}
+template <class T>
+__device__ __forceinline__ T r_sub(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fsub_rn(a, b);
+  else return __dsub_rn(a, b);
+}
+template <class T>
+__device__ __forceinline__ T r_mul(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fmul_rn(a, b);
+  else return __dmul_rn(a, b);
+}
+template <class T>
+__device__ __forceinline__ T r_fma(T a, T b, T c) {
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c);
+  else return __fma_rn(a, b, c);
+}
+// a + s b for a lattice component s = +-1
+template <class T>
+__device__ __forceinline__ T r_addc(T a, int s, T b) {
+  return s > 0 ? r_add(a, b) : r_sub(a, b);
+}
+
 // Density deviation, density and velocity of one cell from its shifted PDFs,
 // summed over opposite pairs (i, i + 1): drho = f_0 + sum (f_i + f_i+1),
-// j = sum c_i (f_i - f_i+1).  Sums start from -0 (x + -0 = x exactly).
+// j = sum c_i (f_i - f_i+1).
 template <class T, int Q>
 __device__ __forceinline__ void moments(const T (&f)[Q], T rho0, T& drho, T& rho, T& ux, T& uy, T& uz, T& uu) {
-  T d = f[0], jx = T(-0.0), jy = T(-0.0), jz = T(-0.0);
+  T d = f[0], jx = T(0), jy = T(0), jz = T(0);
+  bool hx = false, hy = false, hz = false;  // compile-time after unrolling
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
-    const T sp = f[i] + f[i + 1], dm = f[i] - f[i + 1];
-    d += sp;
-    if (lat_cx(i)) jx += T(lat_cx(i)) * dm;
-    if (lat_cy(i)) jy += T(lat_cy(i)) * dm;
-    if (lat_cz(i)) jz += T(lat_cz(i)) * dm;
+    const T sp = r_add(f[i], f[i + 1]), dm = r_sub(f[i], f[i + 1]);
+    d = r_add(d, sp);
+    if (lat_cx(i)) {
+      jx = hx ? r_addc(jx, lat_cx(i), dm) : (lat_cx(i) > 0 ? dm : -dm);
+      hx = true;
+    }
+    if (lat_cy(i)) {
+      jy = hy ? r_addc(jy, lat_cy(i), dm) : (lat_cy(i) > 0 ? dm : -dm);
+      hy = true;
+    }
+    if (lat_cz(i)) {
+      jz = hz ? r_addc(jz, lat_cz(i), dm) : (lat_cz(i) > 0 ? dm : -dm);
+      hz = true;
+    }
   }
   drho = d;
-  rho = rho0 + d;
+  rho = r_add(rho0, d);
   const T inv_rho = recip(rho);
-  ux = jx * inv_rho;
-  uy = jy * inv_rho;
-  uz = jz * inv_rho;
-  uu = ux * ux + uy * uy + uz * uz;
+  ux = r_mul(jx, inv_rho);
+  uy = r_mul(jy, inv_rho);
+  uz = r_mul(jz, inv_rho);
+  uu = r_fma(uz, uz, r_fma(uy, uy, r_mul(ux, ux)));
+}
+
+// c_i . u with separately rounded operations
+template <class T>
+__device__ __forceinline__ T c_dot(int i, T ux, T uy, T uz) {
+  T cu = T(0);
+  bool h = false;
+  if (lat_cx(i)) {
+    cu = lat_cx(i) > 0 ? ux : -ux;
+    h = true;
+  }
+  if (lat_cy(i)) {
+    cu = h ? r_addc(cu, lat_cy(i), uy) : (lat_cy(i) > 0 ? uy : -uy);
+    h = true;
+  }
+  if (lat_cz(i)) cu = h ? r_addc(cu, lat_cz(i), uz) : (lat_cz(i) > 0 ? uz : -uz);
+  return cu;
 }
 
 // Pure fluid cell: f* = f + Omega^F (TRT; BGK is the case omega+ = omega- =
@@ -341,28 +397,25 @@ __device__ __forceinline__ void moments(const T (&f)[Q], T rho0, T& drho, T& rho
 // once s and d are formed.
 template <class T, int Q, int TRT>
 __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drho, T rho, T ux, T uy, T uz, T uu) {
-  const T base = drho - T(1.5) * rho * uu;
+  const T base = r_fma(T(-1.5), r_mul(rho, uu), drho);
   constexpr int NC = Q == 27 ? 4 : 3;
   T A[NC], K[NC], D[NC];  // per class: omega+ w base, 4.5 omega+ w rho, 3 omega- w rho
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    A[c] = C.pw[c] * base;
-    K[c] = C.pk[c] * rho;
-    D[c] = C.pd[c] * rho;
+    A[c] = r_mul(C.pw[c], base);
+    K[c] = r_mul(C.pk[c], rho);
+    D[c] = r_mul(C.pd[c], rho);
   }
-  f[0] = C.omp1 * f[0] + A[0];
+  f[0] = r_fma(C.omp1, f[0], A[0]);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const int j = i + 1, c = lat_cls(i);
-    T cu = T(-0.0);
-    if (lat_cx(i)) cu += T(lat_cx(i)) * ux;
-    if (lat_cy(i)) cu += T(lat_cy(i)) * uy;
-    if (lat_cz(i)) cu += T(lat_cz(i)) * uz;
-    const T sp = f[i] + f[j], dm = f[i] - f[j];
-    const T pe = C.hp1 * sp + (K[c] * (cu * cu) + A[c]);
-    const T mo = C.hm1 * dm + D[c] * cu;
-    f[i] = pe + mo;
-    f[j] = pe - mo;
+    const T cu = c_dot(i, ux, uy, uz);
+    const T sp = r_add(f[i], f[j]), dm = r_sub(f[i], f[j]);
+    const T pe = r_fma(C.hp1, sp, r_fma(K[c], r_mul(cu, cu), A[c]));
+    const T mo = r_fma(C.hm1, dm, r_mul(D[c], cu));
+    f[i] = r_add(pe, mo);
+    f[j] = r_sub(pe, mo);
   }
 }
 
