@@ -250,8 +250,8 @@ int psm_mass(psm_handle h, double* out);
 int psm_synchronize(psm_handle h);
 
 /* Step-kernel variant: PSM_KERNEL_AUTO (default) uses the TMA-staged kernel
- * when the shape allows it, else plain global loads, and runs the AA odd step
- * with whichever of the two measured faster on GB300 (plain loads);
+ * for every step the shape allows (the faster variant measured on GB300), else
+ * plain global loads;
  * PSM_KERNEL_PLAIN forces plain loads; PSM_KERNEL_TMA forces TMA staging for
  * every step the shape allows (PSM_ERR_UNSUPPORTED if it allows none).  TMA
  * shapes: with TX = min(256, nx): nx % TX == 0, 256 % nx == 0 when nx < 256,

@@ -131,6 +131,16 @@ namespace psm {
 
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+void set_slots(StepParams& p, int storage, int Q) {
+  const size_t b = storage == PSM_FP64 ? 8 : (storage == PSM_FP32 ? 4 : 2);
+  char* src = static_cast<char*>(p.f);
+  char* dst = static_cast<char*>(p.f_dst ? p.f_dst : p.f);
+  for (int i = 0; i < 27; ++i) {
+    p.src_slot[i] = i < Q ? src + (size_t)i * (size_t)p.g.ncell * b : nullptr;
+    p.dst_slot[i] = i < Q ? dst + (size_t)i * (size_t)p.g.ncell * b : nullptr;
+  }
+}
+
 Tiling make_tiling(int nx, int ny, int nz) {
   Tiling t;
   int tx = ((nx + 31) / 32) * 32;
@@ -332,9 +342,10 @@ int import_uniform(psm_solver* h, double rho, const double u[3]) {
 bool valid_handle(psm_handle h) { return h != nullptr; }
 
 // 1: under PSM_KERNEL_AUTO the AA odd step (per-direction rows) uses plain
-// global loads even where its TMA-staged variant applies.
+// global loads even where its TMA-staged variant applies (0: the TMA variant,
+// measured faster on GB300).
 #ifndef PSM_AA_ODD_PLAIN
-#define PSM_AA_ODD_PLAIN 1
+#define PSM_AA_ODD_PLAIN 0
 #endif
 
 // TMA shape rules (see k_step_tma): TX = min(256, nx), nx % TX == 0,
@@ -845,6 +856,7 @@ int psm_step(psm_handle h, int n) {
       p.f = h->buf[0];
       p.f_dst = nullptr;
     }
+    psm::set_slots(p, h->lat.storage, h->Q);
     // the AA odd step runs with plain loads unless its TMA variant applies
     const bool tma_now = use_tma && (mode != psm::MODE_AA_ODD ||
                                      (h->tma_odd_ok && (h->variant == PSM_KERNEL_TMA || !PSM_AA_ODD_PLAIN)));
@@ -999,6 +1011,7 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
       for (int b = 0; b < nb; ++b) sp.body[b] = dev_body(h, b, n);
       sp.f = slots[(size_t)(n - ns)];
       sp.f_dst = slots[(size_t)(n - ns + 1)];
+      psm::set_slots(sp, h->lat.storage, h->Q);
       e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, sp, st);
     }
     // adjoint steps ne-1 .. ns

@@ -80,6 +80,12 @@ struct StepParams {
   Tiling t;
   void* f;      // AA: the buffer; TG: source
   void* f_dst;  // TG: destination
+  // slot base pointers (set_slots): src_slot[i] = f + i ncell, dst_slot[i] =
+  // (TG: f_dst, AA: f) + i ncell, in elements of the storage type; read from
+  // the parameter bank, so a streamed access costs one 32-bit index and one
+  // address computation
+  void* src_slot[27];
+  void* dst_slot[27];
   int trt;
   int solid;      // 1, 2, 3
   int weighting;  // 0 direct, 1 tau-weighted
@@ -139,6 +145,8 @@ struct RemapParams {
 constexpr int PSM_THREADS = 256;
 
 Tiling make_tiling(int nx, int ny, int nz);
+// fills p.src_slot / p.dst_slot from p.f, p.f_dst (nullptr: in place), p.g.ncell
+void set_slots(StepParams& p, int storage, int Q);
 
 // Launchers (one set per storage precision, in psm_kern_<storage>.cu).  Each
 // returns cudaSuccess or the launch error.  `grid_out` reports the number of

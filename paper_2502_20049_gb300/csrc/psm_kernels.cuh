@@ -565,15 +565,14 @@ struct ZGhost {
 //   TG       cell x + c_i, slot i of the other buffer;
 // with GHOST, populations that leave the domain through a ghost plane are dropped.
 template <class S, int Q, int MODE, bool GHOST, class T>
-__device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Stencil& sn, const ZGhost& zg,
-                                          unsigned cell, const T (&f)[Q]) {
+__device__ __forceinline__ void psm_store(const StepParams& p, const Stencil& sn, const ZGhost& zg, unsigned cell,
+                                          const T (&f)[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (MODE == MODE_AA_EVEN) {
-      Store<S>::st(buf + (long long)lat_opp(i) * N + cell, f[i]);
+      Store<S>::st(static_cast<S*>(p.dst_slot[lat_opp(i)]) + cell, f[i]);
     } else if (!GHOST || !zg.to(lat_cz(i))) {
-      S* base = (MODE == MODE_TG) ? dst : buf;
-      Store<S>::st(base + (long long)i * N + sn.at(lat_cx(i), lat_cy(i), lat_cz(i)), f[i]);
+      Store<S>::st(static_cast<S*>(p.dst_slot[i]) + sn.at(lat_cx(i), lat_cy(i), lat_cz(i)), f[i]);
     }
   }
 }
@@ -582,20 +581,21 @@ __device__ __forceinline__ void psm_store(S* buf, S* dst, long long N, const Ste
 // of x was stored by x - c_i in slot opp(i); otherwise slot i of x); with
 // GHOST, populations entering from a ghost plane take the ghost value.
 template <class S, int Q, int MODE, bool GHOST, class T>
-__device__ __forceinline__ void psm_load(const StepParams& p, const S* buf, long long N, const Stencil& sn,
-                                         const ZGhost& zg, unsigned cell, T (&f)[Q]) {
+__device__ __forceinline__ void psm_load(const StepParams& p, const Stencil& sn, const ZGhost& zg, unsigned cell,
+                                         T (&f)[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
     if (GHOST && zg.from(cz)) {
       f[i] = cst<T>(p).ghost[i];
     } else if (MODE == MODE_AA_ODD) {
-      f[i] = Store<S>::ld(buf + (long long)lat_opp(i) * N + sn.at(-cx, -cy, -cz));
+      f[i] = Store<S>::ld(static_cast<const S*>(p.src_slot[lat_opp(i)]) + sn.at(-cx, -cy, -cz));
     } else {
-      f[i] = Store<S>::ld(buf + (long long)i * N + cell);
+      f[i] = Store<S>::ld(static_cast<const S*>(p.src_slot[i]) + cell);
     }
   }
 }
+
 // Per-warp force/torque accumulation into s_ft[warp] (fixed order: warp
 // butterfly, then in tile order).  All 32 lanes must call it.
 __device__ __forceinline__ void warp_ft(double (*s_ft)[PSM_MAX_BODIES * 6], int nb, bool contributes, int owner,
@@ -699,9 +699,6 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
 
-  S* __restrict__ buf = static_cast<S*>(p.f);
-  S* __restrict__ dst = static_cast<S*>(p.f_dst);
-  const long long N = p.g.ncell;
   const int ntiles = (int)p.t.ntiles;
   const int lx = (int)threadIdx.x % p.t.tx, ly = (int)threadIdx.x / p.t.tx;
 
@@ -718,7 +715,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
       ZGhost zg;
       zg.init(p.g, z);
       T f[Q];
-      psm_load<S, Q, MODE, GEN>(p, buf, N, sn, zg, cell, f);
+      psm_load<S, Q, MODE, GEN>(p, sn, zg, cell, f);
       if (GEN) psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
       else fluid_collide<T, Q, TRT>(p, f);
       if (MODE == MODE_AA_ODD) {
@@ -730,9 +727,9 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
         asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs), "+r"(cs));
         Stencil sn2;
         sn2.init(p.g, xs, ys, zs, cs);
-        psm_store<S, Q, MODE, GEN>(buf, dst, N, sn2, zg, cs, f);
+        psm_store<S, Q, MODE, GEN>(p, sn2, zg, cs, f);
       } else {
-        psm_store<S, Q, MODE, GEN>(buf, dst, N, sn, zg, cell, f);
+        psm_store<S, Q, MODE, GEN>(p, sn, zg, cell, f);
       }
     }
     if (GEN) warp_ft(s_ft, nb, active && solid_cell && owner >= 0, owner, ft);
@@ -941,9 +938,6 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   const int TX = p.t.tx, TY = p.t.ty;
   unsigned char* stages = base + 128;
   unsigned char* outs = stages + NST * L::STAGE;
-  const long long N = p.g.ncell;
-  S* __restrict__ buf = static_cast<S*>(p.f);
-  S* __restrict__ dst = static_cast<S*>(p.f_dst);
   const int ntiles = (int)p.t.ntiles;
 
   if (threadIdx.x == 0) {
@@ -994,7 +988,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
           // cx = +1: cell x0 reads x0 - 1 (the chunk before the row, wrapped in x);
           // cx = -1: cell x0 + 255 reads x0 + 256 (the chunk after it)
           const int xe = cx > 0 ? (x0 == 0 ? p.g.nx - EP : x0 - EP) : (x0 + PSM_THREADS == p.g.nx ? 0 : x0 + PSM_THREADS);
-          const S* src = buf + (long long)slot * N + ((long long)zs * p.g.ny + ys) * p.g.nx + xe;
+          const S* src = static_cast<const S*>(p.src_slot[slot]) + ((long long)zs * p.g.ny + ys) * p.g.nx + xe;
           mbar_expect_tx(bar, 16u);
           bulk_load_16(cx > 0 ? row - 16 : row + PSM_THREADS * (int)sizeof(S), src, bar);
         }
@@ -1080,7 +1074,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     } else {
       Stencil sn;
       sn.init(p.g, x, y, z, cell);
-      psm_store<S, Q, MODE, GEN>(buf, dst, N, sn, zg, cell, f);
+      psm_store<S, Q, MODE, GEN>(p, sn, zg, cell, f);
     }
     if (GEN) warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
   };
