@@ -329,6 +329,10 @@ def run_ours(args):
                 continue
             vs[f"{storage}/{streaming}"] = variant_mlups(args.workload, streaming, storage, "auto", 300, 5, stream)
         line["variants"] = vs
+        # FP16-shifted storage against this storage, same streaming, one GPU each
+        other = "fp16/" + case.streaming
+        if case.storage == "fp32" and other in vs:
+            line["fp16_over_fp32"] = round(vs[other]["mlups"] / (cells * args.steps / t / 1e6), 3)
         line["adjoint"] = adjoint_cost(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
