@@ -289,6 +289,8 @@ int psm_record(psm_handle h, int K, int flags);
  *   grad_uin:   dJ/d u_in (ghost planes, plus the initial state if recorded
  *               with PSM_RECORD_INIT_FROM_INFLOW), 3 doubles (or NULL).
  * Adjoint arithmetic is FP32 (FP64 for PSM_FP64 storage); sums are FP64.
+ * The K - 1 recompute buffers (one state each) stay allocated by the handle
+ * until psm_destroy or a psm_backward with another K.
  * Synchronises; the handle keeps its state and step counter.
  * PSM_ERR_STATE without a recorded forward. */
 int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* grad_omega, double* grad_uin);

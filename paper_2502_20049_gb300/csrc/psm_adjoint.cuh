@@ -64,7 +64,7 @@ __device__ __forceinline__ T phi(int i, T cv, T vv) {
 }
 
 template <class S, int Q, int TRT>
-__global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constant__ AdjParams p) {
+__global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint(const __grid_constant__ AdjParams p) {
   using T = typename Store<S>::T;
   constexpr int NW = PSM_THREADS / 32;
   constexpr int NC = PSM_MAX_BODIES * 3 + 3;
@@ -81,28 +81,34 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
   const ConstT<T>& C = acst<T>(p);
   const T om_a = C.om_a, om_b = C.om_b, inv_tau = C.inv_tau;
   const int ntiles = (int)p.t.ntiles;
+  const int lx = (int)threadIdx.x % p.t.tx, ly = (int)threadIdx.x / p.t.tx;
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int x, y, z;
-    tile_coords(p.t, tile, x, y, z);
+  // One cell.  GEN: the tile meets a body's cell box or a ghost plane; the
+  // other tiles' cells have no owner (u_s = 0, no force/torque weights) and
+  // no ghost populations, and the compiler drops those terms.
+  auto cell_body = [&](auto gen_c, int x, int y, int z) {
+    constexpr bool GEN = decltype(gen_c)::value;
     const bool active = x < p.g.nx && y < p.g.ny;
     double aw0 = 0, aw1 = 0, aw2 = 0, au0 = 0, au1 = 0, au2 = 0;
     bool has_w = false, has_u = false;
     int owner = -1;
     if (active) {
       const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
-      Nbr nbr;
-      nbr.init(p.g, x, y, z);
+      Stencil sn;
+      sn.init(p.g, x, y, z, cell);
+      ZGhost zg;
+      zg.init(p.g, z);
       T f[Q], mu[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
-        if (nbr.from_ghost(cz)) f[i] = C.ghost[i];
+        if (GEN && zg.from(cz)) f[i] = C.ghost[i];
         else f[i] = Store<S>::ld(fb + (long long)i * N + cell);
-        mu[i] = nbr.to_ghost(cz) ? T(0) : lin[(long long)i * N + (unsigned)(cell + nbr.off(cx, cy, cz))];
+        mu[i] = (GEN && zg.to(cz)) ? T(0) : lin[(long long)i * N + sn.at(cx, cy, cz)];
       }
       // ---- forward recomputation (same arithmetic as psm_collide) ----
-      const float epsf = cell_eps(p.body, nb, x, y, z, owner);
+      float epsf = 0.0f;
+      if (GEN) epsf = cell_eps(p.body, nb, x, y, z, owner);
       T e = T(epsf);
       if (p.delta) e += T(p.delta[cell]);
       T Bw = e, Bp = T(1);
@@ -121,12 +127,12 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
         if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
       }
       const T rho = C.rho0 + drho;
-      const T inv_rho = T(1) / rho;
+      const T inv_rho = recip(rho);
       const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
       const T uu = ux * ux + uy * uy + uz * uz;
       T usx = 0, usy = 0, usz = 0;
       double Rx = 0, Ry = 0, Rz = 0;
-      if (owner >= 0) {
+      if (GEN && owner >= 0) {
         const DevBody& b = p.body[owner];
         Rx = (double)x + 0.5 - b.R[0];
         Ry = (double)y + 0.5 - b.R[1];
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
       const T omB = T(1) - Bw;
       // ---- adjoint of the force/torque terms: s = B sum_i Omega^S_i c_i ----
       T sbx = 0, sby = 0, sbz = 0;
-      if (owner >= 0 && Bw > T(0) && p.w) {
+      if (GEN && owner >= 0 && Bw > T(0) && p.w) {
         const double* wv = p.w + owner * 6;
         // J_n = sum_b w_F . F_b + w_T . T_b with F_b = -sum s, T_b = -sum r x s
         sbx = T(-(wv[0] + (wv[4] * Rz - wv[5] * Ry)));
@@ -259,7 +265,7 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
       for (int i = 0; i < Q; ++i) {
         const T l = f[i] + rhob + T(lat_cx(i)) * jbx + T(lat_cy(i)) * jby + T(lat_cz(i)) * jbz;
         lout[(long long)i * N + cell] = l;
-        if (nbr.from_ghost(lat_cz(i))) {
+        if (GEN && zg.from(lat_cz(i))) {
           // the population is the ghost value g_i(u_in)
           au0 += (double)l * p.dghost[i][0];
           au1 += (double)l * p.dghost[i][1];
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
         }
       }
       grad[cell] += (double)(Bbar * Bp);
-      if (owner >= 0) {
+      if (GEN && owner >= 0) {
         // u_s = omega x r + v  =>  d/d omega = r x usbar
         const double a = (double)usbx, b = (double)usby, c = (double)usbz;
         aw0 = Ry * c - Rz * b;
@@ -278,6 +284,7 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
       }
     }
     // ---- per-warp FP64 sums in a fixed order ----
+    if (!GEN) return;
     if (__any_sync(0xffffffffu, has_w)) {
       for (int bi = 0; bi < nb; ++bi) {
         const bool mine = has_w && owner == bi;
@@ -298,6 +305,24 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_adjoint(const __grid_constan
         s_acc[warp][nb * 3 + 2] += v2;
       }
     }
+  };
+
+  TileWalk walk;
+  walk.init(p.t, blockIdx.x, gridDim.x);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, walk.advance()) {
+    const int x0 = walk.tx * p.t.tx, y0 = walk.ty * p.t.ty, z = walk.z;
+    // the forward's classification without the eps perturbation (delta does
+    // not give a cell an owner)
+    bool gen = p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && (z == 0 || z == p.g.nz - 1);
+#pragma unroll
+    for (int bi = 0; bi < PSM_MAX_BODIES; ++bi) {
+      if (bi < nb) {
+        const DevBody& b = p.body[bi];
+        gen = gen || (x0 < b.x1 && x0 + p.t.tx > b.x0 && y0 < b.y1 && y0 + p.t.ty > b.y0 && z >= b.z0 && z < b.z1);
+      }
+    }
+    if (gen) cell_body(BoolC<true>{}, x0 + lx, y0 + ly, z);
+    else cell_body(BoolC<false>{}, x0 + lx, y0 + ly, z);
   }
   __syncthreads();
   __shared__ double blk[NC];

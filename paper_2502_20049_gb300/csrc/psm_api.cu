@@ -125,6 +125,10 @@ struct psm_solver {
   int rec_flags = 0;
   int64_t rec_n0 = 0;
   std::vector<void*> ckpt;
+  // recompute buffers of psm_backward (slot 0 unused: the checkpoint), kept
+  // between calls, and their tensor maps
+  std::vector<void*> rec_slots;
+  std::vector<BufMaps> rec_maps;
 };
 
 namespace psm {
@@ -615,6 +619,7 @@ int psm_destroy(psm_handle h) {
   cudaFree(h->d_delta);
   cudaFree(h->d_err);
   for (void* c : h->ckpt) cudaFree(c);
+  for (void* c : h->rec_slots) cudaFree(c);
   delete h;
   return PSM_OK;
 }
@@ -929,21 +934,39 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
     if (nb < 1) return fail(PSM_ERR_STATE, "default functional (mean torque) needs a body");
     for (int64_t n = 0; n < N; ++n) w[(size_t)n * nb * 6 + 5] = 1.0 / (double)N;
   }
-  // scratch (stream ordered): K - 1 recompute slots, two adjoint fields, accumulators
-  std::vector<void*> slots((size_t)K, nullptr);
+  // K - 1 recompute buffers, allocated once per K and kept by the handle (with
+  // their tensor maps for the TMA-staged recompute)
+  cudaError_t e = cudaSuccess;
+  if ((int)h->rec_slots.size() != K) {
+    PSM_CUDA(cudaStreamSynchronize(st), "synchronise");
+    for (void* c : h->rec_slots) cudaFree(c);
+    h->rec_slots.assign((size_t)K, nullptr);
+    h->rec_maps.assign((size_t)K, BufMaps{});
+    for (int k = 1; k < K && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&h->rec_slots[k], sbytes);
+      if (e == cudaSuccess && h->tma_ok && !encode_maps(h, h->rec_slots[k], h->rec_maps[k]))
+        e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) {
+      for (void* c : h->rec_slots) cudaFree(c);
+      h->rec_slots.clear();
+      h->rec_maps.clear();
+      return cuda_fail(e, "backward recompute buffers");
+    }
+  }
+  std::vector<void*> slots(h->rec_slots);
+  std::vector<BufMaps> smaps(h->rec_maps);
+  const bool tma_rec = h->tma_ok && h->variant != PSM_KERNEL_PLAIN;
+  // scratch (stream ordered): two adjoint fields, accumulators
   void *lam0 = nullptr, *lam1 = nullptr;
   double *grad = nullptr, *wdev = nullptr, *acc = nullptr, *ftscratch = nullptr;
-  cudaError_t e = cudaSuccess;
-  for (int k = 1; k < K && e == cudaSuccess; ++k) e = cudaMallocAsync(&slots[k], sbytes, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&lam0, (size_t)h->Q * ncell * tb, st);
+  e = cudaMallocAsync(&lam0, (size_t)h->Q * ncell * tb, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&lam1, (size_t)h->Q * ncell * tb, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&grad, ncell * sizeof(double), st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&wdev, sizeof(double) * w.size(), st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&acc, sizeof(double) * (size_t)(N + 1) * ncomp, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&ftscratch, sizeof(double) * PSM_MAX_BODIES * 6, st);
   auto release = [&]() {
-    for (void* s : slots)
-      if (s) cudaFreeAsync(s, st);
     cudaFreeAsync(lam0, st);
     cudaFreeAsync(lam1, st);
     cudaFreeAsync(grad, st);
@@ -960,11 +983,12 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, ncell * sizeof(double), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)(N + 1) * ncomp, st);
 
-  // step parameters for the recompute (two-grid, plain loads) and the adjoint
+  // step parameters for the recompute (two-grid; TMA-staged where the shape
+  // allows, like the forward) and the adjoint
   StepParams sp;
   std::memset(&sp, 0, sizeof sp);
   sp.g = h->g;
-  sp.t = h->tiling;
+  sp.t = tma_rec ? h->tma_tiling : h->tiling;
   fill_consts<float>(h, sp.cf);
   fill_consts<double>(h, sp.cd);
   sp.trt = h->col.fluid == PSM_TRT ? 1 : 0;
@@ -1006,13 +1030,23 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
     const int64_t ns = h->rec_n0 + m * K;
     const int64_t ne = std::min<int64_t>(ns + K, h->step);
     slots[0] = h->ckpt[(size_t)m];
+    if (tma_rec && ne - ns > 1 && !encode_maps(h, slots[0], smaps[0])) e = cudaErrorInvalidValue;
     // recompute f^{ns+1} .. f^{ne-1} into the slots
     for (int64_t n = ns; n + 1 < ne && e == cudaSuccess; ++n) {
       for (int b = 0; b < nb; ++b) sp.body[b] = dev_body(h, b, n);
-      sp.f = slots[(size_t)(n - ns)];
-      sp.f_dst = slots[(size_t)(n - ns + 1)];
+      const size_t a = (size_t)(n - ns), c = a + 1;
+      sp.f = slots[a];
+      sp.f_dst = slots[c];
       psm::set_slots(sp, h->lat.storage, h->Q);
-      e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, sp, st);
+      if (tma_rec) {
+        psm::TmaMaps tm;
+        tm.tile = smaps[a].tile;
+        tm.row1 = smaps[a].row1;
+        tm.dstw = smaps[c].warpq;
+        e = psm::launch_step_tma(h->lat.storage, h->Q, psm::MODE_TG, sp, tm, st);
+      } else {
+        e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, sp, st);
+      }
     }
     // adjoint steps ne-1 .. ns
     for (int64_t n = ne - 1; n >= ns && e == cudaSuccess; --n) {
@@ -1026,7 +1060,6 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
       std::swap(la, lb);
     }
   }
-  slots[0] = nullptr;  // checkpoints stay owned by the handle
   if (e == cudaSuccess && (h->rec_flags & PSM_RECORD_INIT_FROM_INFLOW)) {
     ap.lam_in = la;  // lambda^{n0}
     ap.acc_out = acc + (size_t)N * ncomp + nb * 3;
