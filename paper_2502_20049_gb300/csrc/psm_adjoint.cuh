@@ -167,9 +167,11 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
       // ---- reverse sweep over the rest population and the opposite pairs ----
       T Bbar = 0, rhob = 0;
       T ubx = 0, uby = 0, ubz = 0, usbx = 0, usby = 0, usbz = 0;
+      // Without an owner (the fast path), u_s = 0: G_i = f^eq_i(rho, 0) - w_i rho0
+      // = w_i drho, phi_i(0) = w_i, and there is no u_s adjoint to accumulate.
       {
         const T E0 = feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
-        const T G0 = feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
+        const T G0 = GEN ? feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus) : T(lat_w<Q>(0)) * drho;
         const T n0 = f[0] - E0, m0 = f[0] - G0;
         const T of0 = -(om_a + om_b) * n0;
         T os0;
@@ -189,25 +191,29 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
         }
         f[0] = mu[0] + nb0 + mb0;
         const T Eb = -nb0, Gb = -mb0;
-        rhob += Eb * phi<Q, T>(0, T(0), uu) + Gb * phi<Q, T>(0, T(0), usus);
-        const T ke = T(-3) * rho * T(lat_w<Q>(0)) * Eb, kg = T(-3) * rho * T(lat_w<Q>(0)) * Gb;
+        rhob += Eb * phi<Q, T>(0, T(0), uu) + Gb * (GEN ? phi<Q, T>(0, T(0), usus) : T(lat_w<Q>(0)));
+        const T ke = T(-3) * rho * T(lat_w<Q>(0)) * Eb;
         ubx += ke * ux;
         uby += ke * uy;
         ubz += ke * uz;
-        usbx += kg * usx;
-        usby += kg * usy;
-        usbz += kg * usz;
+        if constexpr (GEN) {
+          const T kg = T(-3) * rho * T(lat_w<Q>(0)) * Gb;
+          usbx += kg * usx;
+          usby += kg * usy;
+          usbz += kg * usz;
+        }
       }
 #pragma unroll
       for (int i = 1; i < Q; i += 2) {
         const int j = i + 1;
         const T cx = T(lat_cx(i)), cy = T(lat_cy(i)), cz = T(lat_cz(i));
         const T cu = cx * ux + cy * uy + cz * uz;
-        const T cs = cx * usx + cy * usy + cz * usz;
+        const T cs = GEN ? cx * usx + cy * usy + cz * usz : T(0);
         const T Ei = feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
         const T Ej = feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
-        const T Gi = feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
-        const T Gj = feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
+        const T wd = T(lat_w<Q>(i)) * drho;
+        const T Gi = GEN ? feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus) : wd;
+        const T Gj = GEN ? feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus) : wd;
         const T ni = f[i] - Ei, nj = f[j] - Ej, mi = f[i] - Gi, mj = f[j] - Gj;
         const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
         const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);
@@ -222,10 +228,11 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
           osi = mj - mi;
           osj = mi - mj;
         }
-        const T sci = sbx * cx + sby * cy + sbz * cz;  // sbar . c_i; c_j = -c_i
-        const T osbi = Bw * (mu[i] + sci), osbj = Bw * (mu[j] - sci);
+        const T sci = GEN ? sbx * cx + sby * cy + sbz * cz : T(0);  // sbar . c_i; c_j = -c_i
+        const T osbi = GEN ? Bw * (mu[i] + sci) : Bw * mu[i], osbj = GEN ? Bw * (mu[j] - sci) : Bw * mu[j];
         const T ofbi = omB * mu[i], ofbj = omB * mu[j];
-        Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj) + sci * (osi - osj);
+        if constexpr (GEN) Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj) + sci * (osi - osj);
+        else Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj);
         T nbi = TRT ? (-om_a * ofbi - om_b * ofbj) : (-om_a * ofbi);
         T nbj = TRT ? (-om_a * ofbj - om_b * ofbi) : (-om_a * ofbj);
         T mbi, mbj;
@@ -244,18 +251,23 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
         f[i] = mu[i] + nbi + mbi;
         f[j] = mu[j] + nbj + mbj;
         const T Ebi = -nbi, Ebj = -nbj, Gbi = -mbi, Gbj = -mbj;
-        rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + Gbi * phi<Q, T>(i, cs, usus) +
-                Gbj * phi<Q, T>(j, -cs, usus);
+        if constexpr (GEN)
+          rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + Gbi * phi<Q, T>(i, cs, usus) +
+                  Gbj * phi<Q, T>(j, -cs, usus);
+        else
+          rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + (Gbi + Gbj) * T(lat_w<Q>(i));
         // d f^eq_i / d v = rho w_i (3 c_i + 9 (c_i.v) c_i - 3 v), and c_j = -c_i
         const T rw = rho * T(lat_w<Q>(i));
         const T ae = rw * (T(3) * (Ebi - Ebj) + T(9) * cu * (Ebi + Ebj)), be = T(-3) * rw * (Ebi + Ebj);
-        const T ag = rw * (T(3) * (Gbi - Gbj) + T(9) * cs * (Gbi + Gbj)), bg = T(-3) * rw * (Gbi + Gbj);
         ubx += ae * cx + be * ux;
         uby += ae * cy + be * uy;
         ubz += ae * cz + be * uz;
-        usbx += ag * cx + bg * usx;
-        usby += ag * cy + bg * usy;
-        usbz += ag * cz + bg * usz;
+        if constexpr (GEN) {
+          const T ag = rw * (T(3) * (Gbi - Gbj) + T(9) * cs * (Gbi + Gbj)), bg = T(-3) * rw * (Gbi + Gbj);
+          usbx += ag * cx + bg * usx;
+          usby += ag * cy + bg * usy;
+          usbz += ag * cz + bg * usz;
+        }
       }
       // u = j / rho
       const T jbx = ubx * inv_rho, jby = uby * inv_rho, jbz = ubz * inv_rho;
