@@ -206,9 +206,9 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
 #pragma unroll
       for (int i = 1; i < Q; i += 2) {
         const int j = i + 1;
-        const T cx = T(lat_cx(i)), cy = T(lat_cy(i)), cz = T(lat_cz(i));
-        const T cu = cx * ux + cy * uy + cz * uz;
-        const T cs = GEN ? cx * usx + cy * usy + cz * usz : T(0);
+        const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+        const T cu = cdot(i, ux, uy, uz);
+        const T cs = GEN ? cdot(i, usx, usy, usz) : T(0);
         const T Ei = feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
         const T Ej = feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
         const T wd = T(lat_w<Q>(i)) * drho;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
           osi = mj - mi;
           osj = mi - mj;
         }
-        const T sci = GEN ? sbx * cx + sby * cy + sbz * cz : T(0);  // sbar . c_i; c_j = -c_i
+        const T sci = GEN ? cdot(i, sbx, sby, sbz) : T(0);  // sbar . c_i; c_j = -c_i
         const T osbi = GEN ? Bw * (mu[i] + sci) : Bw * mu[i], osbj = GEN ? Bw * (mu[j] - sci) : Bw * mu[j];
         const T ofbi = omB * mu[i], ofbj = omB * mu[j];
         if constexpr (GEN) Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj) + sci * (osi - osj);
@@ -259,14 +259,14 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
         // d f^eq_i / d v = rho w_i (3 c_i + 9 (c_i.v) c_i - 3 v), and c_j = -c_i
         const T rw = rho * T(lat_w<Q>(i));
         const T ae = rw * (T(3) * (Ebi - Ebj) + T(9) * cu * (Ebi + Ebj)), be = T(-3) * rw * (Ebi + Ebj);
-        ubx += ae * cx + be * ux;
-        uby += ae * cy + be * uy;
-        ubz += ae * cz + be * uz;
+        ubx += cx ? csign(cx, ae) + be * ux : be * ux;
+        uby += cy ? csign(cy, ae) + be * uy : be * uy;
+        ubz += cz ? csign(cz, ae) + be * uz : be * uz;
         if constexpr (GEN) {
           const T ag = rw * (T(3) * (Gbi - Gbj) + T(9) * cs * (Gbi + Gbj)), bg = T(-3) * rw * (Gbi + Gbj);
-          usbx += ag * cx + bg * usx;
-          usby += ag * cy + bg * usy;
-          usbz += ag * cz + bg * usz;
+          usbx += cx ? csign(cx, ag) + bg * usx : bg * usx;
+          usby += cy ? csign(cy, ag) + bg * usy : bg * usy;
+          usbz += cz ? csign(cz, ag) + bg * usz : bg * usz;
         }
       }
       // u = j / rho
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
       // ---- lambda^n = fbar + drho/df rhobar + dj/df . jbar ----
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const T l = f[i] + rhob + T(lat_cx(i)) * jbx + T(lat_cy(i)) * jby + T(lat_cz(i)) * jbz;
+        const T l = f[i] + rhob + cdot(i, jbx, jby, jbz);
         lout[(long long)i * N + cell] = l;
         if (GEN && zg.from(lat_cz(i))) {
           // the population is the ghost value g_i(u_in)

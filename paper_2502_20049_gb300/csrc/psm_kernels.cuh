@@ -209,9 +209,32 @@ struct Nbr {
 
 // Eq. 3 (sign-corrected) minus the storage shift w rho0, for velocity v:
 //   f^eq_i(rho, v) - w_i rho0 = w_i (drho + rho (3 c.v + 4.5 (c.v)^2 - 1.5 v.v))
+// s a for a lattice component s in {-1, 0, 1}, without multiplying (IEEE
+// arithmetic keeps 0 * a, so products with the zero components are avoided)
+template <class T>
+__device__ __forceinline__ T csign(int c, T a) {
+  return c > 0 ? a : (c < 0 ? -a : T(0));
+}
+// c_i . v over the non-zero components of c_i only
+template <class T>
+__device__ __forceinline__ T cdot(int i, T vx, T vy, T vz) {
+  T r = T(0);
+  bool h = false;
+  if (lat_cx(i)) {
+    r = csign(lat_cx(i), vx);
+    h = true;
+  }
+  if (lat_cy(i)) {
+    r = h ? r + csign(lat_cy(i), vy) : csign(lat_cy(i), vy);
+    h = true;
+  }
+  if (lat_cz(i)) r = h ? r + csign(lat_cz(i), vz) : csign(lat_cz(i), vz);
+  return r;
+}
+
 template <int Q, class T>
 __device__ __forceinline__ T feq_shifted(int i, T drho, T rho, T vx, T vy, T vz, T vv) {
-  const T cv = T(lat_cx(i)) * vx + T(lat_cy(i)) * vy + T(lat_cz(i)) * vz;
+  const T cv = cdot(i, vx, vy, vz);
   return T(lat_w<Q>(i)) * (drho + rho * (T(3) * cv + T(4.5) * cv * cv - T(1.5) * vv));
 }
 
