@@ -269,8 +269,9 @@ int psm_set_eps_delta(psm_handle h, const float* delta);
 
 /* Start recording the trajectory for psm_backward at the current step n0:
  * the state is checkpointed now and before every K-th later step (device
- * memory, stream-ordered allocation).  K = 0 stops recording and frees the
- * checkpoints.  With AA streaming, n0 and K must be even.  flags:
+ * memory, stream-ordered allocation), and the buffers of psm_backward are
+ * allocated.  K = 0 stops recording and frees the checkpoints.  With AA
+ * streaming, n0 and K must be even.  flags:
  * PSM_RECORD_INIT_FROM_INFLOW declares that the state at n0 is
  * f^eq(rho0, u_in) (psm_create or psm_init_equilibrium(rho0, u_in)), so that
  * the gradient with respect to u_in includes the initial state. */
@@ -289,8 +290,9 @@ int psm_record(psm_handle h, int K, int flags);
  *   grad_uin:   dJ/d u_in (ghost planes, plus the initial state if recorded
  *               with PSM_RECORD_INIT_FROM_INFLOW), 3 doubles (or NULL).
  * Adjoint arithmetic is FP32 (FP64 for PSM_FP64 storage); sums are FP64.
- * The K - 1 recompute buffers (one state each) stay allocated by the handle
- * until psm_destroy or a psm_backward with another K.
+ * Its buffers (K - 1 recompute states, two adjoint fields, the FP64
+ * gradient) are allocated by psm_record and kept by the handle until
+ * psm_destroy or a recording with another K.
  * Synchronises; the handle keeps its state and step counter.
  * PSM_ERR_STATE without a recorded forward. */
 int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* grad_omega, double* grad_uin);

@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
       // Without an owner (the fast path), u_s = 0: G_i = f^eq_i(rho, 0) - w_i rho0
       // = w_i drho, phi_i(0) = w_i, and there is no u_s adjoint to accumulate.
       {
-        const T E0 = feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
-        const T G0 = GEN ? feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus) : T(lat_w<Q>(0)) * drho;
+        const T E0 = feq_shifted_nz<Q, T>(0, drho, rho, ux, uy, uz, uu);
+        const T G0 = GEN ? feq_shifted_nz<Q, T>(0, drho, rho, usx, usy, usz, usus) : T(lat_w<Q>(0)) * drho;
         const T n0 = f[0] - E0, m0 = f[0] - G0;
         const T of0 = -(om_a + om_b) * n0;
         T os0;
@@ -209,11 +209,11 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
         const T cu = cdot(i, ux, uy, uz);
         const T cs = GEN ? cdot(i, usx, usy, usz) : T(0);
-        const T Ei = feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
-        const T Ej = feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
+        const T Ei = feq_shifted_nz<Q, T>(i, drho, rho, ux, uy, uz, uu);
+        const T Ej = feq_shifted_nz<Q, T>(j, drho, rho, ux, uy, uz, uu);
         const T wd = T(lat_w<Q>(i)) * drho;
-        const T Gi = GEN ? feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus) : wd;
-        const T Gj = GEN ? feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus) : wd;
+        const T Gi = GEN ? feq_shifted_nz<Q, T>(i, drho, rho, usx, usy, usz, usus) : wd;
+        const T Gj = GEN ? feq_shifted_nz<Q, T>(j, drho, rho, usx, usy, usz, usus) : wd;
         const T ni = f[i] - Ei, nj = f[j] - Ej, mi = f[i] - Gi, mj = f[j] - Gj;
         const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
         const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);

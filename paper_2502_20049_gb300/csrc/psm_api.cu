@@ -129,6 +129,8 @@ struct psm_solver {
   // between calls, and their tensor maps
   std::vector<void*> rec_slots;
   std::vector<BufMaps> rec_maps;
+  void* rec_lam[2] = {nullptr, nullptr};  // the two adjoint fields
+  double* rec_grad = nullptr;             // dJ/d delta accumulator
 };
 
 namespace psm {
@@ -620,6 +622,9 @@ int psm_destroy(psm_handle h) {
   cudaFree(h->d_err);
   for (void* c : h->ckpt) cudaFree(c);
   for (void* c : h->rec_slots) cudaFree(c);
+  cudaFree(h->rec_lam[0]);
+  cudaFree(h->rec_lam[1]);
+  cudaFree(h->rec_grad);
   delete h;
   return PSM_OK;
 }
@@ -895,6 +900,37 @@ int psm_set_eps_delta(psm_handle h, const float* delta) {
   return PSM_OK;
 }
 
+// Buffers of psm_backward, allocated when recording starts (a one-time cost
+// outside the backward sweep) and kept by the handle: K - 1 recompute states
+// with their tensor maps, two adjoint fields, the gradient accumulator.
+int ensure_backward_buffers(psm_solver* h, int K) {
+  const size_t ncell = (size_t)h->g.ncell;
+  const size_t tb = h->lat.storage == PSM_FP64 ? 8 : 4;
+  cudaError_t e = cudaSuccess;
+  if ((int)h->rec_slots.size() != K) {
+    PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+    for (void* c : h->rec_slots) cudaFree(c);
+    h->rec_slots.assign((size_t)K, nullptr);
+    h->rec_maps.assign((size_t)K, BufMaps{});
+    for (int k = 1; k < K && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&h->rec_slots[k], state_bytes(h));
+      if (e == cudaSuccess && h->tma_ok && !encode_maps(h, h->rec_slots[k], h->rec_maps[k]))
+        e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) {
+      for (void* c : h->rec_slots) cudaFree(c);
+      h->rec_slots.clear();
+      h->rec_maps.clear();
+      return cuda_fail(e, "backward recompute buffers");
+    }
+  }
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    if (!h->rec_lam[k]) e = cudaMalloc(&h->rec_lam[k], (size_t)h->Q * ncell * tb);
+  if (e == cudaSuccess && !h->rec_grad) e = cudaMalloc((void**)&h->rec_grad, ncell * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e, "backward buffers");
+  return PSM_OK;
+}
+
 int psm_record(psm_handle h, int K, int flags) {
   if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_record: NULL handle");
   drop_checkpoints(h);
@@ -905,6 +941,10 @@ int psm_record(psm_handle h, int K, int flags) {
     return fail(PSM_ERR_ARG, "AA streaming: record from an even step with an even K (checkpoints need the "
                              "natural layout)");
   if (flags & ~PSM_RECORD_INIT_FROM_INFLOW) return fail(PSM_ERR_ARG, "unknown record flags");
+  {
+    const int rc = ensure_backward_buffers(h, K);
+    if (rc != PSM_OK) return rc;
+  }
   h->rec_K = K;
   h->rec_flags = flags;
   h->rec_n0 = h->step;
@@ -924,7 +964,6 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   const int ncomp = nb * 3 + 3;
   const size_t ncell = (size_t)h->g.ncell;
   const size_t tb = h->lat.storage == PSM_FP64 ? 8 : 4;
-  const size_t sbytes = state_bytes(h);
   cudaStream_t st = h->stream;
   // weights of J on the force/torque series
   std::vector<double> w((size_t)N * nb * 6, 0.0);
@@ -934,42 +973,24 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
     if (nb < 1) return fail(PSM_ERR_STATE, "default functional (mean torque) needs a body");
     for (int64_t n = 0; n < N; ++n) w[(size_t)n * nb * 6 + 5] = 1.0 / (double)N;
   }
-  // K - 1 recompute buffers, allocated once per K and kept by the handle (with
-  // their tensor maps for the TMA-staged recompute)
-  cudaError_t e = cudaSuccess;
-  if ((int)h->rec_slots.size() != K) {
-    PSM_CUDA(cudaStreamSynchronize(st), "synchronise");
-    for (void* c : h->rec_slots) cudaFree(c);
-    h->rec_slots.assign((size_t)K, nullptr);
-    h->rec_maps.assign((size_t)K, BufMaps{});
-    for (int k = 1; k < K && e == cudaSuccess; ++k) {
-      e = cudaMalloc(&h->rec_slots[k], sbytes);
-      if (e == cudaSuccess && h->tma_ok && !encode_maps(h, h->rec_slots[k], h->rec_maps[k]))
-        e = cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) {
-      for (void* c : h->rec_slots) cudaFree(c);
-      h->rec_slots.clear();
-      h->rec_maps.clear();
-      return cuda_fail(e, "backward recompute buffers");
-    }
+  // recompute buffers, adjoint fields and gradient accumulator: allocated by
+  // psm_record (ensure_backward_buffers)
+  {
+    const int rc = ensure_backward_buffers(h, K);
+    if (rc != PSM_OK) return rc;
   }
   std::vector<void*> slots(h->rec_slots);
   std::vector<BufMaps> smaps(h->rec_maps);
   const bool tma_rec = h->tma_ok && h->variant != PSM_KERNEL_PLAIN;
-  // scratch (stream ordered): two adjoint fields, accumulators
-  void *lam0 = nullptr, *lam1 = nullptr;
-  double *grad = nullptr, *wdev = nullptr, *acc = nullptr, *ftscratch = nullptr;
-  e = cudaMallocAsync(&lam0, (size_t)h->Q * ncell * tb, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&lam1, (size_t)h->Q * ncell * tb, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&grad, ncell * sizeof(double), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&wdev, sizeof(double) * w.size(), st);
+  void* lam0 = h->rec_lam[0];
+  void* lam1 = h->rec_lam[1];
+  double* grad = h->rec_grad;
+  // small scratch (stream ordered): the weights and the per-step accumulators
+  double *wdev = nullptr, *acc = nullptr, *ftscratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&wdev, sizeof(double) * w.size(), st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&acc, sizeof(double) * (size_t)(N + 1) * ncomp, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&ftscratch, sizeof(double) * PSM_MAX_BODIES * 6, st);
   auto release = [&]() {
-    cudaFreeAsync(lam0, st);
-    cudaFreeAsync(lam1, st);
-    cudaFreeAsync(grad, st);
     cudaFreeAsync(wdev, st);
     cudaFreeAsync(acc, st);
     cudaFreeAsync(ftscratch, st);

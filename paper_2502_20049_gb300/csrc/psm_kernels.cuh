@@ -207,8 +207,6 @@ struct Nbr {
   __device__ __forceinline__ bool to_ghost(int cz) const { return (cz > 0 && zhi_out) || (cz < 0 && zlo_out); }
 };
 
-// Eq. 3 (sign-corrected) minus the storage shift w rho0, for velocity v:
-//   f^eq_i(rho, v) - w_i rho0 = w_i (drho + rho (3 c.v + 4.5 (c.v)^2 - 1.5 v.v))
 // s a for a lattice component s in {-1, 0, 1}, without multiplying (IEEE
 // arithmetic keeps 0 * a, so products with the zero components are avoided)
 template <class T>
@@ -232,8 +230,17 @@ __device__ __forceinline__ T cdot(int i, T vx, T vy, T vz) {
   return r;
 }
 
+// Eq. 3 (sign-corrected) minus the storage shift w rho0, for velocity v:
+//   f^eq_i(rho, v) - w_i rho0 = w_i (drho + rho (3 c.v + 4.5 (c.v)^2 - 1.5 v.v))
 template <int Q, class T>
 __device__ __forceinline__ T feq_shifted(int i, T drho, T rho, T vx, T vy, T vz, T vv) {
+  const T cv = T(lat_cx(i)) * vx + T(lat_cy(i)) * vy + T(lat_cz(i)) * vz;
+  return T(lat_w<Q>(i)) * (drho + rho * (T(3) * cv + T(4.5) * cv * cv - T(1.5) * vv));
+}
+// the same over the non-zero components of c_i only (fewer instructions; the
+// adjoint kernel's form)
+template <int Q, class T>
+__device__ __forceinline__ T feq_shifted_nz(int i, T drho, T rho, T vx, T vy, T vz, T vv) {
   const T cv = cdot(i, vx, vy, vz);
   return T(lat_w<Q>(i)) * (drho + rho * (T(3) * cv + T(4.5) * cv * cv - T(1.5) * vv));
 }
