@@ -41,6 +41,10 @@ struct AdjParams {
   double* acc_out;      // [nbodies * 3 + 3]: dJ/d omega per body, dJ/d u_in
   ConstT<float> cf;
   ConstT<double> cd;
+  // slot base pointers (elements): f + i ncell (storage S), lam_in / lam_out + i ncell (T)
+  const void* f_slot[27];
+  const void* lin_slot[27];
+  void* lout_slot[27];
 };
 
 #define PSM_DECLARE_ADJOINT(NAME)                                                              \
@@ -63,6 +67,84 @@ __device__ __forceinline__ T phi(int i, T cv, T vv) {
   return T(lat_w<Q>(i)) * (T(1) + T(3) * cv + T(4.5) * cv * cv - T(1.5) * vv);
 }
 
+// Adjoint of one cell whose forward is the pure fluid collision (B = 0: no
+// body box and no eps perturbation in its tile, so u_s = 0 and nothing of the
+// force/torque) with no ghost population.  mu_i = lambda^{n+1}_i(x + c_i).
+// Writes lambda^n(x) to lam and returns mu . d post / d B (the factor of
+// B'(eps) in dJ/d delta).  The forward per opposite pair (fluid_relax):
+//   p = (1 - w+) s/2 + w+ even,  m = (1 - w-) d/2 + w- odd,  f*_i = p + m, f*_j = p - m,
+//   even = w (base + 4.5 rho cu^2), odd = 3 w rho cu,  base = drho - 1.5 rho u.u;
+// reversed with pb = mu_i + mu_j, mb = mu_i - mu_j:
+//   fbar_i = (1 - w+)/2 pb + (1 - w-)/2 mb,  fbar_j = (1 - w+)/2 pb - (1 - w-)/2 mb,
+//   basebar += w w+ pb,  rhobar += cu (4.5 w w+ cu pb + 3 w w- mb),
+//   ubar += rho c (9 w w+ cu pb + 3 w w- mb),
+// then through base, u = j / rho and the moments.  The B-derivative
+// mu . (Omega^S - Omega^F) per pair, with G = w drho (f^eq at u_s = 0) and
+// mu . Omega^F = w+ pb (even - s/2) + w- mb (odd - d/2):
+//   SC1: mu . Omega^S = (G - even) pb + (odd - d) mb
+//   SC2: mu . Omega^S = (G pb - (pb s + mb d)/2) / tau
+//   SC3: mu . Omega^S = -d mb
+template <class T, int Q>
+__device__ __forceinline__ T adj_fluid_cell(const ConstT<T>& C, int solid, T inv_tau, const T (&f)[Q],
+                                            const T (&mu)[Q], T (&lam)[Q]) {
+  const T omp = C.om_a + C.om_b, omm = C.om_a - C.om_b;
+  T drho, rho, ux, uy, uz, uu;
+  moments<T, Q>(f, C.rho0, drho, rho, ux, uy, uz, uu);
+  const T inv_rho = recip(rho);
+  const T base = drho - T(1.5) * rho * uu;
+  // rest population: f*_0 = (1 - w+) f_0 + w+ w_0 base
+  T baseb = C.pw[0] * mu[0];
+  lam[0] = C.omp1 * mu[0];
+  T bb;
+  {
+    const T w0 = T(lat_w<Q>(0));
+    const T n0 = f[0] - w0 * base, m0 = f[0] - w0 * drho;
+    const T os0 = solid == PSM_SC1 ? n0 - m0 : (solid == PSM_SC2 ? -m0 * inv_tau : T(0));
+    bb = mu[0] * (os0 + omp * n0);
+  }
+  T rhob = T(0), upx = T(0), upy = T(0), upz = T(0);  // upx..: u adjoint along c, without the factor rho
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int j = i + 1, c = lat_cls(i);
+    const T w = T(lat_w<Q>(i));
+    const T cu = cdot(i, ux, uy, uz);
+    const T sp = f[i] + f[j], dm = f[i] - f[j];
+    const T pb = mu[i] + mu[j], mb = mu[i] - mu[j];
+    const T a1 = C.pk[c] * cu;
+    const T t = a1 * pb + C.pd[c] * mb;
+    rhob += cu * t;
+    const T t2 = a1 * pb + t;
+    if (lat_cx(i)) upx += csign(lat_cx(i), t2);
+    if (lat_cy(i)) upy += csign(lat_cy(i), t2);
+    if (lat_cz(i)) upz += csign(lat_cz(i), t2);
+    baseb += C.pw[c] * pb;
+    const T hm = C.hm1 * mb;
+    lam[i] = C.hp1 * pb + hm;
+    lam[j] = C.hp1 * pb - hm;
+    // mu . (Omega^S - Omega^F) of the pair
+    const T wr = w * rho;
+    const T even = w * base + T(4.5) * wr * (cu * cu), odd = T(3) * wr * cu;
+    const T muof = omp * pb * (even - T(0.5) * sp) + omm * mb * (odd - T(0.5) * dm);
+    T muos;
+    if (solid == PSM_SC1) muos = (w * drho - even) * pb + (odd - dm) * mb;
+    else if (solid == PSM_SC2) muos = (w * drho * pb - T(0.5) * (pb * sp + mb * dm)) * inv_tau;
+    else muos = -dm * mb;
+    bb += muos - muof;
+  }
+  // base = drho - 1.5 rho u.u
+  T drhob = baseb;
+  rhob += T(-1.5) * uu * baseb;
+  const T uub = T(-1.5) * rho * baseb;
+  // u.u, then u = j / rho
+  const T ubx = rho * upx + T(2) * ux * uub, uby = rho * upy + T(2) * uy * uub, ubz = rho * upz + T(2) * uz * uub;
+  const T jbx = ubx * inv_rho, jby = uby * inv_rho, jbz = ubz * inv_rho;
+  rhob -= (ubx * ux + uby * uy + ubz * uz) * inv_rho;
+  drhob += rhob;  // rho = rho0 + drho
+#pragma unroll
+  for (int i = 0; i < Q; ++i) lam[i] += drhob + cdot(i, jbx, jby, jbz);
+  return bb;
+}
+
 template <class S, int Q, int TRT>
 __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint(const __grid_constant__ AdjParams p) {
   using T = typename Store<S>::T;
@@ -73,19 +155,16 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
   const int ncomp = nb * 3 + 3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < NC; k += 32) s_acc[warp][k] = 0.0;
-  const S* __restrict__ fb = static_cast<const S*>(p.f);
-  const T* __restrict__ lin = static_cast<const T*>(p.lam_in);
-  T* __restrict__ lout = static_cast<T*>(p.lam_out);
   double* __restrict__ grad = p.grad;
-  const long long N = p.g.ncell;
   const ConstT<T>& C = acst<T>(p);
   const T om_a = C.om_a, om_b = C.om_b, inv_tau = C.inv_tau;
   const int ntiles = (int)p.t.ntiles;
   const int lx = (int)threadIdx.x % p.t.tx, ly = (int)threadIdx.x / p.t.tx;
+  // B'(0): the derivative of the weighting at eps = 0 (fluid-only tiles)
+  const T Bp0 = p.weighting == PSM_B_TAU_WEIGHTED ? C.tmh / (T(1) + C.tmh) : T(1);
 
-  // One cell.  GEN: the tile meets a body's cell box or a ghost plane; the
-  // other tiles' cells have no owner (u_s = 0, no force/torque weights) and
-  // no ghost populations, and the compiler drops those terms.
+  // One cell.  GEN: the tile meets a body's cell box, a ghost plane, or an eps
+  // perturbation is set; the other tiles' cells take adj_fluid_cell.
   auto cell_body = [&](auto gen_c, int x, int y, int z) {
     constexpr bool GEN = decltype(gen_c)::value;
     const bool active = x < p.g.nx && y < p.g.ny;
@@ -103,9 +182,16 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
       for (int i = 0; i < Q; ++i) {
         const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
         if (GEN && zg.from(cz)) f[i] = C.ghost[i];
-        else f[i] = Store<S>::ld(fb + (long long)i * N + cell);
-        mu[i] = (GEN && zg.to(cz)) ? T(0) : lin[(long long)i * N + sn.at(cx, cy, cz)];
+        else f[i] = Store<S>::ld(static_cast<const S*>(p.f_slot[i]) + cell);
+        mu[i] = (GEN && zg.to(cz)) ? T(0) : static_cast<const T*>(p.lin_slot[i])[sn.at(cx, cy, cz)];
       }
+      if constexpr (!GEN) {
+        T lam[Q];
+        const T bb = adj_fluid_cell<T, Q>(C, p.solid, inv_tau, f, mu, lam);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) static_cast<T*>(p.lout_slot[i])[cell] = lam[i];
+        grad[cell] += (double)(bb * Bp0);
+      } else {
       // ---- forward recomputation (same arithmetic as psm_collide) ----
       float epsf = 0.0f;
       if (GEN) epsf = cell_eps(p.body, nb, x, y, z, owner);
@@ -276,7 +362,7 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const T l = f[i] + rhob + cdot(i, jbx, jby, jbz);
-        lout[(long long)i * N + cell] = l;
+        static_cast<T*>(p.lout_slot[i])[cell] = l;
         if (GEN && zg.from(lat_cz(i))) {
           // the population is the ghost value g_i(u_in)
           au0 += (double)l * p.dghost[i][0];
@@ -293,6 +379,7 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
         aw1 = Rz * a - Rx * c;
         aw2 = Rx * b - Ry * a;
         has_w = true;
+      }
       }
     }
     // ---- per-warp FP64 sums in a fixed order ----
@@ -323,9 +410,8 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
   walk.init(p.t, blockIdx.x, gridDim.x);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, walk.advance()) {
     const int x0 = walk.tx * p.t.tx, y0 = walk.ty * p.t.ty, z = walk.z;
-    // the forward's classification without the eps perturbation (delta does
-    // not give a cell an owner)
-    bool gen = p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && (z == 0 || z == p.g.nz - 1);
+    // the forward's classification (fluid-only: B = 0 in the whole tile)
+    bool gen = p.delta != nullptr || (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && (z == 0 || z == p.g.nz - 1));
 #pragma unroll
     for (int bi = 0; bi < PSM_MAX_BODIES; ++bi) {
       if (bi < nb) {

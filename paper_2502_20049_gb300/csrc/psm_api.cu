@@ -1075,6 +1075,15 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
       ap.f = slots[(size_t)(n - ns)];
       ap.lam_in = la;
       ap.lam_out = lb;
+      {
+        const size_t fb = storage_bytes(h->lat.storage);
+        for (int i = 0; i < 27; ++i) {
+          const bool in = i < h->Q;
+          ap.f_slot[i] = in ? static_cast<const char*>(ap.f) + (size_t)i * ncell * fb : nullptr;
+          ap.lin_slot[i] = in ? static_cast<const char*>(la) + (size_t)i * ncell * tb : nullptr;
+          ap.lout_slot[i] = in ? static_cast<char*>(lb) + (size_t)i * ncell * tb : nullptr;
+        }
+      }
       ap.w = wdev + (size_t)(n - h->rec_n0) * nb * 6;
       ap.acc_out = acc + (size_t)(n - h->rec_n0) * ncomp;
       e = launch_adjoint(h->lat.storage, h->Q, ap.trt, ap, st);
