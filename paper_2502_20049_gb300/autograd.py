@@ -39,10 +39,14 @@ class PSMTorque(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gJ):
-        ge, gw, gu = ctx.sol.backward()
+        # the eps gradient is written straight into a tensor on eps_delta's
+        # device (HBM for a CUDA tensor: no host round trip)
+        c = ctx.sol.cfg
+        ge = torch.empty((c.nz, c.ny, c.nx), dtype=torch.float64, device=ctx.device)
+        _, gw, gu = ctx.sol.backward(grad_eps=ge)
         g = float(gJ)
         ctx.sol.close()
-        grad_eps = torch.from_numpy(np.asarray(ge) * g).to(device=ctx.device, dtype=ctx.dtype)
+        grad_eps = (ge * g).to(dtype=ctx.dtype)
         grad_omega = torch.from_numpy(np.asarray(gw[0]) * g)
         grad_u = torch.from_numpy(np.asarray(gu) * g)
         return grad_eps, grad_omega, grad_u, None, None, None
