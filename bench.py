@@ -36,10 +36,13 @@ METRIC = "PSM-LBM MLUPS on 1×GB300 and % of HBM roofline; adjoint/forward step 
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per cell update of the step kernel, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum over one launch / cells) for the
-# workload and access pattern named in the key; None until captured for the
-# kernel as it is now.
-NCU_BYTES_PER_CELL = {}
+# (dram__bytes_read.sum + dram__bytes_write.sum over one launch / cells; one
+# full-size launch of the 256^3 workload) for the workload, streaming, storage
+# and kernel variant named in the key, as the kernel is now.
+NCU_BYTES_PER_CELL = {
+    "c2/twogrid/fp32/tma": 2.503120e9 / 16777216,
+    "c2/twogrid/fp16/tma": 1.234720e9 / 16777216,
+}
 
 
 def workload(name: str, streaming: str):
