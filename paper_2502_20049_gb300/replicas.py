@@ -16,18 +16,25 @@ def env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def init(backend: str | None = None):
-    """Initialise torch.distributed when WORLD_SIZE > 1; returns the module or None."""
+def init(backend: str | None = None, timeout_s: float | None = None):
+    """Initialise torch.distributed when WORLD_SIZE > 1; returns the module or None.
+
+    timeout_s bounds every collective: a rank that left (raised, exited) makes
+    the others' next barrier or reduction fail with an error after at most
+    that long instead of waiting forever (None: torch's default)."""
     rank, world, _ = env()
     if world <= 1:
         return None
+    import datetime
+
     import torch
     import torch.distributed as dist
 
     if not dist.is_initialized():
         if backend is None:
             backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
+        kw = {} if timeout_s is None else {"timeout": datetime.timedelta(seconds=timeout_s)}
+        dist.init_process_group(backend, **kw)
     return dist
 
 

@@ -48,6 +48,46 @@ def test_two_gloo_ranks_max_time_and_rate():
         assert rate == pytest.approx(100.0 * 2 / 2.0)
 
 
+def _leaving_worker(rank, world, port, out):
+    """Rank 1 leaves between steps (after the barrier, before the reduction);
+    rank 0 must get an error from its next collective, not wait forever."""
+    import time
+
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    from paper_2502_20049_gb300 import replicas
+
+    dist = replicas.init("gloo", timeout_s=5.0)
+    replicas.barrier(dist)
+    if rank == 1:
+        os._exit(3)  # a rank that leaves without a clean shutdown
+    t0 = time.perf_counter()
+    try:
+        replicas.max_over_ranks(dist, 1.0)
+        out.put((0, "no error"))
+    except Exception as e:  # noqa: BLE001 - any collective error is the detection
+        out.put((0, f"error after {time.perf_counter() - t0:.1f} s: {type(e).__name__}"))
+
+
+def test_rank_that_leaves_is_detected_by_the_others():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_leaving_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, msg = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    assert rank == 0 and procs[1].exitcode == 3 and procs[0].exitcode == 0
+    assert msg.startswith("error after"), msg
+    assert float(msg.split()[2]) < 30.0
+
+
 def test_single_rank_defaults(monkeypatch):
     from paper_2502_20049_gb300 import replicas
 
