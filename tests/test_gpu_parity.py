@@ -71,12 +71,14 @@ def test_c2_reduced_fp16():
     assert err <= 2e-3
 
 
-def test_c2_reduced_bf16_reported():
+def test_c2_reduced_bf16():
+    """BF16 keeps 8 mantissa bits (unit round-off 2^-9, 16x FP16's): the FP16
+    bar scaled by that ratio rounds to 2e-2 (no stated bar for BF16)."""
     case = c2_reduced("bf16")
     g, o = run_gpu(case), run_oracle(case)
     err = u_err(g, o, case)
-    print(f"bf16 shifted storage: velocity L_inf / |u_in| = {err:.3e} (no bar)")
-    assert np.isfinite(err) and err < 0.5
+    print(f"bf16 shifted storage: velocity L_inf / |u_in| = {err:.3e}")
+    assert err <= 2e-2
 
 
 def test_eps_bitwise_every_step():
