@@ -55,6 +55,7 @@ struct BufMaps {
 
 struct HostBody {
   unsigned long long* d_bricks = nullptr;
+  unsigned char* d_occ = nullptr;  // occupancy (DevBody::occ)
   int64_t gx = 0, gy = 0, gz = 0;
   int s = 0, wpb = 1;
   double lo[3] = {0, 0, 0};
@@ -225,6 +226,37 @@ __global__ void k_remap(const __grid_constant__ RemapParams p) {
   }
 }
 
+// one thread per occupancy cell c in [-1, g - 1]^3
+__global__ void k_occupancy(const unsigned long long* __restrict__ bricks, int gx, int gy, int gz, int wpb,
+                            unsigned char* __restrict__ occ) {
+  const long long n = (long long)(gx + 1) * (gy + 1) * (gz + 1);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int cx = (int)(idx % (gx + 1)) - 1;
+    const int cy = (int)((idx / (gx + 1)) % (gy + 1)) - 1;
+    const int cz = (int)(idx / ((long long)(gx + 1) * (gy + 1))) - 1;
+    unsigned long long any = 0ull;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int x = cx + dx, y = cy + dy, z = cz + dz;
+          if (x < 0 || y < 0 || z < 0 || x >= gx || y >= gy || z >= gz) continue;
+          const unsigned long long* w = bricks + (((long long)z * gy + y) * gx + x) * wpb;
+          for (int k = 0; k < wpb; ++k) any |= w[k];
+        }
+    occ[idx] = any ? 1 : 0;
+  }
+}
+
+cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, int gz, int wpb, unsigned char* occ,
+                             cudaStream_t st) {
+  const long long n = (long long)(gx + 1) * (gy + 1) * (gz + 1);
+  long long b = (n + PSM_THREADS - 1) / PSM_THREADS;
+  if (b > 4096) b = 4096;
+  k_occupancy<<<(int)(b < 1 ? 1 : b), PSM_THREADS, 0, st>>>(bricks, gx, gy, gz, wpb, occ);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_remap(const RemapParams& p, cudaStream_t st) {
   long long cells = (long long)p.g.nx * p.g.ny * (p.z_end - p.z_begin);
   long long b = (cells + PSM_THREADS - 1) / PSM_THREADS;
@@ -264,6 +296,7 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
   double Q[9], R[3];
   body_pose(b, n, Q, R);
   d.bricks = b.d_bricks;
+  d.occ = b.d_occ;
   d.gx = (int)b.gx;
   d.gy = (int)b.gy;
   d.gz = (int)b.gz;
@@ -613,7 +646,10 @@ int psm_destroy(psm_handle h) {
   if (!h) return PSM_OK;
   if (h->stream || h->buf[0]) cudaStreamSynchronize(h->stream);
   for (int b = 0; b < 2; ++b) cudaFree(h->buf[b]);
-  for (int b = 0; b < PSM_MAX_BODIES; ++b) cudaFree(h->body[b].d_bricks);
+  for (int b = 0; b < PSM_MAX_BODIES; ++b) {
+    cudaFree(h->body[b].d_bricks);
+    cudaFree(h->body[b].d_occ);
+  }
   cudaFree(h->d_partials);
   cudaFree(h->d_ticket);
   cudaFree(h->d_series);
@@ -806,6 +842,13 @@ int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const 
   PSM_CUDA(cudaMalloc(&b.d_bricks, words * sizeof(unsigned long long)), "geometry field allocation");
   PSM_CUDA(cudaMemcpy(b.d_bricks, field->bricks, words * sizeof(unsigned long long), cudaMemcpyDefault),
            "geometry field upload");
+  cudaFree(b.d_occ);
+  b.d_occ = nullptr;
+  const size_t nocc = (size_t)(field->gx + 1) * (field->gy + 1) * (field->gz + 1);
+  PSM_CUDA(cudaMalloc(&b.d_occ, nocc), "geometry occupancy allocation");
+  PSM_CUDA(psm::launch_occupancy(b.d_bricks, (int)field->gx, (int)field->gy, (int)field->gz, wpb, b.d_occ, h->stream),
+           "geometry occupancy kernel");
+  PSM_CUDA(cudaStreamSynchronize(h->stream), "geometry occupancy");
   b.gx = field->gx;
   b.gy = field->gy;
   b.gz = field->gz;

@@ -29,6 +29,9 @@ enum Layout { LAYOUT_NATURAL = 0, LAYOUT_SWAPPED = 1 };
 // One body as the kernels see it at one step.
 struct DevBody {
   const unsigned long long* bricks;  // [gz][gy][gx][wpb] words
+  // occupancy [gz + 1][gy + 1][gx + 1] bytes, index c + 1 for c = -1 .. g - 1 per
+  // axis: non-zero iff a brick in {c, c + 1}^3 has a set bit (nullptr: none)
+  const unsigned char* occ;
   int gx, gy, gz;
   int s;    // super-sampling depth
   int wpb;  // 64-bit words per brick
@@ -162,6 +165,9 @@ cudaError_t launch_export(int storage, int Q, const IoParams& p, cudaStream_t st
 cudaError_t launch_macro(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_mass(int storage, int Q, const IoParams& p, int blocks, cudaStream_t st);
 cudaError_t launch_remap(const RemapParams& p, cudaStream_t st);
+// occupancy of a geometry field (DevBody::occ) from its bricks (device)
+cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, int gz, int wpb, unsigned char* occ,
+                             cudaStream_t st);
 
 #define PSM_DECLARE_STORAGE(NAME)                                                          \
   cudaError_t launch_step_##NAME(int Q, int mode, int trt, const StepParams& p, cudaStream_t st); \

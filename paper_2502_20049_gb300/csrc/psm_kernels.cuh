@@ -119,6 +119,12 @@ __device__ __forceinline__ float remap_eps(const DevBody& b, int x, int y, int z
     const int glast = gc[k] + (o[k] ? 1 : 0);
     if (glast < 0 || gc[k] >= dims[k]) return 0.0f;
   }
+  // the block touches coarse cells {gc, gc + 1}^3 at most: none holds a set bit
+  // where the occupancy byte is zero (then eps is exactly 0)
+  if (b.occ) {
+    const long long oi = ((long long)(gc[2] + 1) * (b.gy + 1) + (gc[1] + 1)) * (long long)(b.gx + 1) + (gc[0] + 1);
+    if (!__ldg(b.occ + oi)) return 0.0f;
+  }
   int count = 0;
   const int nn = n * n;
   for (int sz = 0; sz < 2; ++sz) {
