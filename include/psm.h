@@ -186,6 +186,19 @@ int psm_geom_free(psm_geom_field* field);
 int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision, void* stream,
                psm_handle* out);
 
+/* psm_create on caller-owned PDF buffers (for instance PyTorch tensors):
+ * buffers[0] (and buffers[1] for two-grid streaming) are device pointers to
+ * Q * nx * ny * nz elements of the storage type each (shifted f - w rho0,
+ * natural layout [Q][nz][ny][nx] in the library's direction order), 16-byte
+ * aligned, distinct.  The caller keeps ownership: psm_destroy never frees
+ * them and they must outlive the handle.  flags: 0 initialises the state to
+ * f^eq(rho0, u_in) like psm_create; PSM_BUFFERS_KEEP keeps buffers[0]'s
+ * contents as the state at step 0.  PSM_ERR_ARG for NULL, misaligned or equal
+ * buffers or unknown flags (before any CUDA call). */
+#define PSM_BUFFERS_KEEP 1
+int psm_create_with_buffers(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision,
+                            void* stream, void* const* buffers, int flags, psm_handle* out);
+
 /* Free everything the handle owns.  NULL is accepted. */
 int psm_destroy(psm_handle h);
 
@@ -193,12 +206,22 @@ int psm_destroy(psm_handle h);
  * entering from a z ghost plane take the ghost value. */
 int psm_init_equilibrium(psm_handle h, double rho, const double u[3]);
 
+/* The same from per-cell fields: rho[nz][ny][nx] (> 0) and u[nz][ny][nx][3]
+ * (|u| < 0.3), host or device, FP64 (PSM_ERR_ARG naming the first bad cell). */
+int psm_init_equilibrium_field(psm_handle h, const double* rho, const double* u);
+
 /* Import / export the full PDF state, natural layout, FP64, unshifted f,
  * [Q][nz][ny][nx] in the library's direction order (Q*nx*ny*nz doubles).
  * Import rounds to the storage precision.  Export of a state in the AA
  * "swapped" layout (after an odd number of AA steps) undoes the swap. */
 int psm_set_state(psm_handle h, const double* f);
 int psm_get_state(psm_handle h, double* f);
+
+/* The stored PDFs in the storage precision: shifted f - w rho0, natural
+ * layout [Q][nz][ny][nx] (un-swapped after an odd AA step; populations
+ * entering from a z ghost plane as the ghost value), Q * ncell elements of
+ * the storage type, host or device. */
+int psm_get_pdfs(psm_handle h, void* f);
 
 /* Natural, unshifted FP64 PDFs of n listed cells (flat indices
  * (z * ny + y) * nx + x, host or device): f[n][Q] in the library's direction
@@ -226,6 +249,13 @@ int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const 
 /* Number of bodies attached. */
 int psm_num_bodies(psm_handle h, int* out);
 
+/* Remapping of the moving geometry onto eps (Sec. 3): every_step = 1
+ * (default) remaps at every step from that step's pose; 0 freezes the poses of
+ * all bodies at the current step (eps, the reference point R and the lever
+ * arm of u_s stay those of that step; omega and v still give u_s), as for a
+ * body whose geometry is static.  PSM_ERR_STATE while recording. */
+int psm_set_remap(psm_handle h, int every_step);
+
 /* Run n >= 0 time steps asynchronously on the handle's stream (one fused
  * kernel launch per step; no host synchronisation). */
 int psm_step(psm_handle h, int n);
@@ -238,6 +268,9 @@ int psm_step_count(psm_handle h, int64_t* out);
  * psm_series_capacity() steps are kept (PSM_ERR_ARG for older steps).
  * PSM_ERR_NONFINITE if any returned value is NaN or infinite. */
 int psm_force_torque(psm_handle h, int body, int64_t step_from, int64_t count, double* out);
+/* The same series with the sign of Eq. 10 / 11 as printed (the momentum the
+ * solid gives the fluid): the negative of psm_force_torque. */
+int psm_force_torque_raw(psm_handle h, int body, int64_t step_from, int64_t count, double* out);
 int psm_series_capacity(psm_handle h, int64_t* out);
 
 /* Total mass sum_x sum_i f_i (FP64, deterministic order).  Synchronises.

@@ -101,10 +101,14 @@ struct psm_solver {
   cudaStream_t stream = nullptr;
   int Q = 19;
   void* buf[2] = {nullptr, nullptr};
+  bool owns_buf = true;  // false: caller-owned PDF buffers (psm_create_with_buffers)
   int cur = 0;
   int64_t step = 0;
   int nbodies = 0;
   HostBody body[PSM_MAX_BODIES];
+  // psm_set_remap(h, 0): every later step uses the body poses of step frozen_step
+  bool remap_frozen = false;
+  int64_t frozen_step = 0;
   double ghost[27];
   int max_blocks = 0;
   double* d_partials = nullptr;
@@ -203,6 +207,7 @@ int step_grid_blocks(int storage, int Q, int mode, int trt) {
   }
 PSM_IO_DISPATCH(import)
 PSM_IO_DISPATCH(export)
+PSM_IO_DISPATCH(export_raw)
 PSM_IO_DISPATCH(macro)
 cudaError_t launch_mass(int storage, int Q, const IoParams& p, int blocks, cudaStream_t st) {
   switch (storage) {
@@ -294,7 +299,7 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
   DevBody d;
   std::memset(&d, 0, sizeof d);
   double Q[9], R[3];
-  body_pose(b, n, Q, R);
+  body_pose(b, h->remap_frozen ? h->frozen_step : n, Q, R);
   d.bricks = b.d_bricks;
   d.occ = b.d_occ;
   d.gx = (int)b.gx;
@@ -558,8 +563,11 @@ int psm_lattice_velocities(int stencil, int* c_out, double* w_out, int* opp_out)
   return PSM_OK;
 }
 
-int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision, void* stream,
-               psm_handle* out) {
+namespace {
+// psm_create and psm_create_with_buffers: user_bufs (nullptr: allocate) hold
+// the caller's PDF buffers; keep: their contents are the initial state.
+int create_impl(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision, void* stream,
+                void* const* user_bufs, bool keep, psm_handle* out) {
   if (!grid || !lattice || !collision || !out) return fail(PSM_ERR_ARG, "psm_create: NULL argument");
   *out = nullptr;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(PSM_ERR_ARG, "grid sizes must be >= 1");
@@ -609,9 +617,14 @@ int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_colli
   h->max_blocks = sms * (2048 / psm::PSM_THREADS);
   const size_t bytes = (size_t)h->Q * (size_t)h->g.ncell * storage_bytes(lattice->storage);
   const int nbuf = lattice->streaming == PSM_STREAM_TWO_GRID ? 2 : 1;
-  for (int b = 0; b < nbuf; ++b) {
-    e = cudaMalloc(&h->buf[b], bytes);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "PDF buffer allocation"));
+  if (user_bufs) {
+    h->owns_buf = false;
+    for (int b = 0; b < nbuf; ++b) h->buf[b] = user_bufs[b];
+  } else {
+    for (int b = 0; b < nbuf; ++b) {
+      e = cudaMalloc(&h->buf[b], bytes);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "PDF buffer allocation"));
+    }
   }
   e = cudaMalloc(&h->d_partials, sizeof(double) * (size_t)h->max_blocks * PSM_MAX_BODIES * 6);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_ticket, sizeof(unsigned int));
@@ -636,16 +649,41 @@ int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_colli
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->d_series, 0, sizeof(double) * (size_t)h->cap * PSM_MAX_BODIES * 6, h->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch initialisation"));
-  int rc = import_uniform(h, grid->rho0, grid->u_in);
-  if (rc != PSM_OK) return cleanup(rc);
+  if (!keep) {
+    const int rc = import_uniform(h, grid->rho0, grid->u_in);
+    if (rc != PSM_OK) return cleanup(rc);
+  } else {
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "synchronise"));
+  }
   *out = h;
   return PSM_OK;
+}
+}  // namespace
+
+int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision, void* stream,
+               psm_handle* out) {
+  return create_impl(grid, lattice, collision, stream, nullptr, false, out);
+}
+
+int psm_create_with_buffers(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision,
+                            void* stream, void* const* buffers, int flags, psm_handle* out) {
+  if (!lattice || !buffers) return fail(PSM_ERR_ARG, "psm_create_with_buffers: NULL argument");
+  if (flags & ~PSM_BUFFERS_KEEP) return fail(PSM_ERR_ARG, "unknown psm_create_with_buffers flags");
+  const int nbuf = lattice->streaming == PSM_STREAM_TWO_GRID ? 2 : 1;
+  for (int b = 0; b < nbuf; ++b) {
+    if (!buffers[b]) return fail(PSM_ERR_ARG, "PDF buffer %d is NULL", b);
+    if (reinterpret_cast<uintptr_t>(buffers[b]) % 16 != 0) return fail(PSM_ERR_ARG, "PDF buffer %d is not 16-byte aligned", b);
+  }
+  if (nbuf == 2 && buffers[0] == buffers[1]) return fail(PSM_ERR_ARG, "the two PDF buffers must differ");
+  return create_impl(grid, lattice, collision, stream, buffers, (flags & PSM_BUFFERS_KEEP) != 0, out);
 }
 
 int psm_destroy(psm_handle h) {
   if (!h) return PSM_OK;
   if (h->stream || h->buf[0]) cudaStreamSynchronize(h->stream);
-  for (int b = 0; b < 2; ++b) cudaFree(h->buf[b]);
+  if (h->owns_buf)
+    for (int b = 0; b < 2; ++b) cudaFree(h->buf[b]);
   for (int b = 0; b < PSM_MAX_BODIES; ++b) {
     cudaFree(h->body[b].d_bricks);
     cudaFree(h->body[b].d_occ);
@@ -723,6 +761,81 @@ int psm_get_state(psm_handle h, double* f) {
                           sizeof(double) * nchunk, cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "state export");
+  }
+  cudaFree(tmp);
+  return rc;
+}
+
+int psm_init_equilibrium_field(psm_handle h, const double* rho, const double* u) {
+  if (!valid_handle(h) || !rho || !u) return fail(PSM_ERR_ARG, "psm_init_equilibrium_field: NULL argument");
+  const int planes = chunk_planes(h, sizeof(double) * 4);
+  const size_t plane = (size_t)h->grid.nx * h->grid.ny;
+  double* tmp = nullptr;
+  PSM_CUDA(cudaMalloc(&tmp, sizeof(double) * 4 * plane * planes), "field staging allocation");
+  int rc = PSM_OK;
+  for (int z0 = 0; z0 < h->grid.nz && rc == PSM_OK; z0 += planes) {
+    const int z1 = (int)std::min<int64_t>(h->grid.nz, z0 + planes);
+    const size_t nchunk = plane * (z1 - z0);
+    cudaError_t e = cudaMemcpyAsync(tmp, rho + (size_t)z0 * plane, sizeof(double) * nchunk, cudaMemcpyDefault,
+                                    h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp + nchunk, u + (size_t)z0 * plane * 3, sizeof(double) * 3 * nchunk, cudaMemcpyDefault,
+                          h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "field upload");
+      break;
+    }
+    // validate on the host side of the copy: rho > 0 and finite, |u| < 0.3
+    std::vector<double> hv(4 * nchunk);
+    e = cudaMemcpy(hv.data(), tmp, sizeof(double) * 4 * nchunk, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "field check");
+      break;
+    }
+    for (size_t c = 0; c < nchunk && rc == PSM_OK; ++c) {
+      const double r = hv[c], *uc = &hv[nchunk + 3 * c];
+      const double un = std::sqrt(uc[0] * uc[0] + uc[1] * uc[1] + uc[2] * uc[2]);
+      if (!(r > 0.0) || !std::isfinite(r) || !(un < 0.3))
+        rc = fail(PSM_ERR_ARG, "cell %zu: rho must be > 0 and |u| < 0.3", (size_t)z0 * plane + c);
+    }
+    if (rc != PSM_OK) break;
+    IoParams p;
+    io_base(h, p);
+    p.z_begin = z0;
+    p.z_end = z1;
+    p.rho_f = tmp;
+    p.u_f = tmp + nchunk;
+    e = psm::launch_import(h->lat.storage, h->Q, p, h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "import kernel");
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  return rc;
+}
+
+int psm_get_pdfs(psm_handle h, void* f) {
+  if (!valid_handle(h) || !f) return fail(PSM_ERR_ARG, "psm_get_pdfs: NULL argument");
+  const size_t b = storage_bytes(h->lat.storage);
+  const int planes = chunk_planes(h, b * h->Q);
+  const size_t plane = (size_t)h->grid.nx * h->grid.ny;
+  char* tmp = nullptr;
+  PSM_CUDA(cudaMalloc(&tmp, b * h->Q * plane * planes), "pdf staging allocation");
+  int rc = PSM_OK;
+  for (int z0 = 0; z0 < h->grid.nz && rc == PSM_OK; z0 += planes) {
+    const int z1 = (int)std::min<int64_t>(h->grid.nz, z0 + planes);
+    const size_t nchunk = plane * (z1 - z0);
+    IoParams p;
+    io_base(h, p);
+    p.z_begin = z0;
+    p.z_end = z1;
+    p.f_out_raw = tmp;
+    cudaError_t e = psm::launch_export_raw(h->lat.storage, h->Q, p, h->stream);
+    for (int i = 0; i < h->Q && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(static_cast<char*>(f) + ((size_t)i * h->g.ncell + (size_t)z0 * plane) * b,
+                          tmp + (size_t)i * nchunk * b, b * nchunk, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "pdf export");
   }
   cudaFree(tmp);
   return rc;
@@ -1231,6 +1344,22 @@ int psm_force_torque(psm_handle h, int body, int64_t step_from, int64_t count, d
     done += run;
   }
   if (!finite) return fail(PSM_ERR_NONFINITE, "force/torque series holds NaN or Inf");
+  return PSM_OK;
+}
+
+int psm_force_torque_raw(psm_handle h, int body, int64_t step_from, int64_t count, double* out) {
+  const int rc = psm_force_torque(h, body, step_from, count, out);
+  if (rc != PSM_OK) return rc;
+  for (int64_t k = 0; k < count * 6; ++k) out[k] = -out[k];
+  return PSM_OK;
+}
+
+int psm_set_remap(psm_handle h, int every_step) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_set_remap: NULL handle");
+  if (every_step != 0 && every_step != 1) return fail(PSM_ERR_ARG, "psm_set_remap: every_step must be 0 or 1");
+  if (h->recording) return fail(PSM_ERR_STATE, "psm_set_remap while recording for psm_backward");
+  if (!every_step && !h->remap_frozen) h->frozen_step = h->step;
+  h->remap_frozen = !every_step;
   return PSM_OK;
 }
 

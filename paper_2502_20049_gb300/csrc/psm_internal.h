@@ -121,12 +121,16 @@ struct IoParams {
   double ghost[27];
   double rho0;
   int z_begin, z_end;  // z-planes handled by this launch
-  // import: from a natural FP64 state chunk (f_in, planes z_begin..z_end) or uniform (rho, u)
+  // import: from a natural FP64 state chunk (f_in, planes z_begin..z_end), uniform
+  // (rho, u), or equilibria of per-cell fields (rho_f[cell], u_f[cell][3] of the chunk)
   const double* f_in;
   int uniform;
   double rho, u[3];
+  const double* rho_f;
+  const double* u_f;
   // export
   double* f_out;    // natural, unshifted, planes z_begin..z_end
+  void* f_out_raw;  // natural, shifted, storage precision, planes z_begin..z_end
   double* rho_out;  // macroscopic
   double* u_out;
   // reduction
@@ -162,6 +166,7 @@ int tma_smem_bytes(int storage, int Q, int mode);
 int step_grid_blocks(int storage, int Q, int mode, int trt);
 cudaError_t launch_import(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_export(int storage, int Q, const IoParams& p, cudaStream_t st);
+cudaError_t launch_export_raw(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_macro(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_mass(int storage, int Q, const IoParams& p, int blocks, cudaStream_t st);
 cudaError_t launch_remap(const RemapParams& p, cudaStream_t st);
@@ -177,6 +182,7 @@ cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, i
   int step_grid_blocks_##NAME(int Q, int mode, int trt);                                  \
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
+  cudaError_t launch_export_raw_##NAME(int Q, const IoParams& p, cudaStream_t st);        \
   cudaError_t launch_macro_##NAME(int Q, const IoParams& p, cudaStream_t st);             \
   cudaError_t launch_mass_##NAME(int Q, const IoParams& p, int blocks, cudaStream_t st);  \
   cudaError_t launch_get_cells_##NAME(int Q, const IoParams& p, const long long* cells, long long n, double* out, \

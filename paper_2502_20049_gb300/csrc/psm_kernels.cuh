@@ -1191,10 +1191,13 @@ __global__ void k_import(const __grid_constant__ IoParams p) {
     nbr.init(p.g, x, y, z);
     for (int i = 0; i < Q; ++i) {
       double v;
-      if (p.uniform) {
-        const double cu = lat_cx(i) * p.u[0] + lat_cy(i) * p.u[1] + lat_cz(i) * p.u[2];
-        const double uu = p.u[0] * p.u[0] + p.u[1] * p.u[1] + p.u[2] * p.u[2];
-        v = lat_w<Q>(i) * p.rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+      if (p.uniform || p.rho_f) {
+        const long long lc = cell - (long long)p.z_begin * plane;
+        const double* uc = p.rho_f ? p.u_f + 3 * lc : p.u;
+        const double rc = p.rho_f ? p.rho_f[lc] : p.rho;
+        const double cu = lat_cx(i) * uc[0] + lat_cy(i) * uc[1] + lat_cz(i) * uc[2];
+        const double uu = uc[0] * uc[0] + uc[1] * uc[1] + uc[2] * uc[2];
+        v = lat_w<Q>(i) * rc * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
       } else {
         v = p.f_in[(long long)i * plane * (p.z_end - p.z_begin) + (cell - (long long)p.z_begin * plane)];
       }
@@ -1229,6 +1232,27 @@ __global__ void k_export(const __grid_constant__ IoParams p) {
     T f[Q];
     read_state<S, Q>(p, buf, nbr, cell, f);
     for (int i = 0; i < Q; ++i) p.f_out[(long long)i * nchunk + idx] = (double)f[i] + lat_w<Q>(i) * p.rho0;
+  }
+}
+
+// Natural layout, shifted, storage precision (psm_get_pdfs): the stored
+// values themselves (ghost-plane populations as the ghost value, rounded).
+template <class S, int Q>
+__global__ void k_export_raw(const __grid_constant__ IoParams p) {
+  using T = typename Store<S>::T;
+  const S* buf = static_cast<const S*>(p.f);
+  S* out = static_cast<S*>(p.f_out_raw);
+  const long long plane = (long long)p.g.nx * p.g.ny;
+  const long long nchunk = plane * (p.z_end - p.z_begin);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;; idx += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    long long cell;
+    if (!io_cell(p, idx, x, y, z, cell)) return;
+    Nbr nbr;
+    nbr.init(p.g, x, y, z);
+    T f[Q];
+    read_state<S, Q>(p, buf, nbr, cell, f);
+    for (int i = 0; i < Q; ++i) Store<S>::st(out + (long long)i * nchunk + idx, f[i]);
   }
 }
 
@@ -1423,6 +1447,11 @@ inline int io_grid(const IoParams& p) {
   cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st) {                         \
     if (Q == 19) k_export<S, 19><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                                \
     else k_export<S, 27><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                                        \
+    return cudaGetLastError();                                                                          \
+  }                                                                                                     \
+  cudaError_t launch_export_raw_##NAME(int Q, const IoParams& p, cudaStream_t st) {                     \
+    if (Q == 19) k_export_raw<S, 19><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                            \
+    else k_export_raw<S, 27><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                                    \
     return cudaGetLastError();                                                                          \
   }                                                                                                     \
   cudaError_t launch_macro_##NAME(int Q, const IoParams& p, cudaStream_t st) {                          \

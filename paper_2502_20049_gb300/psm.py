@@ -89,6 +89,11 @@ def lib() -> ctypes.CDLL:
                 "psm_geom_voxelize_rotor": (i, [P(RotorParams), i, P(GeomField)]),
                 "psm_geom_free": (i, [P(GeomField)]),
                 "psm_create": (i, [P(Grid), P(Lattice), P(Collision), vp, P(H)]),
+                "psm_create_with_buffers": (i, [P(Grid), P(Lattice), P(Collision), vp, P(vp), i, P(H)]),
+                "psm_init_equilibrium_field": (i, [H, vp, vp]),
+                "psm_get_pdfs": (i, [H, vp]),
+                "psm_force_torque_raw": (i, [H, i, i64, i64, vp]),
+                "psm_set_remap": (i, [H, i]),
                 "psm_destroy": (i, [H]),
                 "psm_init_equilibrium": (i, [H, d, P(d)]),
                 "psm_set_state": (i, [H, vp]),
@@ -244,15 +249,27 @@ class SolverConfig:
 class Solver:
     """One libpsm handle (psm_create ... psm_destroy)."""
 
-    def __init__(self, cfg: SolverConfig, stream: int | None = None):
+    def __init__(self, cfg: SolverConfig, stream: int | None = None, buffers=None, keep: bool = False):
+        """buffers: caller-owned device PDF buffers (torch tensors or raw
+        pointers; one for AA, two for two-grid), kept alive by the solver and
+        never freed by it (psm_create_with_buffers); keep: their contents are
+        the initial state."""
         self.cfg = cfg
         grid = Grid(cfg.nx, cfg.ny, cfg.nz, cfg.bc_z, cfg.rho0, (ctypes.c_double * 3)(*cfg.u_in))
         lat = Lattice(cfg.Q, STREAMING[cfg.streaming], STORAGE[cfg.storage])
         col = Collision(FLUID[cfg.fluid], cfg.tau, cfg.trt_lambda, cfg.solid, cfg.weighting)
         self._h = ctypes.c_void_p()
         self.stream = current_stream() if stream is None else stream
-        check(lib().psm_create(ctypes.byref(grid), ctypes.byref(lat), ctypes.byref(col),
-                               ctypes.c_void_p(self.stream), ctypes.byref(self._h)))
+        self._buffers = buffers
+        if buffers is None:
+            check(lib().psm_create(ctypes.byref(grid), ctypes.byref(lat), ctypes.byref(col),
+                                   ctypes.c_void_p(self.stream), ctypes.byref(self._h)))
+        else:
+            ptrs = [b.data_ptr() if hasattr(b, "data_ptr") else int(b) for b in buffers]
+            arr = (ctypes.c_void_p * 2)(*(ptrs + [0] * (2 - len(ptrs))))
+            check(lib().psm_create_with_buffers(ctypes.byref(grid), ctypes.byref(lat), ctypes.byref(col),
+                                                ctypes.c_void_p(self.stream), arr, 1 if keep else 0,
+                                                ctypes.byref(self._h)))
         self._geoms = []
 
     @classmethod
@@ -289,6 +306,40 @@ class Solver:
     def init_equilibrium(self, rho: float, u):
         _, up = _d(u, 3)
         check(lib().psm_init_equilibrium(self._h, rho, up))
+
+    def init_equilibrium_field(self, rho, u):
+        """f = f^eq(rho(x), u(x)) per cell: rho [nz, ny, nx], u [nz, ny, nx, 3]
+        (numpy or torch, host or device, float64)."""
+        if not hasattr(rho, "data_ptr"):
+            rho = np.ascontiguousarray(rho, dtype=np.float64)
+        if not hasattr(u, "data_ptr"):
+            u = np.ascontiguousarray(u, dtype=np.float64)
+        rp, k1 = _ptr(rho, np.float64, self.ncell)
+        up, k2 = _ptr(u, np.float64, 3 * self.ncell)
+        check(lib().psm_init_equilibrium_field(self._h, rp, up))
+
+    def set_remap(self, every_step: bool):
+        """Remap the geometry every step (True) or freeze the poses now (False)."""
+        check(lib().psm_set_remap(self._h, 1 if every_step else 0))
+
+    STORAGE_DTYPES = {"fp64": np.float64, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16}
+
+    def get_pdfs(self, out=None):
+        """Stored PDFs (shifted, natural layout) in the storage precision:
+        [Q, nz, ny, nx] numpy array (BF16 as its raw 16-bit patterns) unless
+        out (numpy or torch, host or device) is given."""
+        dt = self.STORAGE_DTYPES[self.cfg.storage]
+        if out is None:
+            out = np.zeros(self.shape, dtype=dt)
+        n = int(np.prod(self.shape))
+        if hasattr(out, "data_ptr"):
+            if out.numel() * out.element_size() != n * np.dtype(dt).itemsize:
+                raise ValueError("output buffer has the wrong size")
+            p = ctypes.c_void_p(out.data_ptr())
+        else:
+            p, keep = _ptr(out, dt, n)
+        check(lib().psm_get_pdfs(self._h, p))
+        return out
 
     def set_geometry(self, body: int, geom: Geometry, Q0, R0, omega, v):
         a, Qp = _d(Q0, 9)
@@ -343,6 +394,14 @@ class Solver:
             out = np.zeros((count, 6))
         p, keep = _ptr(out, np.float64, count * 6)
         check(lib().psm_force_torque(self._h, body, step_from, count, p))
+        return out
+
+    def force_torque_raw(self, body: int = 0, step_from: int = 0, count: int | None = None):
+        """[count, 6] with the printed sign of Eq. 10 / 11 (minus force_torque)."""
+        if count is None:
+            count = self.step_count - step_from
+        out = np.zeros((count, 6))
+        check(lib().psm_force_torque_raw(self._h, body, step_from, count, ctypes.c_void_p(out.ctypes.data)))
         return out
 
     def mass(self) -> float:

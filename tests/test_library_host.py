@@ -101,3 +101,31 @@ def test_voxeliser_rejects_bad_arguments(psm):
     assert ei.value.code == -1
     with pytest.raises(psm.PSMError):
         psm.voxelize(W.SPHERE, (2.0,), 4)
+
+
+@pytest.mark.parametrize("bufs,flags", [([0, 0], 0), ([0x1008, 0x2000], 0), ([0x1000, 0x1000], 0),
+                                        ([0x1000, 0x2000], 4)])
+def test_create_with_buffers_rejects_bad_buffers(psm, bufs, flags):
+    """NULL, misaligned or equal caller buffers and unknown flags fail before
+    any CUDA call (the pointers are never dereferenced)."""
+    import ctypes
+
+    cfg = psm.SolverConfig(8, 8, 8, streaming="twogrid")
+    grid = psm.Grid(cfg.nx, cfg.ny, cfg.nz, cfg.bc_z, cfg.rho0, (ctypes.c_double * 3)(*cfg.u_in))
+    lat = psm.Lattice(cfg.Q, psm.STREAMING[cfg.streaming], psm.STORAGE[cfg.storage])
+    col = psm.Collision(psm.FLUID[cfg.fluid], cfg.tau, cfg.trt_lambda, cfg.solid, cfg.weighting)
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 2)(*bufs)
+    rc = psm.lib().psm_create_with_buffers(ctypes.byref(grid), ctypes.byref(lat), ctypes.byref(col), None, arr,
+                                           flags, ctypes.byref(h))
+    assert rc == -1 and not h.value
+
+
+def test_null_handle_calls_are_argument_errors(psm):
+    import ctypes
+
+    L = psm.lib()
+    assert L.psm_set_remap(None, 0) == -1
+    assert L.psm_get_pdfs(None, None) == -1
+    assert L.psm_init_equilibrium_field(None, None, None) == -1
+    assert L.psm_force_torque_raw(None, 0, 0, 0, None) == -1
