@@ -96,7 +96,11 @@ def test_get_pdfs_is_the_shifted_state(storage):
         raw = (raw.astype(np.uint32) << 16).view(np.float32)
     _, w, _ = psm.lattice_velocities(case.Q)
     full = s.get_state()
-    assert np.abs(raw.astype(np.float64) + w[:, None, None, None] * case.rho0 - full).max() <= 1e-15
+    d = np.abs(raw.astype(np.float64) + w[:, None, None, None] * case.rho0 - full)
+    # stored populations: the same values; the ghost-plane populations of the
+    # end planes are the ghost value, rounded to the storage type by get_pdfs
+    assert d[:, 1:-1].max() <= 1e-15
+    assert d.max() <= {"fp64": 1e-15, "fp32": 1e-8, "fp16": 1e-4, "bf16": 1e-3}[storage]
 
 
 def test_init_equilibrium_field_uniform_and_varying():
