@@ -75,6 +75,8 @@ def _lib():
                 "or_shape_box": (i, [i, dp, ip, dp]),
                 "or_voxelize": (i, [i, dp, i, u8p]),
                 "or_inside": (i, [i, dp, d, d, d]),
+                "or_mesh_box": (i, [vp, l, i, vp, dp]),
+                "or_voxelize_mesh": (i, [vp, l, vp, l, i, u8p]),
                 "or_remap": (i, [u8p, i, i, i, i, dp, dp, dp, dp, dp, l, i, i, i, dp]),
                 "or_pose": (i, [dp, dp, dp, dp, l, dp, dp]),
                 "or_create": (vp, [vp]),
@@ -215,6 +217,26 @@ def voxelize(kind: int, params, s: int):
     n = 1 << s
     sub = np.zeros((dims[2] * n, dims[1] * n, dims[0] * n), dtype=np.uint8)
     _lib().or_voxelize(kind, _dp(p), s, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return sub, lo
+
+
+def voxelize_mesh(vertices, triangles, s: int):
+    """Binary super-sampled field of a closed triangle mesh by brute-force ray
+    parity in exact integer arithmetic (Sec. 3; rules in psm_oracle.cpp).
+
+    vertices [nv, 3] (float32 body-frame lattice units), triangles [nt, 3]
+    (int32).  Returns (sub[nsz, nsy, nsx] uint8, lo[3])."""
+    v = np.ascontiguousarray(vertices, dtype=np.float32)
+    t = np.ascontiguousarray(triangles, dtype=np.int32)
+    dims = np.zeros(3, dtype=np.int64)
+    lo = np.zeros(3)
+    if _lib().or_mesh_box(v.ctypes.data, len(v), s, dims.ctypes.data, _dp(lo)) != 0:
+        raise ValueError("mesh outside the supported box or s out of 0..3")
+    n = 1 << s
+    sub = np.zeros((dims[2] * n, dims[1] * n, dims[0] * n), dtype=np.uint8)
+    if _lib().or_voxelize_mesh(v.ctypes.data, len(v), t.ctypes.data, len(t), s,
+                               sub.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))) != 0:
+        raise ValueError("bad mesh")
     return sub, lo
 
 

@@ -688,6 +688,123 @@ int or_voxelize(int kind, const double* p, int s, uint8_t* sub_out) {
 
 int or_inside(int kind, const double* p, double x, double y, double z) { return inside_shape(kind, p, x, y, z) ? 1 : 0; }
 
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Voxelisation of a closed triangle mesh (Sec. 3: the body's surface mesh is
+// turned into the super-sampled binary field once).  A sub-cell is inside iff
+// a ray from its centre in the +x direction crosses the surface an odd number
+// of times.  Everything is decided in exact integer arithmetic:
+//   * the box of the field is [lo, lo + dims) with lo = floor(min v) - 1 and
+//     lo + dims = ceil(max v) + 1 per axis (whole cells);
+//   * coordinates relative to lo are quantised to integers in units of
+//     2^-(s+8) cells (round half away from zero); the centre of sub-cell a is
+//     256 a + 128 in those units;
+//   * the ray hits the triangle's projection onto the (y, z) plane when the
+//     three edge orientations have one strict sign, ties broken as if the
+//     centre were moved by (delta^2, delta) in (y, z) for an infinitesimal
+//     delta > 0 (simulation of simplicity: a point on a shared edge or vertex
+//     belongs to exactly one side);
+//   * the crossing counts when it lies at or ahead of the centre in x.
+// Brute force: every sub-cell against every triangle.
+// ---------------------------------------------------------------------------
+struct MeshQ {
+  std::vector<int64_t> v;  // quantised vertices [nv][3]
+  int64_t dims[3];
+  double lo[3];
+};
+
+bool mesh_box(const float* vert, long nv, int s, int64_t dims[3], double lo[3]) {
+  if (nv < 3) return false;
+  for (int k = 0; k < 3; ++k) {
+    double mn = 1e300, mx = -1e300;
+    for (long i = 0; i < nv; ++i) {
+      const double c = (double)vert[3 * i + k];
+      if (!std::isfinite(c)) return false;
+      mn = std::min(mn, c);
+      mx = std::max(mx, c);
+    }
+    lo[k] = std::floor(mn) - 1.0;
+    dims[k] = (int64_t)(std::ceil(mx) + 1.0 - lo[k]);
+    if (dims[k] < 1 || dims[k] > ((int64_t)1 << (19 - s))) return false;
+  }
+  return true;
+}
+
+// sign of the (y, z) orientation of P against the directed edge a -> b, with
+// the symbolic perturbation of P by (delta^2, delta)
+int orient_yz(const int64_t* a, const int64_t* b, int64_t py, int64_t pz) {
+  const int64_t ey = b[1] - a[1], ez = b[2] - a[2];
+  const int64_t o = ey * (pz - a[2]) - ez * (py - a[1]);
+  if (o != 0) return o > 0 ? 1 : -1;
+  if (ey != 0) return ey > 0 ? 1 : -1;
+  if (ez != 0) return ez < 0 ? 1 : -1;
+  return 0;
+}
+
+// does the +x ray from P cross triangle (a, b, c) at or ahead of P?
+bool ray_crosses(const int64_t* a, const int64_t* b, const int64_t* c, int64_t px, int64_t py, int64_t pz) {
+  const int s1 = orient_yz(a, b, py, pz), s2 = orient_yz(b, c, py, pz), s3 = orient_yz(c, a, py, pz);
+  if (s1 == 0 || s1 != s2 || s2 != s3) return false;
+  const int64_t e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  const int64_t e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  const int64_t nx = e1[1] * e2[2] - e1[2] * e2[1];
+  const int64_t ny = e1[2] * e2[0] - e1[0] * e2[2];
+  const int64_t nz = e1[0] * e2[1] - e1[1] * e2[0];
+  // the ray point P + t e_x lies on the plane for t = n . (a - P) / nx
+  const __int128 d = (__int128)nx * (a[0] - px) + (__int128)ny * (a[1] - py) + (__int128)nz * (a[2] - pz);
+  return nx > 0 ? d >= 0 : d <= 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int or_mesh_box(const float* vert, long nv, int s, long* dims_out, double* lo_out) {
+  int64_t dims[3];
+  double lo[3];
+  if (s < 0 || s > 3 || !mesh_box(vert, nv, s, dims, lo)) return -1;
+  for (int k = 0; k < 3; ++k) {
+    dims_out[k] = (long)dims[k];
+    lo_out[k] = lo[k];
+  }
+  return 0;
+}
+
+// sub_out[(az * nsy + ay) * nsx + ax], n = 2^s sub-cells per cell and axis
+int or_voxelize_mesh(const float* vert, long nv, const int* tri, long nt, int s, uint8_t* sub_out) {
+  int64_t dims[3];
+  double lo[3];
+  if (s < 0 || s > 3 || !mesh_box(vert, nv, s, dims, lo)) return -1;
+  const double scale = std::ldexp(1.0, s + 8);
+  std::vector<int64_t> q((size_t)nv * 3);
+  for (long i = 0; i < nv; ++i)
+    for (int k = 0; k < 3; ++k) q[3 * i + k] = (int64_t)std::llround(((double)vert[3 * i + k] - lo[k]) * scale);
+  for (long t = 0; t < nt; ++t)
+    for (int k = 0; k < 3; ++k)
+      if (tri[3 * t + k] < 0 || tri[3 * t + k] >= nv) return -1;
+  const int n = 1 << s;
+  const long nsx = (long)dims[0] * n, nsy = (long)dims[1] * n, nsz = (long)dims[2] * n;
+#pragma omp parallel for schedule(dynamic)
+  for (long az = 0; az < nsz; ++az)
+    for (long ay = 0; ay < nsy; ++ay)
+      for (long ax = 0; ax < nsx; ++ax) {
+        const int64_t px = 256 * (int64_t)ax + 128, py = 256 * (int64_t)ay + 128, pz = 256 * (int64_t)az + 128;
+        int parity = 0;
+        for (long t = 0; t < nt; ++t) {
+          const int64_t* a = &q[3 * (size_t)tri[3 * t]];
+          const int64_t* b = &q[3 * (size_t)tri[3 * t + 1]];
+          const int64_t* c = &q[3 * (size_t)tri[3 * t + 2]];
+          if (ray_crosses(a, b, c, px, py, pz)) parity ^= 1;
+        }
+        sub_out[(az * nsy + ay) * nsx + ax] = (uint8_t)parity;
+      }
+  return 0;
+}
+
+
 // Stand-alone remap of one body (Sec. 3) at the pose of step n over an
 // nx*ny*nz grid -> eps (double, exact multiples of 2^-3s).
 int or_remap(const uint8_t* sub, int nsx, int nsy, int nsz, int s, const double* lo, const double* Q0,

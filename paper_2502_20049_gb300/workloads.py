@@ -161,3 +161,88 @@ def pick_cells(mask: np.ndarray, k: int, seed: int = SEED) -> np.ndarray:
     """k distinct flat indices drawn uniformly from the True cells of mask."""
     idx = np.flatnonzero(mask.reshape(-1))
     return np.sort(rng(seed).choice(idx, size=min(k, idx.size), replace=False))
+
+
+# ---------------------------------------------------------------------------
+# Synthetic closed triangle meshes (inputs of the mesh voxeliser; the paper's
+# CROR and bunny meshes are not available).  Vertices float32 [nv, 3] in body
+# frame lattice units, triangles int32 [nt, 3], outward orientation.
+# ---------------------------------------------------------------------------
+def box_mesh(lo, hi):
+    """Axis-aligned box [lo, hi] as 12 triangles."""
+    (x0, y0, z0), (x1, y1, z1) = lo, hi
+    v = np.array([[x0, y0, z0], [x1, y0, z0], [x1, y1, z0], [x0, y1, z0],
+                  [x0, y0, z1], [x1, y0, z1], [x1, y1, z1], [x0, y1, z1]], dtype=np.float32)
+    t = np.array([[0, 2, 1], [0, 3, 2], [4, 5, 6], [4, 6, 7], [0, 1, 5], [0, 5, 4],
+                  [1, 2, 6], [1, 6, 5], [2, 3, 7], [2, 7, 6], [3, 0, 4], [3, 4, 7]], dtype=np.int32)
+    return v, t
+
+
+def icosphere(radius: float, subdiv: int, centre=(0.0, 0.0, 0.0)):
+    """Sphere approximated by a subdivided icosahedron (vertices on the sphere)."""
+    g = (1.0 + 5 ** 0.5) / 2.0
+    v = [[-1, g, 0], [1, g, 0], [-1, -g, 0], [1, -g, 0], [0, -1, g], [0, 1, g], [0, -1, -g], [0, 1, -g],
+         [g, 0, -1], [g, 0, 1], [-g, 0, -1], [-g, 0, 1]]
+    f = [[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11], [1, 5, 9], [5, 11, 4], [11, 10, 2],
+         [10, 7, 6], [7, 1, 8], [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9], [4, 9, 5], [2, 4, 11],
+         [6, 2, 10], [8, 6, 7], [9, 8, 1]]
+    v = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in v]
+    for _ in range(subdiv):
+        mid = {}
+
+        def m(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                p = v[a] + v[b]
+                v.append(p / np.linalg.norm(p))
+                mid[key] = len(v) - 1
+            return mid[key]
+
+        f = [t for a, b, c in f for t in ([a, m(a, b), m(c, a)], [b, m(b, c), m(a, b)], [c, m(c, a), m(b, c)],
+                                          [m(a, b), m(b, c), m(c, a)])]
+    return (np.array(v) * radius + np.array(centre)).astype(np.float32), np.array(f, dtype=np.int32)
+
+
+def torus_mesh(R: float, r: float, nu: int = 48, nv: int = 24):
+    """Torus about the z axis (tube radius r around the circle of radius R)."""
+    u = 2 * np.pi * np.arange(nu) / nu
+    w = 2 * np.pi * np.arange(nv) / nv
+    U, Wv = np.meshgrid(u, w, indexing="ij")
+    x = (R + r * np.cos(Wv)) * np.cos(U)
+    y = (R + r * np.cos(Wv)) * np.sin(U)
+    z = r * np.sin(Wv)
+    v = np.stack([x, y, z], -1).reshape(-1, 3).astype(np.float32)
+    tri = []
+    for i in range(nu):
+        for j in range(nv):
+            a, b = i * nv + j, ((i + 1) % nu) * nv + j
+            c, d = ((i + 1) % nu) * nv + (j + 1) % nv, i * nv + (j + 1) % nv
+            tri += [[a, b, c], [a, c, d]]
+    return v, np.array(tri, dtype=np.int32)
+
+
+def merge_meshes(*meshes):
+    """Disjoint closed meshes as one (components must not intersect)."""
+    vs, ts, off = [], [], 0
+    for v, t in meshes:
+        vs.append(v)
+        ts.append(t + off)
+        off += len(v)
+    return np.concatenate(vs).astype(np.float32), np.concatenate(ts).astype(np.int32)
+
+
+def transform_mesh(mesh, R=None, shift=(0.0, 0.0, 0.0)):
+    v, t = mesh
+    v = v.astype(np.float64)
+    if R is not None:
+        v = v @ np.asarray(R, dtype=np.float64).T
+    return (v + np.asarray(shift)).astype(np.float32), t
+
+
+def rot(axis: str, angle: float):
+    c, s = np.cos(angle), np.sin(angle)
+    if axis == "x":
+        return np.array([[1, 0, 0], [0, c, -s], [0, s, c]])
+    if axis == "y":
+        return np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]])
+    return np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])
