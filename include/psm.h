@@ -170,6 +170,22 @@ int psm_geom_voxelize_ellipsoid(double a, double b, double c, int s, psm_geom_fi
 int psm_geom_voxelize_box(double hx, double hy, double hz, int s, psm_geom_field* out);
 /* Synthetic rotor (see psm_rotor). */
 int psm_geom_voxelize_rotor(const psm_rotor* rotor, int s, psm_geom_field* out);
+/* Closed triangle mesh (Sec. 3: the body's surface mesh is voxelised once
+ * into this field), on the GPU.  vertices: nv x 3 floats (body frame, lattice
+ * units), triangles: nt x 3 vertex indices, host or device.  A sub-cell is 1
+ * iff a ray from its centre along +x crosses the surface an odd number of
+ * times, decided exactly: the box is lo = floor(min v) - 1 to ceil(max v) + 1
+ * per axis (at most 2^(19-s) cells), coordinates relative to lo are rounded
+ * (half away from zero) to multiples of 2^-(s+8) cells, a centre on an edge or
+ * vertex of the (y, z) projection counts as moved by (delta^2, delta) in
+ * (y, z) for delta -> 0+, and a crossing at the centre's own x counts.  The
+ * mesh must be closed (every edge shared by an even number of triangles) and
+ * its components must not intersect; the result is host memory like the other
+ * voxelisers'.  PSM_ERR_ARG: open mesh, bad index, degenerate index triple,
+ * non-finite or too large coordinates; PSM_ERR_UNSUPPORTED: more than 256
+ * crossings along one sub-cell row. */
+int psm_geom_voxelize_mesh(const float* vertices, int64_t nv, const int32_t* triangles, int64_t nt, int s,
+                           psm_geom_field* out);
 /* Release a field returned by a voxeliser (bricks set to NULL). */
 int psm_geom_free(psm_geom_field* field);
 

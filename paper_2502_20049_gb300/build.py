@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpsm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["psm_api.cu", "psm_kern_fp64.cu", "psm_kern_fp32.cu", "psm_kern_fp16.cu", "psm_kern_bf16.cu",
-           "psm_geom.cpp", "psm_noalloc.cu"]
+           "psm_geom.cpp", "psm_noalloc.cu", "psm_mesh.cu"]
 HEADERS = ["psm_internal.h", "psm_kernels.cuh", os.path.join("..", "..", "include", "psm.h")]
 
 

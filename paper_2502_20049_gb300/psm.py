@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
                 "psm_geom_voxelize_box": (i, [d, d, d, i, P(GeomField)]),
                 "psm_geom_voxelize_rotor": (i, [P(RotorParams), i, P(GeomField)]),
                 "psm_geom_free": (i, [P(GeomField)]),
+                "psm_geom_voxelize_mesh": (i, [vp, i64, vp, i64, i, P(GeomField)]),
                 "psm_create": (i, [P(Grid), P(Lattice), P(Collision), vp, P(H)]),
                 "psm_create_with_buffers": (i, [P(Grid), P(Lattice), P(Collision), vp, P(vp), i, P(H)]),
                 "psm_init_equilibrium_field": (i, [H, vp, vp]),
@@ -225,6 +226,25 @@ def voxelize(kind: int, params, s: int) -> Geometry:
     else:
         raise ValueError(f"unknown shape kind {kind}")
     check(rc)
+    return g
+
+
+def voxelize_mesh(vertices, triangles, s: int) -> Geometry:
+    """GPU voxeliser of a closed triangle mesh (psm_geom_voxelize_mesh):
+    vertices [nv, 3] float32, triangles [nt, 3] int32 (numpy, or torch tensors
+    on the host or the device)."""
+    g = Geometry()
+    if hasattr(vertices, "data_ptr"):
+        vp, nv = ctypes.c_void_p(vertices.data_ptr()), vertices.shape[0]
+    else:
+        vertices = np.ascontiguousarray(vertices, dtype=np.float32)
+        vp, nv = ctypes.c_void_p(vertices.ctypes.data), len(vertices)
+    if hasattr(triangles, "data_ptr"):
+        tp, nt = ctypes.c_void_p(triangles.data_ptr()), triangles.shape[0]
+    else:
+        triangles = np.ascontiguousarray(triangles, dtype=np.int32)
+        tp, nt = ctypes.c_void_p(triangles.ctypes.data), len(triangles)
+    check(lib().psm_geom_voxelize_mesh(vp, nv, tp, nt, s, ctypes.byref(g.field)))
     return g
 
 

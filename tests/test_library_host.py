@@ -129,3 +129,26 @@ def test_null_handle_calls_are_argument_errors(psm):
     assert L.psm_get_pdfs(None, None) == -1
     assert L.psm_init_equilibrium_field(None, None, None) == -1
     assert L.psm_force_torque_raw(None, 0, 0, 0, None) == -1
+
+
+@pytest.mark.parametrize("case", ["open", "index", "degenerate", "nan", "s"])
+def test_mesh_voxeliser_rejects_bad_meshes(psm, case):
+    """Argument errors of the mesh voxeliser are found on the host (no kernel runs)."""
+    v, t = W.box_mesh((0, 0, 0), (2, 2, 2))
+    s = 2
+    if case == "open":
+        t = t[:-1]
+    elif case == "index":
+        t = t.copy()
+        t[0, 0] = 99
+    elif case == "degenerate":
+        t = t.copy()
+        t[0, 1] = t[0, 0]
+    elif case == "nan":
+        v = v.copy()
+        v[0, 0] = np.nan
+    else:
+        s = 4
+    with pytest.raises(psm.PSMError) as ei:
+        psm.voxelize_mesh(v, t, s)
+    assert ei.value.code == -1
