@@ -86,6 +86,8 @@ def _lib():
                 "or_add_body": (i, [vp, u8p, i, i, i, i, dp, dp, dp, dp, dp]),
                 "or_init_eq": (i, [vp, d, dp]),
                 "or_set_body_us_omega": (i, [vp, i, dp]),
+                "or_set_body_dynamics": (i, [vp, i, d, dp, dp, dp]),
+                "or_body_state": (i, [vp, i, dp]),
                 "or_set_f": (i, [vp, dp]),
                 "or_get_f": (i, [vp, dp]),
                 "or_set_delta": (i, [vp, dp]),
@@ -345,6 +347,21 @@ class Sim:
     @property
     def step_count(self) -> int:
         return _lib().or_step_count(self._h)
+
+    def set_body_dynamics(self, b: int, mass: float, inertia, force_ext=(0.0, 0.0, 0.0), torque_ext=(0.0, 0.0, 0.0)):
+        """Two-way coupling of body b from the current step (semi-implicit Euler
+        of the rigid-body equations of motion under the force and torque of each
+        step plus constant external loads)."""
+        Ib = np.ascontiguousarray(inertia, dtype=np.float64).reshape(9)
+        if _lib().or_set_body_dynamics(self._h, b, float(mass), _dp(Ib), _dp(_d3(force_ext)),
+                                       _dp(_d3(torque_ext))) != 0:
+            raise ValueError("bad body dynamics")
+
+    def body_state(self, b: int):
+        """dict R, v, Q (3x3), omega, L of body b for the next step."""
+        out = np.zeros(21)
+        _lib().or_body_state(self._h, b, _dp(out))
+        return dict(R=out[0:3], v=out[3:6], Q=out[6:15].reshape(3, 3), omega=out[15:18], L=out[18:21])
 
     def force_torque(self):
         """[steps, nbodies, 6] force and torque ON each body (-S of Eq. 10/11)."""

@@ -156,7 +156,36 @@ struct Body {
   T omega[3];            // angular velocity (rad / step), world frame: u_s
   double omega_pose[3];  // angular velocity that moves the geometry (pose)
   double v[3];           // translation velocity (cells / step)
+  // Two-way coupling (or_set_body_dynamics; value type only): the body moves
+  // under the force and torque the fluid exerts on it at each step.
+  bool free_body = false;
+  double mass = 0.0, Ib[9], Ibinv[9], Fext[3], Text[3];  // body-frame inertia, external loads (world)
+  double Rd[3], vd[3], Qd[9], wd[3], Ld[3];              // state: position, velocity, orientation, omega, L
 };
+
+// omega = Q Ib^-1 Q^T L (world frame)
+void omega_from_L(const double Q[9], const double Ibinv[9], const double L[3], double w[3]) {
+  double a[3], b[3];
+  for (int i = 0; i < 3; ++i) a[i] = Q[0 * 3 + i] * L[0] + Q[1 * 3 + i] * L[1] + Q[2 * 3 + i] * L[2];  // Q^T L
+  for (int i = 0; i < 3; ++i) b[i] = Ibinv[3 * i + 0] * a[0] + Ibinv[3 * i + 1] * a[1] + Ibinv[3 * i + 2] * a[2];
+  for (int i = 0; i < 3; ++i) w[i] = Q[3 * i + 0] * b[0] + Q[3 * i + 1] * b[1] + Q[3 * i + 2] * b[2];
+}
+
+// Q <- Rot(phi) Q, the rotation by the angle |phi| about phi / |phi| (Rodrigues)
+void rotate_by(double Q[9], const double phi[3]) {
+  const double a = std::sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+  if (!(a > 0.0)) return;
+  const double k[3] = {phi[0] / a, phi[1] / a, phi[2] / a};
+  const double c = std::cos(a), s = std::sin(a), oc = 1.0 - c;
+  const double Rm[9] = {c + oc * k[0] * k[0],        oc * k[0] * k[1] - s * k[2], oc * k[0] * k[2] + s * k[1],
+                        oc * k[1] * k[0] + s * k[2], c + oc * k[1] * k[1],        oc * k[1] * k[2] - s * k[0],
+                        oc * k[2] * k[0] - s * k[1], oc * k[2] * k[1] + s * k[0], c + oc * k[2] * k[2]};
+  double out[9];
+  for (int r = 0; r < 3; ++r)
+    for (int col = 0; col < 3; ++col)
+      out[3 * r + col] = Rm[3 * r + 0] * Q[col] + Rm[3 * r + 1] * Q[3 + col] + Rm[3 * r + 2] * Q[6 + col];
+  for (int k2 = 0; k2 < 9; ++k2) Q[k2] = out[k2];
+}
 
 // Pose of a body at step n (Sec. 3: the cell centre is multiplied by a rotation
 // matrix and shifted by a translation).  Rotation about the axis omega/|omega|
@@ -287,9 +316,10 @@ struct Sim {
     eps.assign(ncell, 0.0);
     owner.assign(ncell, -1);
     std::vector<double> best(ncell, 0.0);
+    const std::vector<Pose> poses = poses_at(n);
     for (size_t b = 0; b < bodies.size(); ++b) {
       const Body<T>& B = bodies[b];
-      Pose P = pose_at(B.Q0, B.R0, B.omega_pose, B.v, n);
+      const Pose& P = poses[b];
       for (int z = 0; z < cfg.nz; ++z)
         for (int y = 0; y < cfg.ny; ++y)
           for (int x = 0; x < cfg.nx; ++x) {
@@ -308,8 +338,37 @@ struct Sim {
 
   std::vector<Pose> poses_at(long n) const {
     std::vector<Pose> poses;
-    for (auto& B : bodies) poses.push_back(pose_at(B.Q0, B.R0, B.omega_pose, B.v, n));
+    for (auto& B : bodies) {
+      if (B.free_body) {
+        Pose P;
+        for (int k = 0; k < 9; ++k) P.Q[k] = B.Qd[k];
+        for (int k = 0; k < 3; ++k) P.R[k] = B.Rd[k];
+        poses.push_back(P);
+      } else {
+        poses.push_back(pose_at(B.Q0, B.R0, B.omega_pose, B.v, n));
+      }
+    }
     return poses;
+  }
+
+  // Two-way coupling, one explicit step of the rigid-body equations of motion
+  // (semi-implicit Euler, dt = 1) with the force F and torque Tq on the body of
+  // this step (about R_n):
+  //   v += (F + Fext) / m,  R += v,  L += Tq + Text,
+  //   Q <- Rot(w*) Q with w* = Q Ib^-1 Q^T L,  then w = Q Ib^-1 Q^T L;
+  // the next step's remap, u_s and lever arm use (R, Q, v, w).
+  void integrate_free(Body<T>& B, const double F[3], const double Tq[3]) {
+    for (int k = 0; k < 3; ++k) B.vd[k] += (F[k] + B.Fext[k]) / B.mass;
+    for (int k = 0; k < 3; ++k) B.Rd[k] += B.vd[k];
+    for (int k = 0; k < 3; ++k) B.Ld[k] += Tq[k] + B.Text[k];
+    double ws[3];
+    omega_from_L(B.Qd, B.Ibinv, B.Ld, ws);
+    rotate_by(B.Qd, ws);
+    omega_from_L(B.Qd, B.Ibinv, B.Ld, B.wd);
+    for (int k = 0; k < 3; ++k) {
+      B.omega[k] = T(B.wd[k]);
+      B.v[k] = B.vd[k];
+    }
   }
 
   // eps and owner of one cell at the pose of step n (same rule as remap_all)
@@ -505,6 +564,13 @@ struct Sim {
           }
       for (int k = 0; k < 3; ++k) ft.push_back(-SF[k]);
       for (int k = 0; k < 3; ++k) ft.push_back(-ST[k]);
+    }
+    for (int b = 0; b < nb; ++b) {
+      if (!bodies[b].free_body) continue;
+      const size_t o = ft.size() - (size_t)(nb - b) * 6;
+      const double F[3] = {val(ft[o]), val(ft[o + 1]), val(ft[o + 2])};
+      const double Tq[3] = {val(ft[o + 3]), val(ft[o + 4]), val(ft[o + 5])};
+      integrate_free(bodies[b], F, Tq);
     }
 
     // Streaming, Eq. 1: f_i(x + c_i, t + 1) = post_i(x), read as a pull from
@@ -841,6 +907,62 @@ int or_set_body_us_omega(void* h, int b, const double* omega) {
   auto* S = static_cast<Sim<double>*>(h);
   if (b < 0 || b >= (int)S->bodies.size()) return -1;
   for (int k = 0; k < 3; ++k) S->bodies[b].omega[k] = omega[k];
+  return 0;
+}
+// Two-way coupling of body b from the current step: mass, body-frame inertia
+// Ib[9] (symmetric positive definite), constant external force and torque
+// (world).  The state starts from the prescribed motion at the current step.
+int or_set_body_dynamics(void* h, int b, double mass, const double* Ib, const double* Fext, const double* Text) {
+  auto* S = static_cast<Sim<double>*>(h);
+  if (b < 0 || b >= (int)S->bodies.size() || !(mass > 0.0)) return -1;
+  Body<double>& B = S->bodies[b];
+  const double det = Ib[0] * (Ib[4] * Ib[8] - Ib[5] * Ib[7]) - Ib[1] * (Ib[3] * Ib[8] - Ib[5] * Ib[6]) +
+                     Ib[2] * (Ib[3] * Ib[7] - Ib[4] * Ib[6]);
+  if (!(det > 0.0)) return -1;
+  // inverse by cofactors
+  B.Ibinv[0] = (Ib[4] * Ib[8] - Ib[5] * Ib[7]) / det;
+  B.Ibinv[1] = (Ib[2] * Ib[7] - Ib[1] * Ib[8]) / det;
+  B.Ibinv[2] = (Ib[1] * Ib[5] - Ib[2] * Ib[4]) / det;
+  B.Ibinv[3] = (Ib[5] * Ib[6] - Ib[3] * Ib[8]) / det;
+  B.Ibinv[4] = (Ib[0] * Ib[8] - Ib[2] * Ib[6]) / det;
+  B.Ibinv[5] = (Ib[2] * Ib[3] - Ib[0] * Ib[5]) / det;
+  B.Ibinv[6] = (Ib[3] * Ib[7] - Ib[4] * Ib[6]) / det;
+  B.Ibinv[7] = (Ib[1] * Ib[6] - Ib[0] * Ib[7]) / det;
+  B.Ibinv[8] = (Ib[0] * Ib[4] - Ib[1] * Ib[3]) / det;
+  for (int k = 0; k < 9; ++k) B.Ib[k] = Ib[k];
+  for (int k = 0; k < 3; ++k) {
+    B.Fext[k] = Fext[k];
+    B.Text[k] = Text[k];
+  }
+  B.mass = mass;
+  const Pose P = pose_at(B.Q0, B.R0, B.omega_pose, B.v, S->step);
+  for (int k = 0; k < 9; ++k) B.Qd[k] = P.Q[k];
+  for (int k = 0; k < 3; ++k) {
+    B.Rd[k] = P.R[k];
+    B.vd[k] = B.v[k];
+    B.wd[k] = B.omega[k];
+  }
+  // L = Q Ib Q^T w
+  double a[3], c[3];
+  for (int i = 0; i < 3; ++i) a[i] = B.Qd[0 * 3 + i] * B.wd[0] + B.Qd[1 * 3 + i] * B.wd[1] + B.Qd[2 * 3 + i] * B.wd[2];
+  for (int i = 0; i < 3; ++i) c[i] = Ib[3 * i + 0] * a[0] + Ib[3 * i + 1] * a[1] + Ib[3 * i + 2] * a[2];
+  for (int i = 0; i < 3; ++i) B.Ld[i] = B.Qd[3 * i + 0] * c[0] + B.Qd[3 * i + 1] * c[1] + B.Qd[3 * i + 2] * c[2];
+  B.free_body = true;
+  return 0;
+}
+// R[3], v[3], Q[9], omega[3], L[3] of body b (the pose of the next step to run)
+int or_body_state(void* h, int b, double* out) {
+  auto* S = static_cast<Sim<double>*>(h);
+  if (b < 0 || b >= (int)S->bodies.size()) return -1;
+  const Body<double>& B = S->bodies[b];
+  if (B.free_body) {
+    for (int k = 0; k < 3; ++k) out[k] = B.Rd[k], out[3 + k] = B.vd[k], out[15 + k] = B.wd[k], out[18 + k] = B.Ld[k];
+    for (int k = 0; k < 9; ++k) out[6 + k] = B.Qd[k];
+  } else {
+    const Pose P = pose_at(B.Q0, B.R0, B.omega_pose, B.v, S->step);
+    for (int k = 0; k < 3; ++k) out[k] = P.R[k], out[3 + k] = B.v[k], out[15 + k] = B.omega[k], out[18 + k] = 0.0;
+    for (int k = 0; k < 9; ++k) out[6 + k] = P.Q[k];
+  }
   return 0;
 }
 int or_init_eq(void* h, double rho, const double* u) {
