@@ -265,6 +265,35 @@ int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const 
 /* Number of bodies attached. */
 int psm_num_bodies(psm_handle h, int* out);
 
+/* Two-way coupling (the paper's validation with a freely settling sphere,
+ * Sec. 4; the performance runs couple one way).  From the current step on,
+ * body `body` moves under the force and torque the fluid exerts on it (the
+ * values psm_force_torque returns) plus constant external loads, one
+ * semi-implicit Euler step of the rigid-body equations per time step (dt = 1):
+ *   v += (F + force_ext) / mass,  R += v,  L += T + torque_ext,
+ *   Q <- Rot(w*) Q  with w* = Q I^-1 Q^T L,  then w = Q I^-1 Q^T L,
+ * integrated on the device in FP64 after each step (no host synchronisation).
+ * The state starts from the prescribed motion at the current step (R_n, Q_n,
+ * v, omega, L = Q I Q^T omega); R is the torque reference point and should be
+ * the centre of mass.  Explicit coupling needs the body heavier than the fluid
+ * it displaces (otherwise the added-mass instability).  psm_set_geometry on
+ * the body returns it to prescribed motion.  PSM_ERR_ARG for a bad body, a
+ * non-positive mass or an inertia that is not symmetric positive definite;
+ * PSM_ERR_STATE while recording for psm_backward (which supports prescribed
+ * motion only) or with the remap frozen. */
+typedef struct {
+  double mass;          /* > 0 (lattice units: fluid density rho0 per cell) */
+  double inertia[9];    /* body-frame inertia about R, row-major, symmetric positive definite */
+  double force_ext[3];  /* constant external force, world frame (e.g. gravity minus buoyancy) */
+  double torque_ext[3]; /* constant external torque about R, world frame */
+} psm_body_dynamics;
+int psm_set_body_dynamics(psm_handle h, int body, const psm_body_dynamics* dyn);
+
+/* Motion of body `body` for the next step to run: R[3], v[3], Q[9]
+ * (world <- body, row-major), omega[3], L[3] (21 doubles; L = 0 for prescribed
+ * motion).  Synchronises. */
+int psm_body_state(psm_handle h, int body, double* out);
+
 /* Remapping of the moving geometry onto eps (Sec. 3): every_step = 1
  * (default) remaps at every step from that step's pose; 0 freezes the poses of
  * all bodies at the current step (eps, the reference point R and the lever

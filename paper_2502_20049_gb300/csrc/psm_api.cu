@@ -109,6 +109,10 @@ struct psm_solver {
   // psm_set_remap(h, 0): every later step uses the body poses of step frozen_step
   bool remap_frozen = false;
   int64_t frozen_step = 0;
+  // two-way coupled bodies (bit b): their state and next-step DevBody on the device
+  unsigned free_mask = 0;
+  psm::BodyDyn* d_dyn = nullptr;
+  psm::DevBody* d_dev_bodies = nullptr;
   double ghost[27];
   int max_blocks = 0;
   double* d_partials = nullptr;
@@ -259,6 +263,90 @@ cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, i
   long long b = (n + PSM_THREADS - 1) / PSM_THREADS;
   if (b > 4096) b = 4096;
   k_occupancy<<<(int)(b < 1 ? 1 : b), PSM_THREADS, 0, st>>>(bricks, gx, gy, gz, wpb, occ);
+  return cudaGetLastError();
+}
+
+// One semi-implicit Euler step of the rigid-body equations per body in mask
+// (thread b), from this step's force and torque on the body ft[b][6]:
+//   v += (F + Fext) / m,  R += v,  L += T + Text,
+//   Q <- Rot(w*) Q, w* = Q Ib^-1 Q^T L,  w = Q Ib^-1 Q^T L,
+// then the DevBody of the next step (pose rounded to float for the remap,
+// kinematics, the cell box of the rotated geometry box widened by 2.5 cells).
+__device__ void q_ibinv_qt(const double* Q, const double* Ibinv, const double* L, double* w) {
+  double a[3], b[3];
+  for (int i = 0; i < 3; ++i) a[i] = Q[i] * L[0] + Q[3 + i] * L[1] + Q[6 + i] * L[2];
+  for (int i = 0; i < 3; ++i) b[i] = Ibinv[3 * i] * a[0] + Ibinv[3 * i + 1] * a[1] + Ibinv[3 * i + 2] * a[2];
+  for (int i = 0; i < 3; ++i) w[i] = Q[3 * i] * b[0] + Q[3 * i + 1] * b[1] + Q[3 * i + 2] * b[2];
+}
+
+__global__ void k_body_update(BodyDyn* dyn, DevBody* dev, const double* ft, unsigned mask, int nb, int nx, int ny,
+                              int nz) {
+  const int b = threadIdx.x;
+  if (b >= nb || !((mask >> b) & 1u)) return;
+  BodyDyn& S = dyn[b];
+  const double* F = ft + 6 * b;
+  for (int k = 0; k < 3; ++k) S.v[k] += (F[k] + S.Fext[k]) / S.mass;
+  for (int k = 0; k < 3; ++k) S.R[k] += S.v[k];
+  for (int k = 0; k < 3; ++k) S.L[k] += F[3 + k] + S.Text[k];
+  double ws[3];
+  q_ibinv_qt(S.Q, S.Ibinv, S.L, ws);
+  const double a = sqrt(ws[0] * ws[0] + ws[1] * ws[1] + ws[2] * ws[2]);
+  if (a > 0.0) {
+    const double k0 = ws[0] / a, k1 = ws[1] / a, k2 = ws[2] / a;
+    double sn, cs;
+    sincos(a, &sn, &cs);
+    const double oc = 1.0 - cs;
+    const double Rm[9] = {cs + oc * k0 * k0,      oc * k0 * k1 - sn * k2, oc * k0 * k2 + sn * k1,
+                          oc * k1 * k0 + sn * k2, cs + oc * k1 * k1,      oc * k1 * k2 - sn * k0,
+                          oc * k2 * k0 - sn * k1, oc * k2 * k1 + sn * k0, cs + oc * k2 * k2};
+    double Qn[9];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) Qn[3 * r + c] = Rm[3 * r] * S.Q[c] + Rm[3 * r + 1] * S.Q[3 + c] + Rm[3 * r + 2] * S.Q[6 + c];
+    for (int k = 0; k < 9; ++k) S.Q[k] = Qn[k];
+  }
+  q_ibinv_qt(S.Q, S.Ibinv, S.L, S.w);
+  DevBody& d = dev[b];
+  for (int k = 0; k < 9; ++k) d.Qf[k] = (float)S.Q[k];
+  for (int k = 0; k < 3; ++k) {
+    d.Rf[k] = (float)S.R[k];
+    d.R[k] = S.R[k];
+    d.omega[k] = S.w[k];
+    d.v[k] = S.v[k];
+    d.omegaf[k] = (float)S.w[k];
+    d.vf[k] = (float)S.v[k];
+  }
+  double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+  const double ext[3] = {(double)S.gx, (double)S.gy, (double)S.gz};
+  for (int c = 0; c < 8; ++c) {
+    double pb[3];
+    for (int k = 0; k < 3; ++k) pb[k] = S.lo[k] + (((c >> k) & 1) ? ext[k] : 0.0);
+    for (int r = 0; r < 3; ++r) {
+      const double w = S.Q[3 * r] * pb[0] + S.Q[3 * r + 1] * pb[1] + S.Q[3 * r + 2] * pb[2] + S.R[r];
+      mn[r] = fmin(mn[r], w);
+      mx[r] = fmax(mx[r], w);
+    }
+  }
+  const int dims[3] = {nx, ny, nz};
+  int lo_[3], hi_[3];
+  for (int k = 0; k < 3; ++k) {
+    double a0 = floor(mn[k] - 2.5), e = ceil(mx[k] + 2.5) + 1.0;
+    if (a0 < 0) a0 = 0;
+    if (e > (double)dims[k]) e = (double)dims[k];
+    if (e < a0) e = a0;
+    lo_[k] = (int)a0;
+    hi_[k] = (int)e;
+  }
+  d.x0 = lo_[0];
+  d.x1 = hi_[0];
+  d.y0 = lo_[1];
+  d.y1 = hi_[1];
+  d.z0 = lo_[2];
+  d.z1 = hi_[2];
+}
+
+cudaError_t launch_body_update(BodyDyn* dyn, DevBody* dev, const double* ft, unsigned mask, int nb, int nx, int ny,
+                               int nz, cudaStream_t st) {
+  k_body_update<<<1, 32, 0, st>>>(dyn, dev, ft, mask, nb, nx, ny, nz);
   return cudaGetLastError();
 }
 
@@ -696,6 +784,8 @@ int psm_destroy(psm_handle h) {
   cudaFree(h->d_err);
   for (void* c : h->ckpt) cudaFree(c);
   for (void* c : h->rec_slots) cudaFree(c);
+  cudaFree(h->d_dyn);
+  cudaFree(h->d_dev_bodies);
   cudaFree(h->rec_lam[0]);
   cudaFree(h->rec_lam[1]);
   cudaFree(h->rec_grad);
@@ -917,6 +1007,16 @@ int psm_get_eps(psm_handle h, float* eps) {
     p.t = h->tiling;
     p.nbodies = h->nbodies;
     for (int b = 0; b < h->nbodies; ++b) p.body[b] = dev_body(h, b, h->step);
+    if (h->free_mask) {
+      // two-way coupled bodies: their pose of this step lives on the device
+      cudaError_t e0 = cudaStreamSynchronize(h->stream);
+      for (int b = 0; b < h->nbodies && e0 == cudaSuccess; ++b)
+        if ((h->free_mask >> b) & 1u) e0 = cudaMemcpy(&p.body[b], h->d_dev_bodies + b, sizeof(DevBody), cudaMemcpyDeviceToHost);
+      if (e0 != cudaSuccess) {
+        rc = cuda_fail(e0, "body state read");
+        break;
+      }
+    }
     p.z_begin = z0;
     p.z_end = z1;
     p.eps_out = tmp;
@@ -974,6 +1074,7 @@ int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const 
     b.v[k] = v[k];
   }
   for (int k = 0; k < 9; ++k) b.Q0[k] = Q0[k];
+  h->free_mask &= ~(1u << body);  // prescribed motion again
   if (body == h->nbodies) h->nbodies++;
   return PSM_OK;
 }
@@ -1023,6 +1124,8 @@ int psm_step(psm_handle h, int n) {
       p.f_dst = nullptr;
     }
     psm::set_slots(p, h->lat.storage, h->Q);
+    p.free_mask = h->free_mask;
+    p.dbody = h->d_dev_bodies;
     // the AA odd step runs with plain loads unless its TMA variant applies
     const bool tma_now = use_tma && (mode != psm::MODE_AA_ODD ||
                                      (h->tma_odd_ok && (h->variant == PSM_KERNEL_TMA || !PSM_AA_ODD_PLAIN)));
@@ -1037,6 +1140,11 @@ int psm_step(psm_handle h, int n) {
     cudaError_t e = tma_now ? psm::launch_step_tma(h->lat.storage, h->Q, mode, p, tm, h->stream)
                             : psm::launch_step(h->lat.storage, h->Q, mode, p, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    if (h->free_mask) {
+      e = psm::launch_body_update(h->d_dyn, h->d_dev_bodies, p.ft_out, h->free_mask, h->nbodies, (int)h->grid.nx,
+                                  (int)h->grid.ny, (int)h->grid.nz, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "body update launch");
+    }
     if (h->lat.streaming == PSM_STREAM_TWO_GRID) h->cur ^= 1;
     h->step++;
   }
@@ -1097,6 +1205,8 @@ int psm_record(psm_handle h, int K, int flags) {
     return fail(PSM_ERR_ARG, "AA streaming: record from an even step with an even K (checkpoints need the "
                              "natural layout)");
   if (flags & ~PSM_RECORD_INIT_FROM_INFLOW) return fail(PSM_ERR_ARG, "unknown record flags");
+  if (h->free_mask)
+    return fail(PSM_ERR_STATE, "psm_backward supports prescribed motion only (two-way coupled bodies attached)");
   {
     const int rc = ensure_backward_buffers(h, K);
     if (rc != PSM_OK) return rc;
@@ -1358,8 +1468,86 @@ int psm_set_remap(psm_handle h, int every_step) {
   if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_set_remap: NULL handle");
   if (every_step != 0 && every_step != 1) return fail(PSM_ERR_ARG, "psm_set_remap: every_step must be 0 or 1");
   if (h->recording) return fail(PSM_ERR_STATE, "psm_set_remap while recording for psm_backward");
+  if (h->free_mask) return fail(PSM_ERR_STATE, "psm_set_remap with two-way coupled bodies");
   if (!every_step && !h->remap_frozen) h->frozen_step = h->step;
   h->remap_frozen = !every_step;
+  return PSM_OK;
+}
+
+int psm_set_body_dynamics(psm_handle h, int body, const psm_body_dynamics* dyn) {
+  if (!valid_handle(h) || !dyn) return fail(PSM_ERR_ARG, "psm_set_body_dynamics: NULL argument");
+  if (body < 0 || body >= h->nbodies) return fail(PSM_ERR_ARG, "no body %d", body);
+  if (h->recording) return fail(PSM_ERR_STATE, "two-way coupling while recording for psm_backward");
+  if (h->remap_frozen) return fail(PSM_ERR_STATE, "two-way coupling with the remap frozen");
+  const double* I = dyn->inertia;
+  bool ok = dyn->mass > 0.0 && std::isfinite(dyn->mass);
+  for (int k = 0; k < 9; ++k) ok = ok && std::isfinite(I[k]);
+  for (int k = 0; k < 3; ++k) ok = ok && std::isfinite(dyn->force_ext[k]) && std::isfinite(dyn->torque_ext[k]);
+  // symmetric positive definite: symmetric, leading principal minors > 0
+  ok = ok && I[1] == I[3] && I[2] == I[6] && I[5] == I[7];
+  const double m2 = I[0] * I[4] - I[1] * I[3];
+  const double det = I[0] * (I[4] * I[8] - I[5] * I[7]) - I[1] * (I[3] * I[8] - I[5] * I[6]) +
+                     I[2] * (I[3] * I[7] - I[4] * I[6]);
+  ok = ok && I[0] > 0.0 && m2 > 0.0 && det > 0.0;
+  if (!ok) return fail(PSM_ERR_ARG, "body dynamics: mass must be > 0 and the inertia symmetric positive definite");
+  if (!h->d_dyn) {
+    PSM_CUDA(cudaMalloc(&h->d_dyn, sizeof(psm::BodyDyn) * PSM_MAX_BODIES), "body state allocation");
+    PSM_CUDA(cudaMalloc(&h->d_dev_bodies, sizeof(DevBody) * PSM_MAX_BODIES), "body state allocation");
+  }
+  const HostBody& hb = h->body[body];
+  psm::BodyDyn S;
+  std::memset(&S, 0, sizeof S);
+  body_pose(hb, h->step, S.Q, S.R);
+  for (int k = 0; k < 3; ++k) {
+    S.v[k] = hb.v[k];
+    S.w[k] = hb.omega[k];
+    S.Fext[k] = dyn->force_ext[k];
+    S.Text[k] = dyn->torque_ext[k];
+    S.lo[k] = hb.lo[k];
+  }
+  S.gx = (int)hb.gx;
+  S.gy = (int)hb.gy;
+  S.gz = (int)hb.gz;
+  S.mass = dyn->mass;
+  // inverse inertia by cofactors
+  S.Ibinv[0] = (I[4] * I[8] - I[5] * I[7]) / det;
+  S.Ibinv[1] = (I[2] * I[7] - I[1] * I[8]) / det;
+  S.Ibinv[2] = (I[1] * I[5] - I[2] * I[4]) / det;
+  S.Ibinv[3] = (I[5] * I[6] - I[3] * I[8]) / det;
+  S.Ibinv[4] = (I[0] * I[8] - I[2] * I[6]) / det;
+  S.Ibinv[5] = (I[2] * I[3] - I[0] * I[5]) / det;
+  S.Ibinv[6] = (I[3] * I[7] - I[4] * I[6]) / det;
+  S.Ibinv[7] = (I[1] * I[6] - I[0] * I[7]) / det;
+  S.Ibinv[8] = (I[0] * I[4] - I[1] * I[3]) / det;
+  // L = Q I Q^T omega
+  double a[3], c[3];
+  for (int i = 0; i < 3; ++i) a[i] = S.Q[i] * S.w[0] + S.Q[3 + i] * S.w[1] + S.Q[6 + i] * S.w[2];
+  for (int i = 0; i < 3; ++i) c[i] = I[3 * i] * a[0] + I[3 * i + 1] * a[1] + I[3 * i + 2] * a[2];
+  for (int i = 0; i < 3; ++i) S.L[i] = S.Q[3 * i] * c[0] + S.Q[3 * i + 1] * c[1] + S.Q[3 * i + 2] * c[2];
+  const DevBody d = dev_body(h, body, h->step);  // this step's pose, as prescribed
+  PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  PSM_CUDA(cudaMemcpy(h->d_dyn + body, &S, sizeof S, cudaMemcpyHostToDevice), "body state upload");
+  PSM_CUDA(cudaMemcpy(h->d_dev_bodies + body, &d, sizeof d, cudaMemcpyHostToDevice), "body state upload");
+  h->free_mask |= 1u << body;
+  return PSM_OK;
+}
+
+int psm_body_state(psm_handle h, int body, double* out) {
+  if (!valid_handle(h) || !out) return fail(PSM_ERR_ARG, "psm_body_state: NULL argument");
+  if (body < 0 || body >= h->nbodies) return fail(PSM_ERR_ARG, "no body %d", body);
+  if ((h->free_mask >> body) & 1u) {
+    psm::BodyDyn S;
+    PSM_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+    PSM_CUDA(cudaMemcpy(&S, h->d_dyn + body, sizeof S, cudaMemcpyDeviceToHost), "body state read");
+    for (int k = 0; k < 3; ++k) out[k] = S.R[k], out[3 + k] = S.v[k], out[15 + k] = S.w[k], out[18 + k] = S.L[k];
+    for (int k = 0; k < 9; ++k) out[6 + k] = S.Q[k];
+  } else {
+    const HostBody& hb = h->body[body];
+    double Q[9], R[3];
+    body_pose(hb, h->remap_frozen ? h->frozen_step : h->step, Q, R);
+    for (int k = 0; k < 3; ++k) out[k] = R[k], out[3 + k] = hb.v[k], out[15 + k] = hb.omega[k], out[18 + k] = 0.0;
+    for (int k = 0; k < 9; ++k) out[6 + k] = Q[k];
+  }
   return PSM_OK;
 }
 

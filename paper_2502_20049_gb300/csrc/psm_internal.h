@@ -49,6 +49,16 @@ struct DevBody {
   int x0, x1, y0, y1, z0, z1;
 };
 
+// State of a body moving under the fluid's force and torque (two-way
+// coupling), integrated on the device after every step (FP64).
+struct BodyDyn {
+  double R[3], v[3], Q[9], w[3], L[3];  // position, velocity, orientation (world <- body), omega, L
+  double mass, Ibinv[9];                // mass, inverse body-frame inertia
+  double Fext[3], Text[3];              // constant external force and torque (world)
+  double lo[3];                         // geometry box origin (body frame)
+  int gx, gy, gz;                       // geometry box size (cells)
+};
+
 struct Grid3 {
   int nx, ny, nz;
   long long ncell;
@@ -94,6 +104,10 @@ struct StepParams {
   int weighting;  // 0 direct, 1 tau-weighted
   int nbodies;
   DevBody body[PSM_MAX_BODIES];
+  // bodies whose motion the device integrates (two-way coupling): bit b set ->
+  // body b of this step is dbody[b] (device memory), not body[b]
+  unsigned free_mask;
+  const DevBody* dbody;
   const float* delta;  // optional additive eps perturbation per cell (nullptr: none)
   // force/torque reduction
   double* partials;      // [gridDim.x][nbodies * 6]
@@ -170,6 +184,10 @@ cudaError_t launch_export_raw(int storage, int Q, const IoParams& p, cudaStream_
 cudaError_t launch_macro(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_mass(int storage, int Q, const IoParams& p, int blocks, cudaStream_t st);
 cudaError_t launch_remap(const RemapParams& p, cudaStream_t st);
+// one rigid-body step of the bodies in `mask` from the force/torque series
+// entry ft (this step's) -> their DevBody of the next step
+cudaError_t launch_body_update(BodyDyn* dyn, DevBody* dev, const double* ft, unsigned mask, int nb, int nx, int ny,
+                               int nz, cudaStream_t st);
 // occupancy of a geometry field (DevBody::occ) from its bricks (device)
 cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, int gz, int wpb, unsigned char* occ,
                              cudaStream_t st);

@@ -462,13 +462,13 @@ __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drh
 // torque on the body (minus Eq. 10 / 11 per cell, about R_n).  A cell with
 // B = 0 takes exactly the arithmetic of fluid_relax.
 template <class T, int Q, int TRT>
-__device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int x, int y, int z, unsigned cell,
-                                            int& owner, bool& solid_cell, double (&ft)[6]) {
+__device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* bodies, T (&f)[Q], int x, int y,
+                                            int z, unsigned cell, int& owner, bool& solid_cell, double (&ft)[6]) {
   const ConstT<T>& C = cst<T>(p);
   const T om_a = C.om_a, om_b = C.om_b;
   const T inv_tau = C.inv_tau;
   // ---- remap (Sec. 3) and weighting (Eq. 5/6) ----
-  const float epsf = cell_eps(p.body, p.nbodies, x, y, z, owner);
+  const float epsf = cell_eps(bodies, p.nbodies, x, y, z, owner);
   T eps = T(epsf);
   if (p.delta) eps += T(p.delta[cell]);
   T Bw = eps;
@@ -486,7 +486,7 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int 
   // ---- PSM cell: f* = f + (1 - B) Omega^F + B Omega^S (Eq. 4) ----
   T usx = 0, usy = 0, usz = 0;
   if (owner >= 0) {
-    const DevBody& b = p.body[owner];
+    const DevBody& b = bodies[owner];
     T rx, ry, rz, wx, wy, wz, vx, vy, vz;
     if constexpr (sizeof(T) == 4) {
       rx = (T(x) + T(0.5)) - b.Rf[0];
@@ -549,7 +549,7 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, T (&f)[Q], int 
   if (owner >= 0) {
     // Eq. 10 / 11 per cell; the body receives minus the solid's momentum transfer
     const double Gx = (double)(Bw * gx), Gy = (double)(Bw * gy), Gz = (double)(Bw * gz);
-    const DevBody& b = p.body[owner];
+    const DevBody& b = bodies[owner];
     const double Rx = (double)x + 0.5 - b.R[0], Ry = (double)y + 0.5 - b.R[1], Rz = (double)z + 0.5 - b.R[2];
     ft[0] = -Gx;
     ft[1] = -Gy;
@@ -691,16 +691,30 @@ struct TileWalk {
   }
 };
 
+// The bodies of this step, copied to shared memory at block start: from the
+// launch parameters, or, for bodies whose motion the device integrates
+// (two-way coupling), from device memory.  The caller synchronises the block.
+__device__ __forceinline__ void load_bodies(const StepParams& p, DevBody* s_body) {
+  static_assert(sizeof(DevBody) % 4 == 0, "DevBody is copied in 4-byte words");
+  constexpr int W = (int)(sizeof(DevBody) / 4);
+  for (int k = threadIdx.x; k < p.nbodies * W; k += blockDim.x) {
+    const int b = k / W, w = k % W;
+    const DevBody* src = ((p.free_mask >> b) & 1u) ? &p.dbody[b] : &p.body[b];
+    reinterpret_cast<unsigned*>(&s_body[b])[w] = reinterpret_cast<const unsigned*>(src)[w];
+  }
+}
+
 // A tile (TX x TY cells of one z plane) takes the fluid-only path when no
 // body's cell box meets it, no eps perturbation is set and its plane is not
 // next to a ghost plane: every cell of such a tile has B = 0, and no
 // population of it enters or leaves through a ghost plane.
-__device__ __forceinline__ bool tile_general(const StepParams& p, int x0, int y0, int z, int TX, int TY) {
+__device__ __forceinline__ bool tile_general(const StepParams& p, const DevBody* bodies, int x0, int y0, int z, int TX,
+                                             int TY) {
   bool gen = p.delta != nullptr || (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && (z == 0 || z == p.g.nz - 1));
 #pragma unroll
   for (int bi = 0; bi < PSM_MAX_BODIES; ++bi) {
     if (bi < p.nbodies) {
-      const DevBody& b = p.body[bi];
+      const DevBody& b = bodies[bi];
       gen = gen || (x0 < b.x1 && x0 + TX > b.x0 && y0 < b.y1 && y0 + TY > b.y0 && z >= b.z0 && z < b.z1);
     }
   }
@@ -731,9 +745,12 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     k_step(const __grid_constant__ StepParams p) {
   using T = typename Store<S>::T;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
+  __shared__ DevBody s_body[PSM_MAX_BODIES];
   const int nb = p.nbodies;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
+  load_bodies(p, s_body);
+  __syncthreads();
 
   const int ntiles = (int)p.t.ntiles;
   const int lx = (int)threadIdx.x % p.t.tx, ly = (int)threadIdx.x / p.t.tx;
@@ -752,7 +769,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
       zg.init(p.g, z);
       T f[Q];
       psm_load<S, Q, MODE, GEN>(p, sn, zg, cell, f);
-      if (GEN) psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
+      if (GEN) psm_collide<T, Q, TRT>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
       else fluid_collide<T, Q, TRT>(p, f);
       if (MODE == MODE_AA_ODD) {
         // rebuild the stencil for the stores rather than keep it live through
@@ -775,7 +792,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   walk.init(p.t, blockIdx.x, gridDim.x);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, walk.advance()) {
     const int x0 = walk.tx * p.t.tx, y0 = walk.ty * p.t.ty, z = walk.z;
-    if (tile_general(p, x0, y0, z, p.t.tx, p.t.ty)) cell_body(BoolC<true>{}, x0 + lx, y0 + ly, z);
+    if (tile_general(p, s_body, x0, y0, z, p.t.tx, p.t.ty)) cell_body(BoolC<true>{}, x0 + lx, y0 + ly, z);
     else cell_body(BoolC<false>{}, x0 + lx, y0 + ly, z);
   }
   if (nb == 0) return;
@@ -958,6 +975,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   __shared__ int s_abort;
   __shared__ int s_issued[NST];  // loads issued per stage (warp 0, lane 0)
   __shared__ int4 s_hdr[NST];    // per stage: tile origin x0, y0, z and the general-path flag
+  __shared__ DevBody s_body[PSM_MAX_BODIES];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // dynamic shared memory is only guaranteed 16-byte alignment: align by hand
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -985,6 +1003,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     }
     fence_mbar_init();
   }
+  load_bodies(p, s_body);
   __syncthreads();
 
   // producer: the 32 lanes of one warp stage the pre-collision PDFs of the
@@ -1030,7 +1049,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
         }
       }
     }
-    if (lane == 0) s_hdr[s] = make_int4(x0, y0, z, tile_general(p, x0, y0, z, TX, TY) ? 1 : 0);
+    if (lane == 0) s_hdr[s] = make_int4(x0, y0, z, tile_general(p, s_body, x0, y0, z, TX, TY) ? 1 : 0);
     __syncwarp();  // every lane's expected bytes are registered before the arrival
     if (lane == 0) {
       mbar_arrive(bar);
@@ -1090,7 +1109,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     int owner = -1;
     bool solid_cell = false;
     double ft[6] = {0, 0, 0, 0, 0, 0};
-    if (GEN) psm_collide<T, Q, TRT>(p, f, x, y, z, cell, owner, solid_cell, ft);
+    if (GEN) psm_collide<T, Q, TRT>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
     else fluid_collide<T, Q, TRT>(p, f);
     if (L::STORE_TMA) {
       // this warp's output box of tile k; lane 0 issued (and committed) the

@@ -68,6 +68,11 @@ class RotorParams(ctypes.Structure):
                 ("hand", ctypes.c_int)]
 
 
+class BodyDynamics(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("inertia", ctypes.c_double * 9), ("force_ext", ctypes.c_double * 3),
+                ("torque_ext", ctypes.c_double * 3)]
+
+
 def lib() -> ctypes.CDLL:
     """Load libpsm.so (raises if it has not been built)."""
     global _LIB
@@ -95,6 +100,8 @@ def lib() -> ctypes.CDLL:
                 "psm_get_pdfs": (i, [H, vp]),
                 "psm_force_torque_raw": (i, [H, i, i64, i64, vp]),
                 "psm_set_remap": (i, [H, i]),
+                "psm_set_body_dynamics": (i, [H, i, P(BodyDynamics)]),
+                "psm_body_state": (i, [H, i, vp]),
                 "psm_destroy": (i, [H]),
                 "psm_init_equilibrium": (i, [H, d, P(d)]),
                 "psm_set_state": (i, [H, vp]),
@@ -337,6 +344,19 @@ class Solver:
         rp, k1 = _ptr(rho, np.float64, self.ncell)
         up, k2 = _ptr(u, np.float64, 3 * self.ncell)
         check(lib().psm_init_equilibrium_field(self._h, rp, up))
+
+    def set_body_dynamics(self, body: int, mass: float, inertia, force_ext=(0.0, 0.0, 0.0),
+                          torque_ext=(0.0, 0.0, 0.0)):
+        """Two-way coupling of a body from the current step (psm_set_body_dynamics)."""
+        d = BodyDynamics(float(mass), (ctypes.c_double * 9)(*np.asarray(inertia, dtype=float).reshape(9)),
+                         (ctypes.c_double * 3)(*force_ext), (ctypes.c_double * 3)(*torque_ext))
+        check(lib().psm_set_body_dynamics(self._h, body, ctypes.byref(d)))
+
+    def body_state(self, body: int = 0):
+        """dict R, v, Q (3x3), omega, L of a body for the next step."""
+        out = np.zeros(21)
+        check(lib().psm_body_state(self._h, body, ctypes.c_void_p(out.ctypes.data)))
+        return dict(R=out[0:3], v=out[3:6], Q=out[6:15].reshape(3, 3), omega=out[15:18], L=out[18:21])
 
     def set_remap(self, every_step: bool):
         """Remap the geometry every step (True) or freeze the poses now (False)."""
