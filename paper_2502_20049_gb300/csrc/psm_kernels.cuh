@@ -666,6 +666,21 @@ __device__ __forceinline__ void block_ft_finish(double (*s_ft)[PSM_MAX_BODIES * 
 
 // Tile walk of a persistent block: tile index t = (z nty + ty) ntx + tx,
 // advanced by the grid size without divisions after the first tile.
+// (tile index t -> (tx, ty, z)) and its increment by a decomposed step
+__device__ __forceinline__ int4 tile_split(const Tiling& t, int tile) {
+  return make_int4(tile % t.ntx, (tile / t.ntx) % t.nty, tile / t.ntx / t.nty, 0);
+}
+__device__ __forceinline__ int4 tile_advance(const Tiling& t, int4 cur, int4 step) {
+  cur.x += step.x;
+  int c = cur.x >= t.ntx;
+  cur.x -= c ? t.ntx : 0;
+  cur.y += step.y + c;
+  c = cur.y >= t.nty;
+  cur.y -= c ? t.nty : 0;
+  cur.z += step.z + c;
+  return cur;
+}
+
 struct TileWalk {
   int tx, ty, z;       // current tile
   int gx, gy, gz;      // the grid size, decomposed like a tile index
@@ -1011,12 +1026,15 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   // walk.  Warp 0 stages the first NST tiles; afterwards warp w refills the
   // stage of tile j when j = w (mod NW), so the producer work rotates over the
   // warps (its walk: tiles w + NST, w + NST + NW, ... of this block).
-  TileWalk walk;
-  walk.init(p.t, blockIdx.x + (warp + NST) * gridDim.x, NW * gridDim.x);
-  auto produce = [&](TileWalk& walk, int s) {
-    const int z = walk.z;
-    const int x0 = walk.tx * TX, y0 = walk.ty * TY;
-    walk.advance();
+  // (kept in shared memory, not in registers across the tile loop)
+  __shared__ int4 s_walk[NW];  // per warp: the next tile it refills (tx, ty, z)
+  __shared__ int4 s_wstep;     // NW * gridDim.x, split like a tile index
+  if (lane == 0) s_walk[warp] = tile_split(p.t, blockIdx.x + (warp + NST) * gridDim.x);
+  if (threadIdx.x == 0) s_wstep = tile_split(p.t, NW * gridDim.x);
+  __syncthreads();
+  auto produce = [&](const int4 cur, int s) {
+    const int z = cur.z;
+    const int x0 = cur.x * TX, y0 = cur.y * TY;
     unsigned char* st = stages + s * L::STAGE;
     unsigned long long* bar = &full[s];
     fence_proxy_async();
@@ -1058,11 +1076,12 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
   };
 
   if (warp == 0) {
-    TileWalk first;
-    first.init(p.t, blockIdx.x, gridDim.x);
+    int4 first = tile_split(p.t, blockIdx.x);
+    const int4 g1 = tile_split(p.t, gridDim.x);
     for (int k = 0; k < NST; ++k) {
       const int tile = blockIdx.x + k * gridDim.x;
       if (tile < ntiles) produce(first, k);
+      first = tile_advance(p.t, first, g1);
     }
   }
 
@@ -1102,8 +1121,13 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
       if (next < ntiles) {
         const int sj = j % NST;
         // warp-uniform outcome (produce needs the whole warp)
-        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[sj], (unsigned)((j / NST) & 1)))) produce(walk, sj);
-        else s_abort = 1;
+        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[sj], (unsigned)((j / NST) & 1)))) {
+          const int4 cur = s_walk[warp];
+          produce(cur, sj);
+          if (lane == 0) s_walk[warp] = tile_advance(p.t, cur, s_wstep);
+        } else {
+          s_abort = 1;
+        }
       }
     }
     int owner = -1;
