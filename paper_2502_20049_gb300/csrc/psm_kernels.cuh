@@ -934,7 +934,8 @@ __device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return
 // The stage count NST fills the shared memory of the resident blocks the
 // launch bounds aim at (228 KB per SM, less 1 KB per block reserved and the
 // kernel's static shared memory), between 2 and PSM_TMA_MAX_STAGES: deeper
-// pipelines for the narrower storage types keep more bytes in flight.
+// pipelines for the narrower storage types keep more bytes in flight.  (A
+// launch checks that the resident blocks per SM reach the target.)
 template <class S, int Q, int MODE>
 struct TmaLayout {
   static constexpr bool LOAD_OWN = MODE != MODE_AA_ODD;
@@ -948,7 +949,11 @@ struct TmaLayout {
   static constexpr int OUT = STORE_TMA ? (PSM_THREADS / 32) * WBOX : 0;
   static constexpr int SM_SMEM = 233472;
   static constexpr int BLOCKS = step_min_blocks<S, Q>();
-  static constexpr int BUDGET0 = (SM_SMEM - BLOCKS * (1024 + 4096)) / BLOCKS - 256;
+  // per block: 1 KB reserved by the hardware and the kernel's static shared
+  // memory (about 5 KB: force/torque slots, reduction scratch, the bodies of
+  // the step, stage headers), allowed for with 6 KB
+  static constexpr int STATIC_SMEM = 6144;
+  static constexpr int BUDGET0 = (SM_SMEM - BLOCKS * (1024 + STATIC_SMEM)) / BLOCKS - 256;
   static constexpr int clamp_st(int n) { return n < 2 ? 2 : (n > PSM_TMA_MAX_STAGES ? PSM_TMA_MAX_STAGES : n); }
   // output boxes per warp: PSM_TMA_OUT_BUFS where that leaves at least 3 input stages, else 1
   static constexpr int NOUT = (PSM_TMA_OUT_BUFS > 1 && (BUDGET0 - PSM_TMA_OUT_BUFS * OUT) / STAGE >= 3) ? PSM_TMA_OUT_BUFS : 1;
