@@ -934,8 +934,8 @@ __device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return
 // The stage count NST fills the shared memory of the resident blocks the
 // launch bounds aim at (228 KB per SM, less 1 KB per block reserved and the
 // kernel's static shared memory), between 2 and PSM_TMA_MAX_STAGES: deeper
-// pipelines for the narrower storage types keep more bytes in flight.  (A
-// launch checks that the resident blocks per SM reach the target.)
+// pipelines for the narrower storage types keep more bytes in flight.  (The
+// launch refuses a build whose static shared memory exceeds STATIC_SMEM.)
 template <class S, int Q, int MODE>
 struct TmaLayout {
   static constexpr bool LOAD_OWN = MODE != MODE_AA_ODD;
@@ -1408,7 +1408,14 @@ template <class S, int Q, int MODE, int TRT>
 cudaError_t launch_step_tma_t(const StepParams& p, const TmaMaps& m, cudaStream_t st) {
   using L = TmaLayout<S, Q, MODE>;
   // persistent grid: resident blocks per SM (registers and shared memory), at most 8 per SM
+  // The stage count assumes at most L::STATIC_SMEM bytes of static shared
+  // memory per block; a build that exceeds it refuses to launch rather than
+  // silently losing resident blocks.
   static const int blocks = [] {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_step_tma<S, Q, MODE, TRT>) != cudaSuccess ||
+        fa.sharedSizeBytes > (size_t)L::STATIC_SMEM)
+      return 0;
     if (cudaFuncSetAttribute(k_step_tma<S, Q, MODE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) !=
         cudaSuccess)
       return 0;
