@@ -13,9 +13,9 @@ What each function follows (sections and equations of the paper):
 * :func:`feq` -- Eq. 3, read with ``-u.u/(2 c_s^2)`` (the printed ``+`` is a
   typo: with it the zeroth moment is not rho).
 * :func:`weighting` -- Eq. 5 (``mode=0``) and Eq. 6 (``mode=1``).
-* :class:`Sim` -- one step = remap (Sec. 3) -> Eq. 4 with Eq. 2 / TRT and the
-  solid collision Eq. 7 / 8 / 9 -> force and torque Eq. 10 / 11 -> streaming
-  Eq. 1.
+* :class:`Sim` -- one step = remap (Sec. 3) -> Eq. 4 with Eq. 2 / TRT / the
+  cumulant operator the paper cites in Sec. 2.2 (D3Q19) and the solid
+  collision Eq. 7 / 8 / 9 -> force and torque Eq. 10 / 11 -> streaming Eq. 1.
 * :func:`voxelize`, :func:`remap` -- the super-sampled geometry field and its
   per-step interpolation onto the lattice (Sec. 3).
 * :class:`TangentSim` -- the same code on dual numbers: exact directional
@@ -131,7 +131,7 @@ class _Cfg(ctypes.Structure):
         ("wall_u_lo", ctypes.c_double * 3), ("wall_u_hi", ctypes.c_double * 3),
         ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("u_in", ctypes.c_double * 3),
         ("fluid", ctypes.c_int), ("tau", ctypes.c_double), ("trt_lambda", ctypes.c_double),
-        ("solid", ctypes.c_int), ("weighting", ctypes.c_int),
+        ("solid", ctypes.c_int), ("weighting", ctypes.c_int), ("cum_rates", ctypes.c_double * 3),
     ]
 
 
@@ -140,7 +140,9 @@ class Config:
     """Oracle configuration (mirrors ``or_config`` in psm_oracle.cpp).
 
     ``bc_z``: 0 periodic, 1 equilibrium ghost planes f^eq(rho0, u_in) at z=-1 and
-    z=nz.  ``fluid``: 0 BGK (Eq. 2), 1 TRT.  ``solid``: 1/2/3 = Eq. 7/8/9.
+    z=nz.  ``fluid``: 0 BGK (Eq. 2), 1 TRT, 2 cumulant (D3Q19; ``cum_rates`` =
+    bulk, third-order and fourth-order rates; the shear rate is 1/tau).
+    ``solid``: 1/2/3 = Eq. 7/8/9.
     ``weighting``: 0 Eq. 5, 1 Eq. 6.  ``walls_y`` and ``force`` are oracle-only
     (half-way bounce-back walls and a Guo body force, used by the pins).
     """
@@ -161,6 +163,7 @@ class Config:
     wall_u_lo: tuple = (0.0, 0.0, 0.0)
     wall_u_hi: tuple = (0.0, 0.0, 0.0)
     force: tuple = (0.0, 0.0, 0.0)
+    cum_rates: tuple = (1.0, 1.0, 1.0)
 
     def _c(self):
         c = _Cfg()
@@ -171,6 +174,7 @@ class Config:
             c.wall_u_hi[k] = self.wall_u_hi[k]
             c.force[k] = self.force[k]
             c.u_in[k] = self.u_in[k]
+            c.cum_rates[k] = self.cum_rates[k]
         c.rho0, c.fluid, c.tau, c.trt_lambda = self.rho0, self.fluid, self.tau, self.trt_lambda
         c.solid, c.weighting = self.solid, self.weighting
         return c

@@ -5,7 +5,7 @@ import numpy as np
 
 from . import BodySpec, Config, Sim, voxelize
 
-FLUID = {"bgk": 0, "trt": 1}
+FLUID = {"bgk": 0, "trt": 1, "cumulant": 2}
 
 
 def sim_from_case(case, threads=None, init: bool = True) -> Sim:
@@ -16,7 +16,7 @@ def sim_from_case(case, threads=None, init: bool = True) -> Sim:
     FP64; the case's storage precision does not apply to it."""
     cfg = Config(nx=case.nx, ny=case.ny, nz=case.nz, Q=case.Q, bc_z=case.bc_z, rho0=case.rho0,
                  u_in=tuple(case.u_in), fluid=FLUID[case.fluid], tau=case.tau, trt_lambda=case.trt_lambda,
-                 solid=case.solid, weighting=case.weighting)
+                 solid=case.solid, weighting=case.weighting, cum_rates=tuple(case.cum_rates))
     sim = Sim(cfg, threads=threads)
     for b in case.bodies:
         sub, lo = voxelize(b.kind, b.params, b.s)

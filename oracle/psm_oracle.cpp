@@ -11,7 +11,7 @@
 //   * PDF array f[i][z][y][x] in natural (pull-streamed, pre-collision) form,
 //     direction order of THIS file: lexicographic in (cz, cy, cx) over {-1,0,1}^3;
 //   * one time step n = remap (Sec. 3) -> per-cell collision Eq. 4 with
-//     Eq. 2/TRT, Eq. 7-9, weighting Eq. 5/6 -> force/torque Eq. 10/11 ->
+//     Eq. 2/TRT/cumulant, Eq. 7-9, weighting Eq. 5/6 -> force/torque Eq. 10/11 ->
 //     streaming Eq. 1 with periodic x/y and either periodic z or equilibrium
 //     ghost planes in z;
 //   * all arithmetic in double (or Dual<double> for the tangent-linear model),
@@ -114,6 +114,121 @@ T weighting(int mode, T eps, double tau) {
   return eps * t / ((T(1.0) - eps) + t);
 }
 
+// ---------------------------------------------------------------------------
+// Cumulant collision on D3Q19.  The paper runs every performance case with
+// the cumulant operator of Geier et al. (2015), which it cites in Sec. 2.2
+// without restating it.  Its definition, restricted to the 19 moments a D3Q19
+// velocity set resolves:
+//   * central moments (rho-weighted) k_abc = sum_i f_i (c_ix - u_x)^a
+//     (c_iy - u_y)^b (c_iz - u_z)^c for the 19 exponent triples with
+//     a, b, c in {0, 1, 2}, not all three non-zero;
+//   * cumulants: of order <= 3 they equal the central moments; of order 4,
+//     C_220 = k_220 - (k_200 k_020 + 2 k_110^2) / rho (and its permutations);
+//   * relaxation towards the cumulant equilibrium (second order rho c_s^2
+//     delta_ab, higher orders 0): the off-diagonal and deviatoric diagonal
+//     second-order cumulants with the shear rate omega_s = 1/tau, their trace
+//     with the bulk rate omega_b, every third-order cumulant with omega_3,
+//     every fourth-order one with omega_4 (rho and u are conserved);
+//   * post-collision central moments from the relaxed cumulants (the same
+//     order-4 relation), and the post-collision PDFs as the solution of the
+//     19 x 19 linear system sum_i M_mi(u) f*_i = k*_m.
+// rates = {omega_s, omega_b, omega_3, omega_4}.
+// ---------------------------------------------------------------------------
+constexpr int kCumE[19][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2},
+                              {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {0, 2, 1},
+                              {1, 0, 2}, {0, 1, 2}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}};
+
+inline int cum_index(int a, int b, int c) {
+  for (int m = 0; m < 19; ++m)
+    if (kCumE[m][0] == a && kCumE[m][1] == b && kCumE[m][2] == c) return m;
+  return -1;
+}
+
+template <class T>
+T ipow(T x, int e) {
+  T r(1.0);
+  for (int k = 0; k < e; ++k) r = r * x;
+  return r;
+}
+
+// Solve A x = b (n x n, row-major, both overwritten) by Gaussian elimination
+// with partial pivoting on the values.
+template <class T>
+void gauss_solve(int n, T* A, T* b, T* x) {
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(val(A[r * n + col])) > std::fabs(val(A[piv * n + col]))) piv = r;
+    if (piv != col) {
+      for (int k = 0; k < n; ++k) std::swap(A[col * n + k], A[piv * n + k]);
+      std::swap(b[col], b[piv]);
+    }
+    for (int r = col + 1; r < n; ++r) {
+      const T fac = A[r * n + col] / A[col * n + col];
+      for (int k = col; k < n; ++k) A[r * n + k] -= fac * A[col * n + k];
+      b[r] -= fac * b[col];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    T acc = b[r];
+    for (int k = r + 1; k < n; ++k) acc -= A[r * n + k] * x[k];
+    x[r] = acc / A[r * n + r];
+  }
+}
+
+template <class T>
+void cumulant_post(const Lattice& L, const double rates[4], const T* f, T rho, const T u[3], T* post) {
+  const double ws = rates[0], wb = rates[1], w3 = rates[2], w4 = rates[3];
+  const double cs2 = 1.0 / 3.0;
+  T M[19 * 19], k[19];
+  for (int m = 0; m < 19; ++m) {
+    k[m] = T(0.0);
+    for (int i = 0; i < 19; ++i) {
+      M[m * 19 + i] = ipow(T(double(L.c[i][0])) - u[0], kCumE[m][0]) * ipow(T(double(L.c[i][1])) - u[1], kCumE[m][1]) *
+                      ipow(T(double(L.c[i][2])) - u[2], kCumE[m][2]);
+      k[m] += M[m * 19 + i] * f[i];
+    }
+  }
+  auto K = [&](int a, int b, int c) -> T& { return k[cum_index(a, b, c)]; };
+  T kp[19];
+  for (int m = 0; m < 19; ++m) kp[m] = k[m];
+  auto KP = [&](int a, int b, int c) -> T& { return kp[cum_index(a, b, c)]; };
+  // conserved: k_000 = rho, first-order central moments 0
+  KP(0, 0, 0) = rho;
+  KP(1, 0, 0) = T(0.0);
+  KP(0, 1, 0) = T(0.0);
+  KP(0, 0, 1) = T(0.0);
+  // second order
+  KP(1, 1, 0) = K(1, 1, 0) * (1.0 - ws);
+  KP(1, 0, 1) = K(1, 0, 1) * (1.0 - ws);
+  KP(0, 1, 1) = K(0, 1, 1) * (1.0 - ws);
+  const T tr = K(2, 0, 0) + K(0, 2, 0) + K(0, 0, 2);
+  const T tr_eq = rho * (3.0 * cs2);
+  const T tr_post = tr + (tr_eq - tr) * wb;
+  KP(2, 0, 0) = tr_post / 3.0 + (K(2, 0, 0) - tr / 3.0) * (1.0 - ws);
+  KP(0, 2, 0) = tr_post / 3.0 + (K(0, 2, 0) - tr / 3.0) * (1.0 - ws);
+  KP(0, 0, 2) = tr_post / 3.0 + (K(0, 0, 2) - tr / 3.0) * (1.0 - ws);
+  // third order: cumulant = central moment, equilibrium 0
+  const int third[6][3] = {{2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}};
+  for (auto& e : third) KP(e[0], e[1], e[2]) = K(e[0], e[1], e[2]) * (1.0 - w3);
+  // fourth order: the three C_aab b-type cumulants of D3Q19
+  const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};  // (x,y), (x,z), (y,z)
+  for (auto& pr : pairs) {
+    int e4[3] = {0, 0, 0}, ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0}, eab[3] = {0, 0, 0};
+    e4[pr[0]] = 2; e4[pr[1]] = 2;
+    ea[pr[0]] = 2;
+    eb[pr[1]] = 2;
+    eab[pr[0]] = 1; eab[pr[1]] = 1;
+    const T Kab = K(eab[0], eab[1], eab[2]);
+    const T C4 = K(e4[0], e4[1], e4[2]) - (K(ea[0], ea[1], ea[2]) * K(eb[0], eb[1], eb[2]) + 2.0 * Kab * Kab) / rho;
+    const T C4p = C4 * (1.0 - w4);
+    const T KPab = KP(eab[0], eab[1], eab[2]);
+    KP(e4[0], e4[1], e4[2]) =
+        C4p + (KP(ea[0], ea[1], ea[2]) * KP(eb[0], eb[1], eb[2]) + 2.0 * KPab * KPab) / rho;
+  }
+  gauss_solve(19, M, kp, post);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -131,11 +246,12 @@ typedef struct {
   double force[3];       // oracle-only constant body force (Guo forcing)
   double rho0;           // reference density (ghost planes hold f^eq(rho0, u_in))
   double u_in[3];        // inflow velocity held by the ghost planes
-  int fluid;             // 0: BGK (Eq. 2), 1: TRT
+  int fluid;             // 0: BGK (Eq. 2), 1: TRT, 2: cumulant (D3Q19)
   double tau;            // relaxation time (TRT: 1/omega_plus)
   double trt_lambda;     // TRT magic parameter Lambda
   int solid;             // 1, 2, 3: SC1 (Eq. 7), SC2 (Eq. 8), SC3 (Eq. 9)
   int weighting;         // 0: B = eps (Eq. 5); 1: tau-weighted (Eq. 6)
+  double cum_rates[3];   // cumulant (fluid 2): omega_bulk, omega_3, omega_4
 } or_config;
 
 }  // extern "C"
@@ -433,8 +549,14 @@ struct Sim {
       E[i] = feq<T>(L, i, rho, u);    // f^eq(rho, u)
       G[i] = feq<T>(L, i, rho, us);   // f^eq(rho, u_s)
     }
-    // fluid collision: Eq. 2 (BGK) or two-relaxation-time
-    for (int i = 0; i < Q; ++i) {
+    // fluid collision: Eq. 2 (BGK), two-relaxation-time, or cumulant
+    if (cfg.fluid == 2) {
+      const double rates[4] = {1.0 / tau, cfg.cum_rates[0], cfg.cum_rates[1], cfg.cum_rates[2]};
+      T cp[27];
+      cumulant_post<T>(L, rates, fl, rho, u, cp);
+      for (int i = 0; i < Q; ++i) OF[i] = cp[i] - fl[i];
+    }
+    for (int i = 0; i < Q && cfg.fluid != 2; ++i) {
       const int ib = L.opp[i];
       if (cfg.fluid == 0) {
         OF[i] = -(fl[i] - E[i]) / tau;
@@ -610,6 +732,9 @@ template <class T>
 Sim<T>* make_sim(const or_config* cfg) {
   if (cfg->Q != 19 && cfg->Q != 27) return nullptr;
   if (cfg->nx <= 0 || cfg->ny <= 0 || cfg->nz <= 0) return nullptr;
+  // the cumulant operator is defined here on D3Q19 only, without a body force
+  if (cfg->fluid == 2 && (cfg->Q != 19 || cfg->force[0] != 0.0 || cfg->force[1] != 0.0 || cfg->force[2] != 0.0))
+    return nullptr;
   auto* S = new Sim<T>();
   S->cfg = *cfg;
   S->L = make_lattice(cfg->Q);

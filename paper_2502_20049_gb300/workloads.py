@@ -76,9 +76,10 @@ class Case:
     Q: int = 19
     storage: str = "fp32"         # fp64 | fp32 | fp16 | bf16
     streaming: str = "aa"         # aa | twogrid
-    fluid: str = "bgk"            # bgk | trt
+    fluid: str = "bgk"            # bgk | trt | cumulant (D3Q19)
     tau: float = 0.8
     trt_lambda: float = 3.0 / 16.0
+    cum_rates: tuple = (1.0, 1.0, 1.0)  # cumulant: bulk, third-order, fourth-order rates
     solid: int = 1                # SC1 / SC2 / SC3 (Eq. 7 / 8 / 9)
     weighting: int = 1            # 0: Eq. 5, 1: Eq. 6
     bc_z: int = 1                 # 0 periodic, 1 equilibrium inlet/outlet planes
