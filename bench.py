@@ -45,7 +45,17 @@ NCU_BYTES_PER_CELL = {
 }
 
 
-def workload(name: str, streaming: str):
+FLUID_NAME = {"bgk": "BGK", "trt": "TRT", "cumulant": "cumulant"}
+
+
+def with_fluid(case, desc, fluid):
+    """The workload with another fluid operator (None: its own)."""
+    if not fluid or fluid == case.fluid:
+        return case, desc
+    return case.with_(fluid=fluid), desc.replace(FLUID_NAME[case.fluid], FLUID_NAME[fluid], 1)
+
+
+def workload(name: str, streaming: str, fluid: str | None = None):
     from paper_2502_20049_gb300 import workloads as W
 
     if name == "c2":
@@ -67,20 +77,21 @@ def workload(name: str, streaming: str):
     else:
         raise SystemExit(f"unknown workload {name}")
     case = case.with_(streaming=streaming)
-    return case, desc
+    return with_fluid(case, desc, fluid)
 
 
-def reference_sample(name: str):
+def reference_sample(name: str, fluid: str | None = None):
     """The bounded sample the CPU oracle runs per step: the same workload on a
     48^3 lattice with the body scaled by 48/n (about 0.1 MLUP per step)."""
     from paper_2502_20049_gb300 import workloads as W
 
     if name == "c2":
-        return W.c2_ellipsoid(scale=48 / 256, n=48, steps=1)
-    if name == "c5":
-        return W.c5_large(dims=(48, 48, 48), steps=1)
-    storage = name.split("_")[1]
-    return W.c3_rotor(storage, scale=48 / 512, dims=(48, 48, 60), steps=1)
+        case = W.c2_ellipsoid(scale=48 / 256, n=48, steps=1)
+    elif name == "c5":
+        case = W.c5_large(dims=(48, 48, 48), steps=1)
+    else:
+        case = W.c3_rotor(name.split("_")[1], scale=48 / 512, dims=(48, 48, 60), steps=1)
+    return with_fluid(case, "", fluid)[0]
 
 
 def peaks():
@@ -148,11 +159,11 @@ class Clocks:
                 "reasons": reasons, "samples": len(loaded)}
 
 
-def cpu_baseline(name: str, steps: int = 3):
+def cpu_baseline(name: str, steps: int = 3, fluid: str | None = None):
     """The oracle as it stands on this host's cores: `steps` steps of the full workload."""
     from oracle.cases import sim_from_case as oracle_sim
 
-    case, _ = workload(name, "twogrid")
+    case, _ = workload(name, "twogrid", fluid)
     case = case.with_(storage="fp64")
     sim = oracle_sim(case)
     t0 = time.perf_counter()
@@ -172,14 +183,14 @@ def run_reference(args):
         return
     from oracle.cases import sim_from_case as oracle_sim
 
-    case = reference_sample(args.workload)
+    case = reference_sample(args.workload, args.fluid)
     sim = oracle_sim(case)
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
     dt = time.perf_counter() - t0
     mlups = case.cells * args.steps / dt / 1e6
-    _, desc = workload(args.workload, args.streaming)
+    _, desc = workload(args.workload, args.streaming, args.fluid)
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -205,11 +216,11 @@ def time_steps(sol, steps: int, stream) -> float:
     return ev0.elapsed_time(ev1) / 1e3
 
 
-def variant_mlups(name, streaming, storage, kernel, steps, warmup, stream):
-    """MLUPS of one storage / streaming variant of the workload (same timing rules)."""
+def variant_mlups(name, streaming, storage, kernel, steps, warmup, stream, fluid=None):
+    """MLUPS of one storage / streaming / fluid-operator variant of the workload (same timing rules)."""
     from paper_2502_20049_gb300 import psm
 
-    case, _ = workload(name, streaming)
+    case, _ = workload(name, streaming, fluid)
     case = case.with_(storage=storage)
     sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
     if kernel != "auto":
@@ -271,7 +282,7 @@ def run_ours(args):
     G.build()
     from paper_2502_20049_gb300 import psm
 
-    case, desc = workload(args.workload, args.streaming)
+    case, desc = workload(args.workload, args.streaming, args.fluid)
     if args.storage:
         case = case.with_(storage=args.storage)
         desc = desc.replace("FP32", args.storage.upper()).replace("FP16-shifted", args.storage.upper())
@@ -296,7 +307,8 @@ def run_ours(args):
     bpc = sol.bytes_per_cell_update()
     achieved = bpc * cells / (t / args.steps) / 1e9
     peak, peak_kind = peaks()
-    key = f"{args.workload}/{case.streaming}/{case.storage}/{sol.kernel_variant}"
+    key = f"{args.workload}/{case.streaming}/{case.storage}/{sol.kernel_variant}" + (
+        f"/{args.fluid}" if args.fluid else "")
     traffic = NCU_BYTES_PER_CELL.get(key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"hbm_gbs of {peak_kind}",
@@ -337,7 +349,13 @@ def run_ours(args):
         for streaming, storage in (("twogrid", "fp16"), ("twogrid", "bf16"), ("aa", "fp32"), ("aa", "fp16")):
             if streaming == case.streaming and storage == case.storage:
                 continue
-            vs[f"{storage}/{streaming}"] = variant_mlups(args.workload, streaming, storage, "auto", 300, 5, stream)
+            vs[f"{storage}/{streaming}"] = variant_mlups(args.workload, streaming, storage, "auto", 300, 5, stream,
+                                                         fluid=args.fluid)
+        # the cumulant operator (the paper's performance runs use it; D3Q19) on the same workload
+        if case.Q == 19 and case.fluid != "cumulant":
+            for streaming, storage in (("twogrid", "fp32"), ("twogrid", "fp16"), ("aa", "fp16")):
+                vs[f"{storage}/{streaming}/cumulant"] = variant_mlups(args.workload, streaming, storage, "auto", 300,
+                                                                       5, stream, fluid="cumulant")
         line["variants"] = vs
         # FP16-shifted storage against this storage, same streaming, one GPU each
         other = "fp16/" + case.streaming
@@ -345,7 +363,7 @@ def run_ours(args):
             line["fp16_over_fp32"] = round(vs[other]["mlups"] / (cells * args.steps / t / 1e6), 3)
         line["adjoint"] = adjoint_cost(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, fluid=args.fluid)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -362,6 +380,8 @@ def main():
     ap.add_argument("--streaming", default="twogrid", choices=["aa", "twogrid"])
     ap.add_argument("--storage", default=None, choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
+    ap.add_argument("--fluid", default=None, choices=["bgk", "trt", "cumulant"],
+                    help="fluid operator (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the variant and adjoint measurements")
     args = ap.parse_args()

@@ -8,7 +8,7 @@
  *   2. the remap of the super-sampled binary geometry field onto the per-cell
  *      solid fraction eps (Sec. 3),
  *   3. the per-cell PSM collision f* = f + (1 - B) Omega^F + B Omega^S
- *      (Eq. 4) with Omega^F = BGK (Eq. 2) or TRT, Omega^S = SC1/SC2/SC3
+ *      (Eq. 4) with Omega^F = BGK (Eq. 2), TRT or cumulant, Omega^S = SC1/SC2/SC3
  *      (Eq. 7/8/9), B = B(eps) (Eq. 5 or Eq. 6), f^eq of Eq. 3 (read with
  *      -u.u/(2 c_s^2)),
  *   4. streaming f_i(x + c_i, t + 1) = f*_i(x) (Eq. 1): AA pattern in place, or
@@ -73,6 +73,16 @@ extern "C" {
 /* psm_collision.fluid */
 #define PSM_BGK 0 /* single relaxation time, Eq. 2 */
 #define PSM_TRT 1 /* two relaxation times: omega+ = 1/tau, Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) */
+/* Cumulant operator (Geier et al. 2015; the paper's Sec. 2.2 names it as the
+ * operator of its performance runs), D3Q19 only: central moments of the 19
+ * exponent triples (a, b, c) in {0,1,2}^3 with at most two non-zero;
+ * cumulants (order <= 3: the central moments; order 4:
+ * C_220 = k_220 - (k_200 k_020 + 2 k_110^2) / rho and permutations) relaxed
+ * towards rho c_s^2 delta (second order) and 0 (higher orders): the
+ * off-diagonal and deviatoric second-order cumulants with 1/tau, their trace
+ * with cum_omega[0], third order with cum_omega[1], fourth order with
+ * cum_omega[2]; the PDFs are the unique D3Q19 set with the relaxed moments. */
+#define PSM_CUMULANT 2
 /* psm_collision.solid: SC1 (Eq. 7), SC2 (Eq. 8 as printed: u_s in both brackets), SC3 (Eq. 9) */
 #define PSM_SC1 1
 #define PSM_SC2 2
@@ -101,11 +111,14 @@ typedef struct {
 } psm_lattice;
 
 typedef struct {
-  int fluid;          /* PSM_BGK or PSM_TRT */
-  double tau;         /* relaxation time, > 1/2 (TRT: 1/omega+) */
-  double trt_lambda;  /* TRT Lambda (> 0); ignored for BGK.  3/16 is the usual choice */
+  int fluid;          /* PSM_BGK, PSM_TRT or PSM_CUMULANT (D3Q19 only) */
+  double tau;         /* relaxation time, > 1/2 (TRT: 1/omega+; cumulant: 1/shear rate) */
+  double trt_lambda;  /* TRT Lambda (> 0); ignored otherwise.  3/16 is the usual choice */
   int solid;          /* PSM_SC1, PSM_SC2 or PSM_SC3 */
   int weighting;      /* PSM_B_DIRECT or PSM_B_TAU_WEIGHTED */
+  double cum_omega[3]; /* PSM_CUMULANT: bulk, third-order and fourth-order rates, each in
+                          (0, 2), or 0 for the default 1 (relax to equilibrium in one step);
+                          ignored otherwise */
 } psm_collision;
 
 /*
@@ -352,7 +365,9 @@ int psm_set_eps_delta(psm_handle h, const float* delta);
  * streaming, n0 and K must be even.  flags:
  * PSM_RECORD_INIT_FROM_INFLOW declares that the state at n0 is
  * f^eq(rho0, u_in) (psm_create or psm_init_equilibrium(rho0, u_in)), so that
- * the gradient with respect to u_in includes the initial state. */
+ * the gradient with respect to u_in includes the initial state.
+ * PSM_ERR_UNSUPPORTED for the cumulant operator (the adjoint step is written
+ * for BGK and TRT). */
 #define PSM_RECORD_INIT_FROM_INFLOW 1
 int psm_record(psm_handle h, int K, int flags);
 

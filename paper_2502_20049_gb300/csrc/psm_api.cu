@@ -170,34 +170,26 @@ Tiling make_tiling(int nx, int ny, int nz) {
 
 cudaError_t launch_step(int storage, int Q, int mode, const StepParams& p, cudaStream_t st) {
   switch (storage) {
-    case PSM_FP64: return launch_step_fp64(Q, mode, p.trt, p, st);
-    case PSM_FP32: return launch_step_fp32(Q, mode, p.trt, p, st);
-    case PSM_FP16_SHIFTED: return launch_step_fp16(Q, mode, p.trt, p, st);
-    default: return launch_step_bf16(Q, mode, p.trt, p, st);
+    case PSM_FP64: return launch_step_fp64(Q, mode, p.fluid, p, st);
+    case PSM_FP32: return launch_step_fp32(Q, mode, p.fluid, p, st);
+    case PSM_FP16_SHIFTED: return launch_step_fp16(Q, mode, p.fluid, p, st);
+    default: return launch_step_bf16(Q, mode, p.fluid, p, st);
   }
 }
 cudaError_t launch_step_tma(int storage, int Q, int mode, const StepParams& p, const TmaMaps& m, cudaStream_t st) {
   switch (storage) {
-    case PSM_FP64: return launch_step_tma_fp64(Q, mode, p.trt, p, m, st);
-    case PSM_FP32: return launch_step_tma_fp32(Q, mode, p.trt, p, m, st);
-    case PSM_FP16_SHIFTED: return launch_step_tma_fp16(Q, mode, p.trt, p, m, st);
-    default: return launch_step_tma_bf16(Q, mode, p.trt, p, m, st);
+    case PSM_FP64: return launch_step_tma_fp64(Q, mode, p.fluid, p, m, st);
+    case PSM_FP32: return launch_step_tma_fp32(Q, mode, p.fluid, p, m, st);
+    case PSM_FP16_SHIFTED: return launch_step_tma_fp16(Q, mode, p.fluid, p, m, st);
+    default: return launch_step_tma_bf16(Q, mode, p.fluid, p, m, st);
   }
 }
-int tma_smem_bytes(int storage, int Q, int mode) {
+int tma_smem_bytes(int storage, int Q, int mode, int fl) {
   switch (storage) {
-    case PSM_FP64: return tma_smem_bytes_fp64(Q, mode);
-    case PSM_FP32: return tma_smem_bytes_fp32(Q, mode);
-    case PSM_FP16_SHIFTED: return tma_smem_bytes_fp16(Q, mode);
-    default: return tma_smem_bytes_bf16(Q, mode);
-  }
-}
-int step_grid_blocks(int storage, int Q, int mode, int trt) {
-  switch (storage) {
-    case PSM_FP64: return step_grid_blocks_fp64(Q, mode, trt);
-    case PSM_FP32: return step_grid_blocks_fp32(Q, mode, trt);
-    case PSM_FP16_SHIFTED: return step_grid_blocks_fp16(Q, mode, trt);
-    default: return step_grid_blocks_bf16(Q, mode, trt);
+    case PSM_FP64: return tma_smem_bytes_fp64(Q, mode, fl);
+    case PSM_FP32: return tma_smem_bytes_fp32(Q, mode, fl);
+    case PSM_FP16_SHIFTED: return tma_smem_bytes_fp16(Q, mode, fl);
+    default: return tma_smem_bytes_bf16(Q, mode, fl);
   }
 }
 #define PSM_IO_DISPATCH(FN)                                                    \
@@ -496,7 +488,7 @@ bool tma_shape(const psm_solver* h, psm::Tiling& t) {
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
   const int mode = h->lat.streaming == PSM_STREAM_TWO_GRID ? psm::MODE_TG : psm::MODE_AA_EVEN;
-  if (psm::tma_smem_bytes(h->lat.storage, h->Q, mode) > optin) return false;
+  if (psm::tma_smem_bytes(h->lat.storage, h->Q, mode, h->col.fluid) > optin) return false;
   t.tx = (int)TX;
   t.ty = (int)TY;
   t.ntx = (int)(nx / TX);
@@ -568,6 +560,12 @@ void fill_consts(const psm_solver* h, psm::ConstT<T>& c) {
   c.omp1 = (T)(1.0 - omp);
   c.hp1 = (T)(0.5 * (1.0 - omp));
   c.hm1 = (T)(0.5 * (1.0 - omm));
+  // cumulant: 1 - rate for the shear, bulk, third- and fourth-order families
+  c.cum1[0] = (T)(1.0 - 1.0 / h->col.tau);
+  for (int k = 0; k < 3; ++k) {
+    const double w = h->col.cum_omega[k] == 0.0 ? 1.0 : h->col.cum_omega[k];
+    c.cum1[k + 1] = (T)(1.0 - w);
+  }
   // weight per class |c|^2 = 0..3 (D3Q19 has no corner directions)
   const double w19[4] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0, 0.0};
   const double w27[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
@@ -672,7 +670,15 @@ int create_impl(const psm_grid* grid, const psm_lattice* lattice, const psm_coll
   if (lattice->streaming != PSM_STREAM_AA && lattice->streaming != PSM_STREAM_TWO_GRID)
     return fail(PSM_ERR_ARG, "bad streaming");
   if (lattice->storage < PSM_FP64 || lattice->storage > PSM_BF16_SHIFTED) return fail(PSM_ERR_ARG, "bad storage");
-  if (collision->fluid != PSM_BGK && collision->fluid != PSM_TRT) return fail(PSM_ERR_ARG, "bad fluid collision");
+  if (collision->fluid != PSM_BGK && collision->fluid != PSM_TRT && collision->fluid != PSM_CUMULANT)
+    return fail(PSM_ERR_ARG, "bad fluid collision");
+  if (collision->fluid == PSM_CUMULANT) {
+    if (lattice->stencil != PSM_D3Q19) return fail(PSM_ERR_UNSUPPORTED, "the cumulant operator is D3Q19 only");
+    for (int k = 0; k < 3; ++k) {
+      const double w = collision->cum_omega[k];
+      if (!(w == 0.0 || (w > 0.0 && w < 2.0))) return fail(PSM_ERR_ARG, "cum_omega must be 0 (default 1) or in (0, 2)");
+    }
+  }
   if (!(collision->tau > 0.5) || !std::isfinite(collision->tau)) return fail(PSM_ERR_ARG, "tau must be > 1/2");
   if (collision->fluid == PSM_TRT && !(collision->trt_lambda > 0.0)) return fail(PSM_ERR_ARG, "trt_lambda must be > 0");
   if (collision->solid < PSM_SC1 || collision->solid > PSM_SC3) return fail(PSM_ERR_ARG, "bad solid collision");
@@ -731,7 +737,7 @@ int create_impl(const psm_grid* grid, const psm_lattice* lattice, const psm_coll
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     h->tma_odd_ok = h->tma_ok && h->tma_tiling.tx == psm::PSM_THREADS &&
-                    psm::tma_smem_bytes(h->lat.storage, h->Q, psm::MODE_AA_ODD) <= optin;
+                    psm::tma_smem_bytes(h->lat.storage, h->Q, psm::MODE_AA_ODD, h->col.fluid) <= optin;
   }
   e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), h->stream);
   if (e == cudaSuccess)
@@ -1095,7 +1101,7 @@ int psm_step(psm_handle h, int n) {
   p.t = use_tma ? h->tma_tiling : h->tiling;
   fill_consts<float>(h, p.cf);
   fill_consts<double>(h, p.cd);
-  p.trt = h->col.fluid == PSM_TRT ? 1 : 0;
+  p.fluid = h->col.fluid;
   p.solid = h->col.solid;
   p.weighting = h->col.weighting;
   p.nbodies = h->nbodies;
@@ -1205,6 +1211,8 @@ int psm_record(psm_handle h, int K, int flags) {
     return fail(PSM_ERR_ARG, "AA streaming: record from an even step with an even K (checkpoints need the "
                              "natural layout)");
   if (flags & ~PSM_RECORD_INIT_FROM_INFLOW) return fail(PSM_ERR_ARG, "unknown record flags");
+  if (h->col.fluid == PSM_CUMULANT)
+    return fail(PSM_ERR_UNSUPPORTED, "psm_backward supports BGK and TRT (no adjoint of the cumulant operator)");
   if (h->free_mask)
     return fail(PSM_ERR_STATE, "psm_backward supports prescribed motion only (two-way coupled bodies attached)");
   {
@@ -1278,7 +1286,7 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   sp.t = tma_rec ? h->tma_tiling : h->tiling;
   fill_consts<float>(h, sp.cf);
   fill_consts<double>(h, sp.cd);
-  sp.trt = h->col.fluid == PSM_TRT ? 1 : 0;
+  sp.fluid = h->col.fluid;
   sp.solid = h->col.solid;
   sp.weighting = h->col.weighting;
   sp.nbodies = nb;
@@ -1292,7 +1300,7 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   ap.g = h->g;
   ap.t = h->tiling;
   ap.grad = grad;
-  ap.trt = sp.trt;
+  ap.trt = sp.fluid == PSM_TRT ? 1 : 0;
   ap.solid = sp.solid;
   ap.weighting = sp.weighting;
   ap.nbodies = nb;

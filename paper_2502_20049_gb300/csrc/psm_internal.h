@@ -86,6 +86,7 @@ struct ConstT {
   T pw[4];        // omega+ w_c
   T pk[4];        // 4.5 omega+ w_c
   T pd[4];        // 3 omega- w_c
+  T cum1[4];      // cumulant: 1 - omega for shear (1/tau), bulk, third order, fourth order
 };
 
 struct StepParams {
@@ -99,7 +100,7 @@ struct StepParams {
   // address computation
   void* src_slot[27];
   void* dst_slot[27];
-  int trt;
+  int fluid;      // PSM_BGK, PSM_TRT, PSM_CUMULANT
   int solid;      // 1, 2, 3
   int weighting;  // 0 direct, 1 tau-weighted
   int nbodies;
@@ -176,8 +177,7 @@ cudaError_t launch_step(int storage, int Q, int mode, const StepParams& p, cudaS
 // TMA-staged variant (shape rules at k_step_tma); p.t must be the TMA tiling.
 cudaError_t launch_step_tma(int storage, int Q, int mode, const StepParams& p, const TmaMaps& m, cudaStream_t st);
 // dynamic shared memory bytes of the TMA variant for one mode
-int tma_smem_bytes(int storage, int Q, int mode);
-int step_grid_blocks(int storage, int Q, int mode, int trt);
+int tma_smem_bytes(int storage, int Q, int mode, int fl);
 cudaError_t launch_import(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_export(int storage, int Q, const IoParams& p, cudaStream_t st);
 cudaError_t launch_export_raw(int storage, int Q, const IoParams& p, cudaStream_t st);
@@ -193,11 +193,10 @@ cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, i
                              cudaStream_t st);
 
 #define PSM_DECLARE_STORAGE(NAME)                                                          \
-  cudaError_t launch_step_##NAME(int Q, int mode, int trt, const StepParams& p, cudaStream_t st); \
-  cudaError_t launch_step_tma_##NAME(int Q, int mode, int trt, const StepParams& p, const TmaMaps& m, \
+  cudaError_t launch_step_##NAME(int Q, int mode, int fl, const StepParams& p, cudaStream_t st); \
+  cudaError_t launch_step_tma_##NAME(int Q, int mode, int fl, const StepParams& p, const TmaMaps& m, \
                                      cudaStream_t st);                                    \
-  int tma_smem_bytes_##NAME(int Q, int mode);                                             \
-  int step_grid_blocks_##NAME(int Q, int mode, int trt);                                  \
+  int tma_smem_bytes_##NAME(int Q, int mode, int fl);                                             \
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_raw_##NAME(int Q, const IoParams& p, cudaStream_t st);        \

@@ -311,8 +311,15 @@ __device__ __forceinline__ void grid_reduce(const double* blk, int ncomp, double
 // Resident blocks per SM of a step kernel for storage S and stencil Q: FP64
 // state needs twice the registers per PDF, so one block fewer (80 / 128 / 255
 // registers per thread at 3 / 2 / 1 blocks of 256 threads).
-template <class S, int Q>
+// The cumulant operator (FL = 2, D3Q19) keeps about twice the values of
+// BGK/TRT live: it aims at PSM_MIN_BLOCKS_CUM blocks (128 registers at 2),
+// and FP64 at one.
+#ifndef PSM_MIN_BLOCKS_CUM
+#define PSM_MIN_BLOCKS_CUM 2
+#endif
+template <class S, int Q, int FL = 0>
 __host__ __device__ constexpr int step_min_blocks() {
+  if (FL == 2) return sizeof(S) == 8 ? 1 : PSM_MIN_BLOCKS_CUM;
   return sizeof(S) == 8 ? (Q == 19 ? PSM_MIN_BLOCKS_Q19 - 1 : PSM_MIN_BLOCKS_Q27 - 1)
                         : (Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27);
 }
@@ -431,8 +438,16 @@ __device__ __forceinline__ T c_dot(int i, T ux, T uy, T uz) {
 // The products of omega+-, the weight and the numeric factors are host
 // constants per weight class (ConstT pw, pk, pd); f_i and f_j are not needed
 // once s and d are formed.
-template <class T, int Q, int TRT>
+template <class T>
+__device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T drho, T rho, T ux, T uy, T uz);
+
+template <class T, int Q, int FL>
 __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drho, T rho, T ux, T uy, T uz, T uu) {
+  if constexpr (FL == 2) {
+    static_assert(Q == 19, "the cumulant operator is defined for D3Q19");
+    cumulant_relax<T>(C, f, drho, rho, ux, uy, uz);
+    return;
+  }
   const T base = r_fma(T(-1.5), r_mul(rho, uu), drho);
   constexpr int NC = Q == 27 ? 4 : 3;
   T A[NC], K[NC], D[NC];  // per class: omega+ w base, 4.5 omega+ w rho, 3 omega- w rho
@@ -455,13 +470,151 @@ __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drh
   }
 }
 
+// Cumulant collision of one D3Q19 cell (the operator the paper names in
+// Sec. 2.2 for its performance runs: Geier et al. 2015), restricted to the 19
+// moments D3Q19 resolves, from the shifted PDFs f (f - w rho0), in place.
+//   raw moments of the shifted PDFs, plane by plane (D3Q19 has no corner
+//     directions, so the x-y face diagonals alone carry c_x^2 c_y^2, c_x^2 c_y,
+//     c_x c_y^2 and c_x c_y);
+//   central moments k_abc about u, kept as deviations from the fluid at rest
+//     (k^_200 = k_200 - rho/3, k^_220 = k_220 - rho/9): every term is then of
+//     the size of u^2 or the non-equilibrium part, so FP32 loses nothing to
+//     cancellation against rho/3 or rho/9;
+//   relaxation: off-diagonal and deviatoric second order with 1 - 1/tau, the
+//     trace with 1 - omega_bulk, third order with 1 - omega_3, the fourth-order
+//     cumulants C_220 = k_220 - (k_200 k_020 + 2 k_110^2) / rho with
+//     1 - omega_4 (host constants cum1[0..3]);
+//   raw moments of the result by the inverse shift, then the D3Q19 PDFs in
+//     closed form: f(sx, sy, 0) = (m_220 + sx m_120 + sy m_210 + sx sy m_110) / 4,
+//     f(s, 0, 0) = ((m_200 - m_220 - m_202) + s (m_100 - m_120 - m_102)) / 2,
+//     f_0 = m_000 - m_200 - m_020 - m_002 + m_220 + m_202 + m_022.
+// Operations are separately rounded (same bits in every kernel that inlines it).
+template <class T>
+__device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T drho, T rho, T ux, T uy, T uz) {
+  auto ad = [](T a, T b) { return r_add(a, b); };
+  auto sb = [](T a, T b) { return r_sub(a, b); };
+  auto ml = [](T a, T b) { return r_mul(a, b); };
+  auto fm = [](T a, T b, T c) { return r_fma(a, b, c); };
+  const T third = T(1.0 / 3.0), ninth = T(1.0 / 9.0);
+  // ---- raw moments of the shifted PDFs ----
+  const T Ax = ad(f[1], f[2]), Bx = sb(f[1], f[2]);
+  const T Ay = ad(f[3], f[4]), By = sb(f[3], f[4]);
+  const T Az = ad(f[5], f[6]), Bz = sb(f[5], f[6]);
+  T Sxy, Mxy, Xxy, Yxy, Sxz, Mxz, Xxz, Zxz, Syz, Myz, Yyz, Zyz;
+  {
+    // group (a, b) with f[k] = (+,+), f[k+1] = (-,-), f[k+2] = (+,-), f[k+3] = (-,+)
+    auto group = [&](int k, T& S, T& M, T& A, T& B) {
+      const T p1 = ad(f[k], f[k + 1]), m1 = sb(f[k], f[k + 1]);
+      const T p2 = ad(f[k + 2], f[k + 3]), m2 = sb(f[k + 2], f[k + 3]);
+      S = ad(p1, p2);  // sum c_a^2 c_b^2 f
+      M = sb(p1, p2);  // sum c_a c_b f
+      A = ad(m1, m2);  // sum c_a f (= sum c_a c_b^2 f)
+      B = sb(m1, m2);  // sum c_b f (= sum c_a^2 c_b f)
+    };
+    group(7, Sxy, Mxy, Xxy, Yxy);
+    group(11, Sxz, Mxz, Xxz, Zxz);
+    group(15, Syz, Myz, Yyz, Zyz);
+  }
+  const T jx = ad(ad(Bx, Xxy), Xxz), jy = ad(ad(By, Yxy), Yyz), jz = ad(ad(Bz, Zxz), Zyz);
+  const T m200 = ad(ad(Ax, Sxy), Sxz), m020 = ad(ad(Ay, Sxy), Syz), m002 = ad(ad(Az, Sxz), Syz);
+  // ---- central moments (deviation form) ----
+  const T dt = ml(drho, third), dn = ml(drho, ninth);
+  const T rux = ml(rho, ux), ruy = ml(rho, uy), ruz = ml(rho, uz);
+  const T k200 = sb(m200, fm(rux, ux, dt)), k020 = sb(m020, fm(ruy, uy, dt)), k002 = sb(m002, fm(ruz, uz, dt));
+  const T k110 = sb(Mxy, ml(rux, uy)), k101 = sb(Mxz, ml(rux, uz)), k011 = sb(Myz, ml(ruy, uz));
+  const T r0t = ml(C.rho0, third);
+  const T M200 = ad(m200, r0t), M020 = ad(m020, r0t), M002 = ad(m002, r0t);  // full raw c_a^2 moments
+  const T n2ux = ml(T(-2), ux), n2uy = ml(T(-2), uy), n2uz = ml(T(-2), uz);
+  // k_aab = m_aab - u_b M_aa - 2 u_a k_ab
+  const T k210 = fm(n2ux, k110, fm(-uy, M200, Yxy)), k120 = fm(n2uy, k110, fm(-ux, M020, Xxy));
+  const T k201 = fm(n2ux, k101, fm(-uz, M200, Zxz)), k102 = fm(n2uz, k101, fm(-ux, M002, Xxz));
+  const T k021 = fm(n2uy, k011, fm(-uz, M020, Zyz)), k012 = fm(n2uz, k011, fm(-uy, M002, Yyz));
+  const T uxx = ml(ux, ux), uyy = ml(uy, uy), uzz = ml(uz, uz);
+  // k^_aabb = (m_aabb - drho/9) - 2 u_b k_aab - 2 u_a k_abb - 4 u_a u_b k_ab - u_b^2 k^_aa
+  //           - u_a^2 k^_bb - rho (u_a^2 + u_b^2) / 3 - rho u_a^2 u_b^2
+  auto k4 = [&](T S, T kaab, T kabb, T ua, T ub, T uaa, T ubb, T kab, T kaa, T kbb) {
+    T r = sb(S, dn);
+    r = fm(ml(T(-2), ub), kaab, r);
+    r = fm(ml(T(-2), ua), kabb, r);
+    r = fm(ml(T(-4), ml(ua, ub)), kab, r);
+    r = fm(-ubb, kaa, r);
+    r = fm(-uaa, kbb, r);
+    r = fm(-ml(rho, third), ad(uaa, ubb), r);
+    return fm(-ml(rho, uaa), ubb, r);
+  };
+  const T k220 = k4(Sxy, k210, k120, ux, uy, uxx, uyy, k110, k200, k020);
+  const T k202 = k4(Sxz, k201, k102, ux, uz, uxx, uzz, k101, k200, k002);
+  const T k022 = k4(Syz, k021, k012, uy, uz, uyy, uzz, k011, k020, k002);
+  // ---- relaxation ----
+  const T s1 = C.cum1[0], b1 = C.cum1[1], t1 = C.cum1[2], q1 = C.cum1[3];
+  const T inv_rho = recip(rho);
+  const T d1 = ml(s1, sb(k200, k020)), d2 = ml(s1, sb(k200, k002)), tr = ml(b1, ad(ad(k200, k020), k002));
+  const T p200 = ml(ad(ad(tr, d1), d2), third);
+  const T p020 = ml(ad(fm(T(-2), d1, tr), d2), third);
+  const T p002 = ml(fm(T(-2), d2, ad(tr, d1)), third);
+  const T p110 = ml(s1, k110), p101 = ml(s1, k101), p011 = ml(s1, k011);
+  const T p210 = ml(t1, k210), p120 = ml(t1, k120), p201 = ml(t1, k201);
+  const T p102 = ml(t1, k102), p021 = ml(t1, k021), p012 = ml(t1, k012);
+  // fourth order: C = k^_aabb - (k^_aa + k^_bb)/3 - (k^_aa k^_bb + 2 k_ab^2)/rho, relaxed, and back
+  auto c4 = [&](T k, T kaa, T kbb, T kab, T paa, T pbb, T pab) {
+    const T c = sb(fm(-third, ad(kaa, kbb), k), ml(fm(kaa, kbb, ml(ml(T(2), kab), kab)), inv_rho));
+    return fm(third, ad(paa, pbb), ad(ml(q1, c), ml(fm(paa, pbb, ml(ml(T(2), pab), pab)), inv_rho)));
+  };
+  const T p220 = c4(k220, k200, k020, k110, p200, p020, p110);
+  const T p202 = c4(k202, k200, k002, k101, p200, p002, p101);
+  const T p022 = c4(k022, k020, k002, k011, p020, p002, p011);
+  // ---- raw moments of the result (shifted PDFs) ----
+  const T n200 = fm(rux, ux, ad(p200, dt)), n020 = fm(ruy, uy, ad(p020, dt)), n002 = fm(ruz, uz, ad(p002, dt));
+  const T n110 = fm(rux, uy, p110), n101 = fm(rux, uz, p101), n011 = fm(ruy, uz, p011);
+  const T rt = ml(rho, third);
+  const T F200 = fm(rux, ux, ad(p200, rt)), F020 = fm(ruy, uy, ad(p020, rt)), F002 = fm(ruz, uz, ad(p002, rt));
+  const T n2 = T(2);
+  const T n210 = fm(ml(n2, ux), p110, fm(uy, F200, p210)), n120 = fm(ml(n2, uy), p110, fm(ux, F020, p120));
+  const T n201 = fm(ml(n2, ux), p101, fm(uz, F200, p201)), n102 = fm(ml(n2, uz), p101, fm(ux, F002, p102));
+  const T n021 = fm(ml(n2, uy), p011, fm(uz, F020, p021)), n012 = fm(ml(n2, uz), p011, fm(uy, F002, p012));
+  // m_aabb = k^_aabb + drho/9 + 2 u_b k_aab + 2 u_a k_abb + 4 u_a u_b k_ab + u_b^2 (k^_aa + rho/3)
+  //          + u_a^2 (k^_bb + rho/3) + rho u_a^2 u_b^2
+  auto b4 = [&](T k, T kaab, T kabb, T ua, T ub, T uaa, T ubb, T kab, T kaa, T kbb) {
+    T r = ad(k, dn);
+    r = fm(ml(n2, ub), kaab, r);
+    r = fm(ml(n2, ua), kabb, r);
+    r = fm(ml(T(4), ml(ua, ub)), kab, r);
+    r = fm(ubb, ad(kaa, rt), r);
+    r = fm(uaa, ad(kbb, rt), r);
+    return fm(ml(rho, uaa), ubb, r);
+  };
+  const T n220 = b4(p220, p210, p120, ux, uy, uxx, uyy, p110, p200, p020);
+  const T n202 = b4(p202, p201, p102, ux, uz, uxx, uzz, p101, p200, p002);
+  const T n022 = b4(p022, p021, p012, uy, uz, uyy, uzz, p011, p020, p002);
+  // ---- PDFs ----
+  const T qtr = T(0.25), hf = T(0.5);
+  auto ungroup = [&](int k, T S, T M, T A, T B) {
+    const T a = ad(S, M), b = sb(S, M), p = ad(A, B), q = sb(A, B);
+    f[k] = ml(qtr, ad(a, p));
+    f[k + 1] = ml(qtr, sb(a, p));
+    f[k + 2] = ml(qtr, ad(b, q));
+    f[k + 3] = ml(qtr, sb(b, q));
+  };
+  ungroup(7, n220, n110, n120, n210);
+  ungroup(11, n202, n101, n102, n201);
+  ungroup(15, n022, n011, n012, n021);
+  auto axis = [&](int k, T e, T o) {
+    f[k] = ml(hf, ad(e, o));
+    f[k + 1] = ml(hf, sb(e, o));
+  };
+  axis(1, sb(sb(n200, n220), n202), sb(sb(jx, n120), n102));
+  axis(3, sb(sb(n020, n220), n022), sb(sb(jy, n210), n012));
+  axis(5, sb(sb(n002, n202), n022), sb(sb(jz, n201), n021));
+  f[0] = ad(ad(ad(sb(sb(sb(drho, n200), n020), n002), n220), n202), n022);
+}
+
 // One cell's PSM update in registers, from its pre-collision (shifted) PDFs f:
 // remap (Sec. 3), B (Eq. 5/6), moments, u_s = omega x r + v, Omega^F (Eq. 2 /
 // TRT), Omega^S (Eq. 7/8/9), blend (Eq. 4).  f becomes the post-collision
 // state.  For a cell in contact with a body (B > 0) ft receives the force and
 // torque on the body (minus Eq. 10 / 11 per cell, about R_n).  A cell with
 // B = 0 takes exactly the arithmetic of fluid_relax.
-template <class T, int Q, int TRT>
+template <class T, int Q, int FL>
 __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* bodies, T (&f)[Q], int x, int y,
                                             int z, unsigned cell, int& owner, bool& solid_cell, double (&ft)[6]) {
   const ConstT<T>& C = cst<T>(p);
@@ -480,7 +633,7 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
   moments<T, Q>(f, C.rho0, drho, rho, ux, uy, uz, uu);
   solid_cell = Bw != T(0);
   if (!solid_cell) {
-    fluid_relax<T, Q, TRT>(C, f, drho, rho, ux, uy, uz, uu);
+    fluid_relax<T, Q, FL>(C, f, drho, rho, ux, uy, uz, uu);
     return;
   }
   // ---- PSM cell: f* = f + (1 - B) Omega^F + B Omega^S (Eq. 4) ----
@@ -507,11 +660,20 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
   }
   const T usus = usx * usx + usy * usy + usz * usz;
   const T omB = T(1) - Bw;
+  // cumulant: Omega^F = C(f) - f from the relaxed copy fc
+  T fc[Q];
+  if constexpr (FL == 2) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fc[i] = f[i];
+    fluid_relax<T, Q, FL>(C, fc, drho, rho, ux, uy, uz, uu);
+  }
   T gx = 0, gy = 0, gz = 0;
   {
     const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
     const T m0 = f[0] - feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
-    const T of = -(om_a + om_b) * n0;
+    T of;
+    if constexpr (FL == 2) of = fc[0] - f[0];
+    else of = -(om_a + om_b) * n0;
     T os;
     if (p.solid == PSM_SC1) os = n0 - m0;
     else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
@@ -525,8 +687,14 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
     const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
     const T mi = f[i] - feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
     const T mj = f[j] - feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
-    const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
-    const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);
+    T ofi, ofj;
+    if constexpr (FL == 2) {
+      ofi = fc[i] - f[i];
+      ofj = fc[j] - f[j];
+    } else {
+      ofi = FL == 1 ? (-om_a * ni - om_b * nj) : (-om_a * ni);
+      ofj = FL == 1 ? (-om_a * nj - om_b * ni) : (-om_a * nj);
+    }
     T osi, osj;
     if (p.solid == PSM_SC1) {
       osi = nj - mi;
@@ -743,20 +911,20 @@ struct BoolC {
 
 // One cell of a fluid-only tile: moments and Omega^F (the arithmetic psm_collide
 // takes for B = 0).
-template <class T, int Q, int TRT>
+template <class T, int Q, int FL>
 __device__ __forceinline__ void fluid_collide(const StepParams& p, T (&f)[Q]) {
   const ConstT<T>& C = cst<T>(p);
   T drho, rho, ux, uy, uz, uu;
   moments<T, Q>(f, C.rho0, drho, rho, ux, uy, uz, uu);
-  fluid_relax<T, Q, TRT>(C, f, drho, rho, ux, uy, uz, uu);
+  fluid_relax<T, Q, FL>(C, f, drho, rho, ux, uy, uz, uu);
 }
 
 // ---------------------------------------------------------------------------
 // The fused step kernel with plain global loads (any grid shape; persistent:
 // blocks stride over tiles of TX x TY cells of one z plane).
 // ---------------------------------------------------------------------------
-template <class S, int Q, int MODE, int TRT>
-__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
+template <class S, int Q, int MODE, int FL>
+__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
     k_step(const __grid_constant__ StepParams p) {
   using T = typename Store<S>::T;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
@@ -784,8 +952,8 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
       zg.init(p.g, z);
       T f[Q];
       psm_load<S, Q, MODE, GEN>(p, sn, zg, cell, f);
-      if (GEN) psm_collide<T, Q, TRT>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
-      else fluid_collide<T, Q, TRT>(p, f);
+      if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
+      else fluid_collide<T, Q, FL>(p, f);
       if (MODE == MODE_AA_ODD) {
         // rebuild the stencil for the stores rather than keep it live through
         // the collision (register pressure); the empty asm hides the equality
@@ -936,7 +1104,7 @@ __device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return
 // kernel's static shared memory), between 2 and PSM_TMA_MAX_STAGES: deeper
 // pipelines for the narrower storage types keep more bytes in flight.  (The
 // launch refuses a build whose static shared memory exceeds STATIC_SMEM.)
-template <class S, int Q, int MODE>
+template <class S, int Q, int MODE, int FL = 0>
 struct TmaLayout {
   static constexpr bool LOAD_OWN = MODE != MODE_AA_ODD;
   static constexpr bool STORE_TMA = PSM_TMA_STORE && MODE == MODE_AA_EVEN;
@@ -948,7 +1116,7 @@ struct TmaLayout {
   static constexpr int WBOX = r128(Q * 32 * (int)sizeof(S));
   static constexpr int OUT = STORE_TMA ? (PSM_THREADS / 32) * WBOX : 0;
   static constexpr int SM_SMEM = 233472;
-  static constexpr int BLOCKS = step_min_blocks<S, Q>();
+  static constexpr int BLOCKS = step_min_blocks<S, Q, FL>();
   // per block: 1 KB reserved by the hardware and the kernel's static shared
   // memory (about 5 KB: force/torque slots, reduction scratch, the bodies of
   // the step, stage headers), allowed for with 6 KB
@@ -976,11 +1144,11 @@ struct TmaLayout {
 // step every warp writes its 32 cells to shared memory and back with one TMA
 // tensor store.  No block barrier inside the tile loop.
 // ---------------------------------------------------------------------------
-template <class S, int Q, int MODE, int TRT>
-__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
+template <class S, int Q, int MODE, int FL>
+__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
     k_step_tma(const __grid_constant__ StepParams p, const __grid_constant__ TmaMaps maps) {
   using T = typename Store<S>::T;
-  using L = TmaLayout<S, Q, MODE>;
+  using L = TmaLayout<S, Q, MODE, FL>;
   constexpr int NST = L::NST;
   constexpr int NOUT = L::NOUT;
   // refill lag in tiles: a stage is refilled LAG tiles after it was read, so the
@@ -1138,8 +1306,8 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q>())
     int owner = -1;
     bool solid_cell = false;
     double ft[6] = {0, 0, 0, 0, 0, 0};
-    if (GEN) psm_collide<T, Q, TRT>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
-    else fluid_collide<T, Q, TRT>(p, f);
+    if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
+    else fluid_collide<T, Q, FL>(p, f);
     if (L::STORE_TMA) {
       // this warp's output box of tile k; lane 0 issued (and committed) the
       // warp's earlier stores: the one NOUT tiles back must have read it
@@ -1396,77 +1564,90 @@ int persistent_blocks(K kernel, long long work_blocks) {
   return (int)(b < 1 ? 1 : b);
 }
 
-template <class S, int Q, int MODE, int TRT>
+template <class S, int Q, int MODE, int FL>
 cudaError_t launch_step_t(const StepParams& p, cudaStream_t st) {
-  static int blocks = persistent_blocks(k_step<S, Q, MODE, TRT>, 1ll << 40);
+  static int blocks = persistent_blocks(k_step<S, Q, MODE, FL>, 1ll << 40);
   const int grid = (int)(p.t.ntiles < blocks ? p.t.ntiles : blocks);
-  k_step<S, Q, MODE, TRT><<<grid, PSM_THREADS, 0, st>>>(p);
+  k_step<S, Q, MODE, FL><<<grid, PSM_THREADS, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-template <class S, int Q, int MODE, int TRT>
+template <class S, int Q, int MODE, int FL>
 cudaError_t launch_step_tma_t(const StepParams& p, const TmaMaps& m, cudaStream_t st) {
-  using L = TmaLayout<S, Q, MODE>;
+  using L = TmaLayout<S, Q, MODE, FL>;
   // persistent grid: resident blocks per SM (registers and shared memory), at most 8 per SM
   // The stage count assumes at most L::STATIC_SMEM bytes of static shared
   // memory per block; a build that exceeds it refuses to launch rather than
   // silently losing resident blocks.
   static const int blocks = [] {
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, k_step_tma<S, Q, MODE, TRT>) != cudaSuccess ||
+    if (cudaFuncGetAttributes(&fa, k_step_tma<S, Q, MODE, FL>) != cudaSuccess ||
         fa.sharedSizeBytes > (size_t)L::STATIC_SMEM)
       return 0;
-    if (cudaFuncSetAttribute(k_step_tma<S, Q, MODE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) !=
+    if (cudaFuncSetAttribute(k_step_tma<S, Q, MODE, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) !=
         cudaSuccess)
       return 0;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<S, Q, MODE, TRT>, PSM_THREADS, L::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<S, Q, MODE, FL>, PSM_THREADS, L::SMEM);
     if (per_sm > 8) per_sm = 8;
     return sms * per_sm;
   }();
   if (blocks < 1) return cudaErrorInvalidConfiguration;
   const long long grid = p.t.ntiles < blocks ? p.t.ntiles : blocks;
-  k_step_tma<S, Q, MODE, TRT><<<(int)grid, PSM_THREADS, L::SMEM, st>>>(p, m);
+  k_step_tma<S, Q, MODE, FL><<<(int)grid, PSM_THREADS, L::SMEM, st>>>(p, m);
   return cudaGetLastError();
 }
 
-template <class S, int Q>
-cudaError_t launch_step_tma_q(int mode, int trt, const StepParams& p, const TmaMaps& m, cudaStream_t st) {
-  if (mode == MODE_TG)
-    return trt ? launch_step_tma_t<S, Q, MODE_TG, 1>(p, m, st) : launch_step_tma_t<S, Q, MODE_TG, 0>(p, m, st);
-  if (mode == MODE_AA_EVEN)
-    return trt ? launch_step_tma_t<S, Q, MODE_AA_EVEN, 1>(p, m, st) : launch_step_tma_t<S, Q, MODE_AA_EVEN, 0>(p, m, st);
-  return trt ? launch_step_tma_t<S, Q, MODE_AA_ODD, 1>(p, m, st) : launch_step_tma_t<S, Q, MODE_AA_ODD, 0>(p, m, st);
+// fluid operator fl (PSM_BGK, PSM_TRT, PSM_CUMULANT) -> template argument FL;
+// the cumulant kernels exist for D3Q19 only
+template <class S, int Q, int MODE>
+cudaError_t launch_step_tma_m(int fl, const StepParams& p, const TmaMaps& m, cudaStream_t st) {
+  if (fl == PSM_TRT) return launch_step_tma_t<S, Q, MODE, 1>(p, m, st);
+  if (fl == PSM_CUMULANT) {
+    if constexpr (Q == 19) return launch_step_tma_t<S, Q, MODE, 2>(p, m, st);
+    else return cudaErrorNotSupported;
+  }
+  return launch_step_tma_t<S, Q, MODE, 0>(p, m, st);
 }
 
 template <class S, int Q>
-int tma_smem_q(int mode) {
-  if (mode == MODE_TG) return TmaLayout<S, Q, MODE_TG>::SMEM;
-  if (mode == MODE_AA_EVEN) return TmaLayout<S, Q, MODE_AA_EVEN>::SMEM;
-  return TmaLayout<S, Q, MODE_AA_ODD>::SMEM;
+cudaError_t launch_step_tma_q(int mode, int fl, const StepParams& p, const TmaMaps& m, cudaStream_t st) {
+  if (mode == MODE_TG) return launch_step_tma_m<S, Q, MODE_TG>(fl, p, m, st);
+  if (mode == MODE_AA_EVEN) return launch_step_tma_m<S, Q, MODE_AA_EVEN>(fl, p, m, st);
+  return launch_step_tma_m<S, Q, MODE_AA_ODD>(fl, p, m, st);
 }
 
-template <class S, int Q, int MODE, int TRT>
-int step_blocks_t() {
-  static int blocks = persistent_blocks(k_step<S, Q, MODE, TRT>, 1ll << 40);
-  return blocks;
-}
-
-template <class S, int Q>
-cudaError_t launch_step_q(int mode, int trt, const StepParams& p, cudaStream_t st) {
-  if (mode == MODE_TG) return trt ? launch_step_t<S, Q, MODE_TG, 1>(p, st) : launch_step_t<S, Q, MODE_TG, 0>(p, st);
-  if (mode == MODE_AA_EVEN)
-    return trt ? launch_step_t<S, Q, MODE_AA_EVEN, 1>(p, st) : launch_step_t<S, Q, MODE_AA_EVEN, 0>(p, st);
-  return trt ? launch_step_t<S, Q, MODE_AA_ODD, 1>(p, st) : launch_step_t<S, Q, MODE_AA_ODD, 0>(p, st);
+template <class S, int Q, int FL>
+int tma_smem_f(int mode) {
+  if (mode == MODE_TG) return TmaLayout<S, Q, MODE_TG, FL>::SMEM;
+  if (mode == MODE_AA_EVEN) return TmaLayout<S, Q, MODE_AA_EVEN, FL>::SMEM;
+  return TmaLayout<S, Q, MODE_AA_ODD, FL>::SMEM;
 }
 
 template <class S, int Q>
-int step_blocks_q(int mode, int trt) {
-  if (mode == MODE_TG) return trt ? step_blocks_t<S, Q, MODE_TG, 1>() : step_blocks_t<S, Q, MODE_TG, 0>();
-  if (mode == MODE_AA_EVEN) return trt ? step_blocks_t<S, Q, MODE_AA_EVEN, 1>() : step_blocks_t<S, Q, MODE_AA_EVEN, 0>();
-  return trt ? step_blocks_t<S, Q, MODE_AA_ODD, 1>() : step_blocks_t<S, Q, MODE_AA_ODD, 0>();
+int tma_smem_q(int mode, int fl) {
+  if constexpr (Q == 19)
+    if (fl == PSM_CUMULANT) return tma_smem_f<S, Q, 2>(mode);
+  return tma_smem_f<S, Q, 0>(mode);
+}
+
+template <class S, int Q, int MODE>
+cudaError_t launch_step_m(int fl, const StepParams& p, cudaStream_t st) {
+  if (fl == PSM_TRT) return launch_step_t<S, Q, MODE, 1>(p, st);
+  if (fl == PSM_CUMULANT) {
+    if constexpr (Q == 19) return launch_step_t<S, Q, MODE, 2>(p, st);
+    else return cudaErrorNotSupported;
+  }
+  return launch_step_t<S, Q, MODE, 0>(p, st);
+}
+
+template <class S, int Q>
+cudaError_t launch_step_q(int mode, int fl, const StepParams& p, cudaStream_t st) {
+  if (mode == MODE_TG) return launch_step_m<S, Q, MODE_TG>(fl, p, st);
+  if (mode == MODE_AA_EVEN) return launch_step_m<S, Q, MODE_AA_EVEN>(fl, p, st);
+  return launch_step_m<S, Q, MODE_AA_ODD>(fl, p, st);
 }
 
 inline long long io_cells(const IoParams& p) { return (long long)p.g.nx * p.g.ny * (p.z_end - p.z_begin); }
@@ -1481,18 +1662,15 @@ inline int io_grid(const IoParams& p) {
 // One translation unit per storage precision defines its launchers with this.
 #define PSM_DEFINE_STORAGE(NAME, S)                                                                     \
   namespace psm {                                                                                       \
-  cudaError_t launch_step_##NAME(int Q, int mode, int trt, const StepParams& p, cudaStream_t st) {      \
-    return Q == 19 ? launch_step_q<S, 19>(mode, trt, p, st) : launch_step_q<S, 27>(mode, trt, p, st);   \
+  cudaError_t launch_step_##NAME(int Q, int mode, int fl, const StepParams& p, cudaStream_t st) {       \
+    return Q == 19 ? launch_step_q<S, 19>(mode, fl, p, st) : launch_step_q<S, 27>(mode, fl, p, st);     \
   }                                                                                                     \
-  cudaError_t launch_step_tma_##NAME(int Q, int mode, int trt, const StepParams& p, const TmaMaps& m,   \
+  cudaError_t launch_step_tma_##NAME(int Q, int mode, int fl, const StepParams& p, const TmaMaps& m,    \
                                      cudaStream_t st) {                                                 \
-    return Q == 19 ? launch_step_tma_q<S, 19>(mode, trt, p, m, st) : launch_step_tma_q<S, 27>(mode, trt, p, m, st); \
+    return Q == 19 ? launch_step_tma_q<S, 19>(mode, fl, p, m, st) : launch_step_tma_q<S, 27>(mode, fl, p, m, st); \
   }                                                                                                     \
-  int tma_smem_bytes_##NAME(int Q, int mode) {                                                          \
-    return Q == 19 ? tma_smem_q<S, 19>(mode) : tma_smem_q<S, 27>(mode);                                 \
-  }                                                                                                     \
-  int step_grid_blocks_##NAME(int Q, int mode, int trt) {                                               \
-    return Q == 19 ? step_blocks_q<S, 19>(mode, trt) : step_blocks_q<S, 27>(mode, trt);                 \
+  int tma_smem_bytes_##NAME(int Q, int mode, int fl) {                                                  \
+    return Q == 19 ? tma_smem_q<S, 19>(mode, fl) : tma_smem_q<S, 27>(mode, fl);                         \
   }                                                                                                     \
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st) {                         \
     if (Q == 19) k_import<S, 19><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                                \

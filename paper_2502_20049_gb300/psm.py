@@ -32,7 +32,7 @@ ERRORS = {-1: "PSM_ERR_ARG", -2: "PSM_ERR_CUDA", -3: "PSM_ERR_OOM", -4: "PSM_ERR
 PSM_MAX_BODIES = 4
 STORAGE = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 STREAMING = {"aa": 0, "twogrid": 1}
-FLUID = {"bgk": 0, "trt": 1}
+FLUID = {"bgk": 0, "trt": 1, "cumulant": 2}
 STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
 
 
@@ -53,7 +53,7 @@ class Lattice(ctypes.Structure):
 
 class Collision(ctypes.Structure):
     _fields_ = [("fluid", ctypes.c_int), ("tau", ctypes.c_double), ("trt_lambda", ctypes.c_double),
-                ("solid", ctypes.c_int), ("weighting", ctypes.c_int)]
+                ("solid", ctypes.c_int), ("weighting", ctypes.c_int), ("cum_omega", ctypes.c_double * 3)]
 
 
 class GeomField(ctypes.Structure):
@@ -269,6 +269,7 @@ class SolverConfig:
     solid: int = 1
     weighting: int = 1
     bc_z: int = 1
+    cum_rates: tuple = (1.0, 1.0, 1.0)  # cumulant: bulk, third-order, fourth-order rates
     rho0: float = 1.0
     u_in: tuple = (0.0, 0.0, 0.0)
 
@@ -284,7 +285,8 @@ class Solver:
         self.cfg = cfg
         grid = Grid(cfg.nx, cfg.ny, cfg.nz, cfg.bc_z, cfg.rho0, (ctypes.c_double * 3)(*cfg.u_in))
         lat = Lattice(cfg.Q, STREAMING[cfg.streaming], STORAGE[cfg.storage])
-        col = Collision(FLUID[cfg.fluid], cfg.tau, cfg.trt_lambda, cfg.solid, cfg.weighting)
+        col = Collision(FLUID[cfg.fluid], cfg.tau, cfg.trt_lambda, cfg.solid, cfg.weighting,
+                        (ctypes.c_double * 3)(*cfg.cum_rates))
         self._h = ctypes.c_void_p()
         self.stream = current_stream() if stream is None else stream
         self._buffers = buffers
@@ -303,7 +305,8 @@ class Solver:
     def from_case(cls, case: "W.Case", stream: int | None = None, init: bool = True) -> "Solver":
         cfg = SolverConfig(case.nx, case.ny, case.nz, Q=case.Q, streaming=case.streaming, storage=case.storage,
                            fluid=case.fluid, tau=case.tau, trt_lambda=case.trt_lambda, solid=case.solid,
-                           weighting=case.weighting, bc_z=case.bc_z, rho0=case.rho0, u_in=tuple(case.u_in))
+                           weighting=case.weighting, bc_z=case.bc_z, rho0=case.rho0, u_in=tuple(case.u_in),
+                           cum_rates=tuple(case.cum_rates))
         s = cls(cfg, stream=stream)
         for bi, b in enumerate(case.bodies):
             g = voxelize(b.kind, b.params, b.s)

@@ -95,6 +95,19 @@ def test_create_rejects_bad_arguments(psm, bad):
         pass  # an unknown enum name never reaches the library
 
 
+@pytest.mark.parametrize("bad,code", [(dict(fluid="cumulant", Q=27), -6), (dict(fluid="cumulant", cum_rates=(2.0, 1.0, 1.0)), -1),
+                                      (dict(fluid="cumulant", cum_rates=(1.0, -0.5, 1.0)), -1),
+                                      (dict(fluid="cumulant", cum_rates=(1.0, 1.0, float("nan"))), -1)])
+def test_create_rejects_bad_cumulant(psm, bad, code):
+    """The cumulant operator is D3Q19 only (PSM_ERR_UNSUPPORTED for D3Q27) and
+    its rates lie in (0, 2) (0 selects 1); both fail before any CUDA call."""
+    kw = dict(nx=8, ny=8, nz=8)
+    kw.update(bad)
+    with pytest.raises(psm.PSMError) as ei:
+        psm.Solver(psm.SolverConfig(**kw), stream=0)
+    assert ei.value.code == code
+
+
 def test_voxeliser_rejects_bad_arguments(psm):
     with pytest.raises(psm.PSMError) as ei:
         psm.voxelize(W.SPHERE, (-1.0,), 2)
