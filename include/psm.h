@@ -73,8 +73,8 @@ extern "C" {
 /* psm_collision.fluid */
 #define PSM_BGK 0 /* single relaxation time, Eq. 2 */
 #define PSM_TRT 1 /* two relaxation times: omega+ = 1/tau, Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) */
-/* Cumulant operator (Geier et al. 2015; the paper's Sec. 2.2 names it as the
- * operator of its performance runs), D3Q19 only: central moments of the 19
+/* Cumulant operator (Geier et al. 2015; listed in the paper's Sec. 2.2, the
+ * operator of every performance run in Sec. 5.1), D3Q19 only: central moments of the 19
  * exponent triples (a, b, c) in {0,1,2}^3 with at most two non-zero;
  * cumulants (order <= 3: the central moments; order 4:
  * C_220 = k_220 - (k_200 k_020 + 2 k_110^2) / rho and permutations) relaxed

@@ -14,7 +14,7 @@ What each function follows (sections and equations of the paper):
   typo: with it the zeroth moment is not rho).
 * :func:`weighting` -- Eq. 5 (``mode=0``) and Eq. 6 (``mode=1``).
 * :class:`Sim` -- one step = remap (Sec. 3) -> Eq. 4 with Eq. 2 / TRT / the
-  cumulant operator the paper cites in Sec. 2.2 (D3Q19) and the solid
+  cumulant operator of Sec. 2.2 / Sec. 5.1 (D3Q19) and the solid
   collision Eq. 7 / 8 / 9 -> force and torque Eq. 10 / 11 -> streaming Eq. 1.
 * :func:`voxelize`, :func:`remap` -- the super-sampled geometry field and its
   per-step interpolation onto the lattice (Sec. 3).

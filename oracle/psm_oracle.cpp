@@ -115,9 +115,9 @@ T weighting(int mode, T eps, double tau) {
 }
 
 // ---------------------------------------------------------------------------
-// Cumulant collision on D3Q19.  The paper runs every performance case with
-// the cumulant operator of Geier et al. (2015), which it cites in Sec. 2.2
-// without restating it.  Its definition, restricted to the 19 moments a D3Q19
+// Cumulant collision on D3Q19.  The paper runs every performance case of
+// Sec. 5.1 with the cumulant operator of Geier et al. (2015), which Sec. 2.2
+// lists without restating it.  Its definition, restricted to the 19 moments a D3Q19
 // velocity set resolves:
 //   * central moments (rho-weighted) k_abc = sum_i f_i (c_ix - u_x)^a
 //     (c_iy - u_y)^b (c_iz - u_z)^c for the 19 exponent triples with

@@ -470,8 +470,8 @@ __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drh
   }
 }
 
-// Cumulant collision of one D3Q19 cell (the operator the paper names in
-// Sec. 2.2 for its performance runs: Geier et al. 2015), restricted to the 19
+// Cumulant collision of one D3Q19 cell (Geier et al. 2015: listed in Sec. 2.2,
+// the operator of every performance run in Sec. 5.1), restricted to the 19
 // moments D3Q19 resolves, from the shifted PDFs f (f - w rho0), in place.
 //   raw moments of the shifted PDFs, plane by plane (D3Q19 has no corner
 //     directions, so the x-y face diagonals alone carry c_x^2 c_y^2, c_x^2 c_y,

@@ -1,5 +1,5 @@
-"""GPU parity of the PSM step with the cumulant fluid operator (D3Q19; the
-operator the paper names in Sec. 2.2 for its performance runs) against the
+"""GPU parity of the PSM step with the cumulant fluid operator (D3Q19; listed
+in Sec. 2.2, the operator of every performance run in Sec. 5.1) against the
 FP64 CPU oracle, through the C ABI.
 
 Tolerances as for BGK/TRT (velocity: max |u_gpu - u_oracle| / |u_in|):

@@ -1,5 +1,5 @@
-"""Pins of the oracle's cumulant collision on D3Q19 (the operator the paper
-cites in Sec. 2.2 for all its performance runs, Geier et al. 2015).
+"""Pins of the oracle's cumulant collision on D3Q19 (Geier et al. 2015: listed
+in Sec. 2.2, the operator of every performance run in Sec. 5.1).
 
 The oracle computes central moments, cumulants, relaxes them and solves a
 linear system back to PDFs.  These tests check its output against facts that
