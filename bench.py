@@ -282,6 +282,10 @@ def run_ours(args):
     G.build()
     from paper_2502_20049_gb300 import psm
 
+    if args.adjoint_only:
+        # the adjoint workload alone (for profiling the backward kernels)
+        print(json.dumps({"adjoint": adjoint_cost(torch.cuda.current_stream())}), flush=True)
+        return
     case, desc = workload(args.workload, args.streaming, args.fluid)
     if args.storage:
         case = case.with_(storage=args.storage)
@@ -384,6 +388,7 @@ def main():
                     help="fluid operator (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the variant and adjoint measurements")
+    ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint cost measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

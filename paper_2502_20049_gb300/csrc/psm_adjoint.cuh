@@ -177,6 +177,10 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
       sn.init(p.g, x, y, z, cell);
       ZGhost zg;
       zg.init(p.g, z);
+      // the gradient accumulator is read with the PDFs and the adjoint field, so
+      // that its read-modify-write at the end does not add a second memory round
+      // trip (each cell belongs to one thread of the launch)
+      const double g_old = grad[cell];
       T f[Q], mu[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
         const T bb = adj_fluid_cell<T, Q>(C, p.solid, inv_tau, f, mu, lam);
 #pragma unroll
         for (int i = 0; i < Q; ++i) static_cast<T*>(p.lout_slot[i])[cell] = lam[i];
-        grad[cell] += (double)(bb * Bp0);
+        grad[cell] = g_old + (double)(bb * Bp0);
       } else {
       // ---- forward recomputation (same arithmetic as psm_collide) ----
       float epsf = 0.0f;
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
           has_u = true;
         }
       }
-      grad[cell] += (double)(Bbar * Bp);
+      grad[cell] = g_old + (double)(Bbar * Bp);
       if (GEN && owner >= 0) {
         // u_s = omega x r + v  =>  d/d omega = r x usbar
         const double a = (double)usbx, b = (double)usby, c = (double)usbz;

@@ -562,9 +562,11 @@ void fill_consts(const psm_solver* h, psm::ConstT<T>& c) {
   c.hm1 = (T)(0.5 * (1.0 - omm));
   // cumulant: 1 - rate for the shear, bulk, third- and fourth-order families
   c.cum1[0] = (T)(1.0 - 1.0 / h->col.tau);
+  c.cum_unit = 1;
   for (int k = 0; k < 3; ++k) {
     const double w = h->col.cum_omega[k] == 0.0 ? 1.0 : h->col.cum_omega[k];
     c.cum1[k + 1] = (T)(1.0 - w);
+    if (w != 1.0) c.cum_unit = 0;
   }
   // weight per class |c|^2 = 0..3 (D3Q19 has no corner directions)
   const double w19[4] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0, 0.0};

@@ -87,6 +87,7 @@ struct ConstT {
   T pk[4];        // 4.5 omega+ w_c
   T pd[4];        // 3 omega- w_c
   T cum1[4];      // cumulant: 1 - omega for shear (1/tau), bulk, third order, fourth order
+  int cum_unit;   // cumulant: bulk, third- and fourth-order rates all 1
 };
 
 struct StepParams {

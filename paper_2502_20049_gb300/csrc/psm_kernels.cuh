@@ -438,14 +438,15 @@ __device__ __forceinline__ T c_dot(int i, T ux, T uy, T uz) {
 // The products of omega+-, the weight and the numeric factors are host
 // constants per weight class (ConstT pw, pk, pd); f_i and f_j are not needed
 // once s and d are formed.
-template <class T>
+template <class T, bool UNIT>
 __device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T drho, T rho, T ux, T uy, T uz);
 
 template <class T, int Q, int FL>
 __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drho, T rho, T ux, T uy, T uz, T uu) {
   if constexpr (FL == 2) {
     static_assert(Q == 19, "the cumulant operator is defined for D3Q19");
-    cumulant_relax<T>(C, f, drho, rho, ux, uy, uz);
+    if (C.cum_unit) cumulant_relax<T, true>(C, f, drho, rho, ux, uy, uz);
+    else cumulant_relax<T, false>(C, f, drho, rho, ux, uy, uz);
     return;
   }
   const T base = r_fma(T(-1.5), r_mul(rho, uu), drho);
@@ -483,13 +484,15 @@ __device__ __forceinline__ void fluid_relax(const ConstT<T>& C, T (&f)[Q], T drh
 //   relaxation: off-diagonal and deviatoric second order with 1 - 1/tau, the
 //     trace with 1 - omega_bulk, third order with 1 - omega_3, the fourth-order
 //     cumulants C_220 = k_220 - (k_200 k_020 + 2 k_110^2) / rho with
-//     1 - omega_4 (host constants cum1[0..3]);
+//     1 - omega_4 (host constants cum1[0..3]); with the default rates (bulk,
+//     third and fourth order 1, UNIT) the trace, third- and fourth-order
+//     cumulants are set to equilibrium without computing them;
 //   raw moments of the result by the inverse shift, then the D3Q19 PDFs in
 //     closed form: f(sx, sy, 0) = (m_220 + sx m_120 + sy m_210 + sx sy m_110) / 4,
 //     f(s, 0, 0) = ((m_200 - m_220 - m_202) + s (m_100 - m_120 - m_102)) / 2,
 //     f_0 = m_000 - m_200 - m_020 - m_002 + m_220 + m_202 + m_022.
 // Operations are separately rounded (same bits in every kernel that inlines it).
-template <class T>
+template <class T, bool UNIT>
 __device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T drho, T rho, T ux, T uy, T uz) {
   auto ad = [](T a, T b) { return r_add(a, b); };
   auto sb = [](T a, T b) { return r_sub(a, b); };
@@ -524,60 +527,88 @@ __device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T
   const T k110 = sb(Mxy, ml(rux, uy)), k101 = sb(Mxz, ml(rux, uz)), k011 = sb(Myz, ml(ruy, uz));
   const T r0t = ml(C.rho0, third);
   const T M200 = ad(m200, r0t), M020 = ad(m020, r0t), M002 = ad(m002, r0t);  // full raw c_a^2 moments
-  const T n2ux = ml(T(-2), ux), n2uy = ml(T(-2), uy), n2uz = ml(T(-2), uz);
-  // k_aab = m_aab - u_b M_aa - 2 u_a k_ab
-  const T k210 = fm(n2ux, k110, fm(-uy, M200, Yxy)), k120 = fm(n2uy, k110, fm(-ux, M020, Xxy));
-  const T k201 = fm(n2ux, k101, fm(-uz, M200, Zxz)), k102 = fm(n2uz, k101, fm(-ux, M002, Xxz));
-  const T k021 = fm(n2uy, k011, fm(-uz, M020, Zyz)), k012 = fm(n2uz, k011, fm(-uy, M002, Yyz));
   const T uxx = ml(ux, ux), uyy = ml(uy, uy), uzz = ml(uz, uz);
-  // k^_aabb = (m_aabb - drho/9) - 2 u_b k_aab - 2 u_a k_abb - 4 u_a u_b k_ab - u_b^2 k^_aa
-  //           - u_a^2 k^_bb - rho (u_a^2 + u_b^2) / 3 - rho u_a^2 u_b^2
-  auto k4 = [&](T S, T kaab, T kabb, T ua, T ub, T uaa, T ubb, T kab, T kaa, T kbb) {
-    T r = sb(S, dn);
-    r = fm(ml(T(-2), ub), kaab, r);
-    r = fm(ml(T(-2), ua), kabb, r);
-    r = fm(ml(T(-4), ml(ua, ub)), kab, r);
-    r = fm(-ubb, kaa, r);
-    r = fm(-uaa, kbb, r);
-    r = fm(-ml(rho, third), ad(uaa, ubb), r);
-    return fm(-ml(rho, uaa), ubb, r);
-  };
-  const T k220 = k4(Sxy, k210, k120, ux, uy, uxx, uyy, k110, k200, k020);
-  const T k202 = k4(Sxz, k201, k102, ux, uz, uxx, uzz, k101, k200, k002);
-  const T k022 = k4(Syz, k021, k012, uy, uz, uyy, uzz, k011, k020, k002);
-  // ---- relaxation ----
-  const T s1 = C.cum1[0], b1 = C.cum1[1], t1 = C.cum1[2], q1 = C.cum1[3];
+  const T s1 = C.cum1[0];
   const T inv_rho = recip(rho);
-  const T d1 = ml(s1, sb(k200, k020)), d2 = ml(s1, sb(k200, k002)), tr = ml(b1, ad(ad(k200, k020), k002));
-  const T p200 = ml(ad(ad(tr, d1), d2), third);
-  const T p020 = ml(ad(fm(T(-2), d1, tr), d2), third);
-  const T p002 = ml(fm(T(-2), d2, ad(tr, d1)), third);
   const T p110 = ml(s1, k110), p101 = ml(s1, k101), p011 = ml(s1, k011);
-  const T p210 = ml(t1, k210), p120 = ml(t1, k120), p201 = ml(t1, k201);
-  const T p102 = ml(t1, k102), p021 = ml(t1, k021), p012 = ml(t1, k012);
-  // fourth order: C = k^_aabb - (k^_aa + k^_bb)/3 - (k^_aa k^_bb + 2 k_ab^2)/rho, relaxed, and back
-  auto c4 = [&](T k, T kaa, T kbb, T kab, T paa, T pbb, T pab) {
-    const T c = sb(fm(-third, ad(kaa, kbb), k), ml(fm(kaa, kbb, ml(ml(T(2), kab), kab)), inv_rho));
-    return fm(third, ad(paa, pbb), ad(ml(q1, c), ml(fm(paa, pbb, ml(ml(T(2), pab), pab)), inv_rho)));
+  const T d1 = ml(s1, sb(k200, k020)), d2 = ml(s1, sb(k200, k002));
+  // relaxed second-order (deviatoric with 1 - 1/tau, trace with 1 - omega_bulk),
+  // third-order (k_aab) and fourth-order (k^_aabb) central moments
+  T p200, p020, p002, p210 = T(0), p120 = T(0), p201 = T(0), p102 = T(0), p021 = T(0), p012 = T(0);
+  T p220, p202, p022;
+  // k^_aabb of a Gaussian-like closure: (p_aa + p_bb)/3 + (p_aa p_bb + 2 p_ab^2)/rho
+  auto closure = [&](T paa, T pbb, T pab) {
+    return fm(third, ad(paa, pbb), ml(fm(paa, pbb, ml(ml(T(2), pab), pab)), inv_rho));
   };
-  const T p220 = c4(k220, k200, k020, k110, p200, p020, p110);
-  const T p202 = c4(k202, k200, k002, k101, p200, p002, p101);
-  const T p022 = c4(k022, k020, k002, k011, p020, p002, p011);
+  if constexpr (UNIT) {
+    // bulk, third- and fourth-order rates 1: trace, third-order and fourth-order
+    // cumulants take their equilibrium values (0 in deviation form)
+    p200 = ml(ad(d1, d2), third);
+    p020 = ml(fm(T(-2), d1, d2), third);
+    p002 = ml(fm(T(-2), d2, d1), third);
+    p220 = closure(p200, p020, p110);
+    p202 = closure(p200, p002, p101);
+    p022 = closure(p020, p002, p011);
+  } else {
+    const T b1 = C.cum1[1], t1 = C.cum1[2], q1 = C.cum1[3];
+    const T r0t = ml(C.rho0, third);
+    const T M200 = ad(m200, r0t), M020 = ad(m020, r0t), M002 = ad(m002, r0t);  // full raw c_a^2 moments
+    const T n2ux = ml(T(-2), ux), n2uy = ml(T(-2), uy), n2uz = ml(T(-2), uz);
+    // k_aab = m_aab - u_b M_aa - 2 u_a k_ab
+    const T k210 = fm(n2ux, k110, fm(-uy, M200, Yxy)), k120 = fm(n2uy, k110, fm(-ux, M020, Xxy));
+    const T k201 = fm(n2ux, k101, fm(-uz, M200, Zxz)), k102 = fm(n2uz, k101, fm(-ux, M002, Xxz));
+    const T k021 = fm(n2uy, k011, fm(-uz, M020, Zyz)), k012 = fm(n2uz, k011, fm(-uy, M002, Yyz));
+    // k^_aabb = (m_aabb - drho/9) - 2 u_b k_aab - 2 u_a k_abb - 4 u_a u_b k_ab - u_b^2 k^_aa
+    //           - u_a^2 k^_bb - rho (u_a^2 + u_b^2) / 3 - rho u_a^2 u_b^2
+    auto k4 = [&](T S, T kaab, T kabb, T ua, T ub, T uaa, T ubb, T kab, T kaa, T kbb) {
+      T r = sb(S, dn);
+      r = fm(ml(T(-2), ub), kaab, r);
+      r = fm(ml(T(-2), ua), kabb, r);
+      r = fm(ml(T(-4), ml(ua, ub)), kab, r);
+      r = fm(-ubb, kaa, r);
+      r = fm(-uaa, kbb, r);
+      r = fm(-ml(rho, third), ad(uaa, ubb), r);
+      return fm(-ml(rho, uaa), ubb, r);
+    };
+    const T k220 = k4(Sxy, k210, k120, ux, uy, uxx, uyy, k110, k200, k020);
+    const T k202 = k4(Sxz, k201, k102, ux, uz, uxx, uzz, k101, k200, k002);
+    const T k022 = k4(Syz, k021, k012, uy, uz, uyy, uzz, k011, k020, k002);
+    const T tr = ml(b1, ad(ad(k200, k020), k002));
+    p200 = ml(ad(ad(tr, d1), d2), third);
+    p020 = ml(ad(fm(T(-2), d1, tr), d2), third);
+    p002 = ml(fm(T(-2), d2, ad(tr, d1)), third);
+    p210 = ml(t1, k210), p120 = ml(t1, k120), p201 = ml(t1, k201);
+    p102 = ml(t1, k102), p021 = ml(t1, k021), p012 = ml(t1, k012);
+    // fourth order: C = k^_aabb - closure(k), relaxed with 1 - omega_4, plus closure(p)
+    auto c4 = [&](T k, T kaa, T kbb, T kab) {
+      return sb(fm(-third, ad(kaa, kbb), k), ml(fm(kaa, kbb, ml(ml(T(2), kab), kab)), inv_rho));
+    };
+    p220 = fm(q1, c4(k220, k200, k020, k110), closure(p200, p020, p110));
+    p202 = fm(q1, c4(k202, k200, k002, k101), closure(p200, p002, p101));
+    p022 = fm(q1, c4(k022, k020, k002, k011), closure(p020, p002, p011));
+  }
   // ---- raw moments of the result (shifted PDFs) ----
   const T n200 = fm(rux, ux, ad(p200, dt)), n020 = fm(ruy, uy, ad(p020, dt)), n002 = fm(ruz, uz, ad(p002, dt));
   const T n110 = fm(rux, uy, p110), n101 = fm(rux, uz, p101), n011 = fm(ruy, uz, p011);
   const T rt = ml(rho, third);
   const T F200 = fm(rux, ux, ad(p200, rt)), F020 = fm(ruy, uy, ad(p020, rt)), F002 = fm(ruz, uz, ad(p002, rt));
   const T n2 = T(2);
-  const T n210 = fm(ml(n2, ux), p110, fm(uy, F200, p210)), n120 = fm(ml(n2, uy), p110, fm(ux, F020, p120));
-  const T n201 = fm(ml(n2, ux), p101, fm(uz, F200, p201)), n102 = fm(ml(n2, uz), p101, fm(ux, F002, p102));
-  const T n021 = fm(ml(n2, uy), p011, fm(uz, F020, p021)), n012 = fm(ml(n2, uz), p011, fm(uy, F002, p012));
+  // m_aab = k_aab + u_b F_aa + 2 u_a k_ab
+  auto b3 = [&](T paab, T ub, T Faa, T ua, T pab) {
+    if constexpr (UNIT) return fm(ml(n2, ua), pab, ml(ub, Faa));
+    else return fm(ml(n2, ua), pab, fm(ub, Faa, paab));
+  };
+  const T n210 = b3(p210, uy, F200, ux, p110), n120 = b3(p120, ux, F020, uy, p110);
+  const T n201 = b3(p201, uz, F200, ux, p101), n102 = b3(p102, ux, F002, uz, p101);
+  const T n021 = b3(p021, uz, F020, uy, p011), n012 = b3(p012, uy, F002, uz, p011);
   // m_aabb = k^_aabb + drho/9 + 2 u_b k_aab + 2 u_a k_abb + 4 u_a u_b k_ab + u_b^2 (k^_aa + rho/3)
   //          + u_a^2 (k^_bb + rho/3) + rho u_a^2 u_b^2
   auto b4 = [&](T k, T kaab, T kabb, T ua, T ub, T uaa, T ubb, T kab, T kaa, T kbb) {
     T r = ad(k, dn);
-    r = fm(ml(n2, ub), kaab, r);
-    r = fm(ml(n2, ua), kabb, r);
+    if constexpr (!UNIT) {
+      r = fm(ml(n2, ub), kaab, r);
+      r = fm(ml(n2, ua), kabb, r);
+    }
     r = fm(ml(T(4), ml(ua, ub)), kab, r);
     r = fm(ubb, ad(kaa, rt), r);
     r = fm(uaa, ad(kbb, rt), r);
