@@ -132,3 +132,13 @@ def test_c5_full_1e9_fp16_aa():
     worst, ns, n = check_one_step(case, 11)
     print(f"1024x1024x960 FP16 AA: {ns} cells, step {n}: max |df| {worst:.2e}")
     assert worst <= TOL["fp16"]
+
+
+@pytest.mark.parametrize("storage,streaming,steps_before", [("fp32", "twogrid", 37), ("fp16", "twogrid", 37),
+                                                            ("fp16", "aa", 21)])
+def test_c2_full_256_cumulant(storage, streaming, steps_before):
+    """The cumulant variants bench.py times (256^3, default rates)."""
+    case = W.c2_ellipsoid().with_(streaming=streaming, storage=storage, fluid="cumulant")
+    worst, ns, n = check_one_step(case, steps_before)
+    print(f"256^3 cumulant {storage} {streaming}: {ns} cells, step {n}: max |df| {worst:.2e}")
+    assert worst <= TOL[storage]
