@@ -126,7 +126,10 @@ struct psm_solver {
   bool tma_ok = false;
   bool tma_odd_ok = false;  // the AA odd step has its TMA variant too (full 256-cell rows)
   int variant = PSM_KERNEL_AUTO;
-  psm::Tiling tma_tiling;
+  psm::Tiling tma_tiling;      // the solver's two-grid or AA even steps
+  psm::Tiling tma_tiling_odd;  // AA odd steps (one cell per thread)
+  psm::Tiling tma_tiling_tg;   // two-grid steps of the backward recompute
+  bool tma_tg_ok = false;      // the backward recompute has its TMA variant
   BufMaps maps[2];
   // trajectory recording for psm_backward: checkpoints every rec_K steps from rec_n0
   bool recording = false;
@@ -476,24 +479,34 @@ bool valid_handle(psm_handle h) { return h != nullptr; }
 // 256 % nx == 0 if nx < 256, TY = 256 / TX divides ny, rows of 16-byte
 // multiples, at least 32 cells per row segment, and the staging buffers of
 // the modes used fit the shared memory a block may have.
-bool tma_shape(const psm_solver* h, psm::Tiling& t) {
+// Tiling of the TMA step kernel in `mode`: tiles of TX = min(nx, 256) cells
+// of TY rows, TX TY = 256 times the kernel's cells per thread.  false where
+// the shape does not allow it.
+bool tma_tiling_for(const psm_solver* h, int mode, psm::Tiling& t) {
   const int64_t nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
   const int64_t b = (int64_t)storage_bytes(h->lat.storage);
   const int64_t TX = nx >= 256 ? 256 : nx;
   if (TX < 32 || nx % TX != 0 || (nx < 256 && 256 % nx != 0)) return false;
-  const int64_t TY = 256 / TX;
+  const int64_t TY = (256 / TX) * psm::tma_cells_per_thread((int)b, mode, h->Q, h->col.fluid);
   if (ny % TY != 0 || (TX * b) % 16 != 0 || (nx * b) % 16 != 0) return false;
+  t.tx = (int)TX;
+  t.ty = (int)TY;
+  t.ntx = (int)(nx / TX);
+  t.nty = (int)(ny / TY);
+  t.ntiles = (long long)t.ntx * t.nty * nz;
+  return true;
+}
+
+bool tma_shape(const psm_solver* h, psm::Tiling& t, psm::Tiling& t_odd) {
+  const int own_mode = h->lat.streaming == PSM_STREAM_TWO_GRID ? psm::MODE_TG : psm::MODE_AA_EVEN;
+  if (!tma_tiling_for(h, own_mode, t)) return false;
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
   const int mode = h->lat.streaming == PSM_STREAM_TWO_GRID ? psm::MODE_TG : psm::MODE_AA_EVEN;
   if (psm::tma_smem_bytes(h->lat.storage, h->Q, mode, h->col.fluid) > optin) return false;
-  t.tx = (int)TX;
-  t.ty = (int)TY;
-  t.ntx = (int)(nx / TX);
-  t.nty = (int)(ny / TY);
-  t.ntiles = (long long)t.ntx * t.nty * nz;
+  if (!tma_tiling_for(h, psm::MODE_AA_ODD, t_odd)) return false;
   return true;
 }
 
@@ -511,7 +524,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tensor maps of PDF buffer `buf` as a (x, y, z, slot) tensor.
-bool encode_maps(const psm_solver* h, void* buf, BufMaps& m) {
+bool encode_maps(const psm_solver* h, void* buf, BufMaps& m, const psm::Tiling& tiling) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   CUtensorMapDataType dt = h->lat.storage == PSM_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -523,8 +536,8 @@ bool encode_maps(const psm_solver* h, void* buf, BufMaps& m) {
                               (cuuint64_t)h->Q};
   const cuuint64_t strides[3] = {dims[0] * b, dims[0] * dims[1] * b, dims[0] * dims[1] * dims[2] * b};
   const cuuint32_t elem[4] = {1, 1, 1, 1};
-  const cuuint32_t box_q[4] = {(cuuint32_t)h->tma_tiling.tx, (cuuint32_t)h->tma_tiling.ty, 1, (cuuint32_t)h->Q};
-  const cuuint32_t box_1[4] = {(cuuint32_t)h->tma_tiling.tx, 1, 1, 1};
+  const cuuint32_t box_q[4] = {(cuuint32_t)tiling.tx, (cuuint32_t)tiling.ty, 1, (cuuint32_t)h->Q};
+  const cuuint32_t box_1[4] = {(cuuint32_t)tiling.tx, 1, 1, 1};
   CUresult r1 = enc(&m.tile, dt, 4, buf, dims, strides, box_q, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   CUresult r2 = enc(&m.row1, dt, 4, buf, dims, strides, box_1, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -586,6 +599,7 @@ int check_err(psm_solver* h) {
   if (e != cudaSuccess) return cuda_fail(e, "error-flag read");
   if (flag) {
     cudaMemset(h->d_err, 0, sizeof(int));
+    if (flag == 2) return fail(PSM_ERR_CUDA, "a step kernel was launched with a tiling it was not built for (results invalid)");
     return fail(PSM_ERR_CUDA, "a step kernel timed out waiting for its staged loads (results invalid)");
   }
   return PSM_OK;
@@ -732,14 +746,16 @@ int create_impl(const psm_grid* grid, const psm_lattice* lattice, const psm_coll
   e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "scratch initialisation"));
   // the TMA-staged kernel where the shape allows it
-  if (tma_shape(h, h->tma_tiling)) {
+  if (tma_shape(h, h->tma_tiling, h->tma_tiling_odd)) {
     h->tma_ok = true;
-    for (int b = 0; b < nbuf; ++b) h->tma_ok = h->tma_ok && encode_maps(h, h->buf[b], h->maps[b]);
+    for (int b = 0; b < nbuf; ++b) h->tma_ok = h->tma_ok && encode_maps(h, h->buf[b], h->maps[b], h->tma_tiling);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     h->tma_odd_ok = h->tma_ok && h->tma_tiling.tx == psm::PSM_THREADS &&
                     psm::tma_smem_bytes(h->lat.storage, h->Q, psm::MODE_AA_ODD, h->col.fluid) <= optin;
+    h->tma_tg_ok = h->tma_ok && tma_tiling_for(h, psm::MODE_TG, h->tma_tiling_tg) &&
+                   psm::tma_smem_bytes(h->lat.storage, h->Q, psm::MODE_TG, h->col.fluid) <= optin;
   }
   e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), h->stream);
   if (e == cudaSuccess)
@@ -1137,7 +1153,7 @@ int psm_step(psm_handle h, int n) {
     // the AA odd step runs with plain loads unless its TMA variant applies
     const bool tma_now = use_tma && (mode != psm::MODE_AA_ODD ||
                                      (h->tma_odd_ok && (h->variant == PSM_KERNEL_TMA || !PSM_AA_ODD_PLAIN)));
-    p.t = tma_now ? h->tma_tiling : h->tiling;
+    p.t = !tma_now ? h->tiling : (mode == psm::MODE_AA_ODD ? h->tma_tiling_odd : h->tma_tiling);
     psm::TmaMaps tm;
     if (tma_now) {
       const int dsti = h->lat.streaming == PSM_STREAM_TWO_GRID ? (src ^ 1) : 0;
@@ -1186,7 +1202,7 @@ int ensure_backward_buffers(psm_solver* h, int K) {
     h->rec_maps.assign((size_t)K, BufMaps{});
     for (int k = 1; k < K && e == cudaSuccess; ++k) {
       e = cudaMalloc(&h->rec_slots[k], state_bytes(h));
-      if (e == cudaSuccess && h->tma_ok && !encode_maps(h, h->rec_slots[k], h->rec_maps[k]))
+      if (e == cudaSuccess && h->tma_tg_ok && !encode_maps(h, h->rec_slots[k], h->rec_maps[k], h->tma_tiling_tg))
         e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) {
@@ -1257,7 +1273,7 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   }
   std::vector<void*> slots(h->rec_slots);
   std::vector<BufMaps> smaps(h->rec_maps);
-  const bool tma_rec = h->tma_ok && h->variant != PSM_KERNEL_PLAIN;
+  const bool tma_rec = h->tma_tg_ok && h->variant != PSM_KERNEL_PLAIN;
   void* lam0 = h->rec_lam[0];
   void* lam1 = h->rec_lam[1];
   double* grad = h->rec_grad;
@@ -1285,7 +1301,7 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   StepParams sp;
   std::memset(&sp, 0, sizeof sp);
   sp.g = h->g;
-  sp.t = tma_rec ? h->tma_tiling : h->tiling;
+  sp.t = tma_rec ? h->tma_tiling_tg : h->tiling;
   fill_consts<float>(h, sp.cf);
   fill_consts<double>(h, sp.cd);
   sp.fluid = h->col.fluid;
@@ -1327,7 +1343,7 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
     const int64_t ns = h->rec_n0 + m * K;
     const int64_t ne = std::min<int64_t>(ns + K, h->step);
     slots[0] = h->ckpt[(size_t)m];
-    if (tma_rec && ne - ns > 1 && !encode_maps(h, slots[0], smaps[0])) e = cudaErrorInvalidValue;
+    if (tma_rec && ne - ns > 1 && !encode_maps(h, slots[0], smaps[0], h->tma_tiling_tg)) e = cudaErrorInvalidValue;
     // recompute f^{ns+1} .. f^{ne-1} into the slots
     for (int64_t n = ns; n + 1 < ne && e == cudaSuccess; ++n) {
       for (int b = 0; b < nb; ++b) sp.body[b] = dev_body(h, b, n);

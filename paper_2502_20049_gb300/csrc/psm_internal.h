@@ -20,6 +20,25 @@ enum Storage { ST_FP64 = PSM_FP64, ST_FP32 = PSM_FP32, ST_FP16 = PSM_FP16_SHIFTE
 //                  x + c_i (natural).
 enum Mode { MODE_TG = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 
+// 1: the AA even step of the TMA kernel writes its tiles back with TMA tensor
+// stores (one per warp); 0 (default, measured faster on GB300): plain stores
+#ifndef PSM_TMA_STORE
+#define PSM_TMA_STORE 0
+#endif
+// Cells per thread in a tile of the TMA step kernel: PSM_TMA_CPT16 for the
+// D3Q19 two-grid step with BGK/TRT in 2-byte storage (FP16, BF16), where the
+// kernel is issue-bound and sharing the per-tile work (stage wait, refill,
+// tile classification, loop) between two cells measured faster; one
+// elsewhere (memory-bound 4- and 8-byte storage; D3Q27, AA and the cumulant,
+// where the larger stages of two-cell tiles cost more pipeline depth than the
+// shared work saves).
+#ifndef PSM_TMA_CPT16
+#define PSM_TMA_CPT16 2
+#endif
+__host__ __device__ constexpr int tma_cells_per_thread(int storage_bytes, int mode, int Q, int fluid) {
+  return (storage_bytes == 2 && mode == MODE_TG && Q == 19 && fluid != PSM_CUMULANT) ? PSM_TMA_CPT16 : 1;
+}
+
 // Layout a state is stored in.  Pre-collision f_i(x) sits at
 //   NATURAL: slot i of x;  SWAPPED: slot opp(i) of x - c_i.
 // Populations whose upstream cell x - c_i lies in a ghost plane are not

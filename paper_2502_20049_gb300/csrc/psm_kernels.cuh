@@ -1102,11 +1102,6 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 #ifndef PSM_TMA_OUT_BUFS
 #define PSM_TMA_OUT_BUFS 2
 #endif
-// 1: the AA even step writes its tiles back with TMA tensor stores (one per
-// warp); 0 (default, measured faster on GB300): plain coalesced stores
-#ifndef PSM_TMA_STORE
-#define PSM_TMA_STORE 0
-#endif
 
 
 // Lattice components for a run-time direction index (the producer's copy
@@ -1123,7 +1118,8 @@ __device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return
 // Shared-memory layout of the TMA step kernel (bytes; every box 128-byte
 // aligned): [barriers 128 B] [NST input stages] [NOUT output buffers].
 //   input, own-cell modes (two-grid, AA even): one [Q][TY][TX] box per tile
-//     (TX TY = 256): slot i of thread t at element 256 i + t;
+//     (TX TY = 256 CPT): slot i of cell r of thread t at element
+//     256 CPT i + 256 r + t;
 //   input, AA odd (TX = 256, TY = 1): per direction i a record of ROW bytes
 //     holding, from byte 128, the 256 values of slot opp(i) at x - c_i for the
 //     tile's cells, preceded and followed by a 16-byte x-edge chunk, so that
@@ -1139,9 +1135,12 @@ template <class S, int Q, int MODE, int FL = 0>
 struct TmaLayout {
   static constexpr bool LOAD_OWN = MODE != MODE_AA_ODD;
   static constexpr bool STORE_TMA = PSM_TMA_STORE && MODE == MODE_AA_EVEN;
+  // cells per thread and tile (tma_cells_per_thread: the host tiles alike)
+  static constexpr int CPT = tma_cells_per_thread((int)sizeof(S), MODE, Q, FL);  // FL numbers the fluid like psm.h
   static constexpr int EP = 16 / (int)sizeof(S);  // elements per 16-byte edge chunk
   static constexpr int r128(int b) { return ((b + 127) / 128) * 128; }
-  static constexpr int BOX = r128(Q * PSM_THREADS * (int)sizeof(S));
+  static constexpr int BOX_BYTES = Q * PSM_THREADS * CPT * (int)sizeof(S);
+  static constexpr int BOX = r128(BOX_BYTES);
   static constexpr int ROW = r128(128 + PSM_THREADS * (int)sizeof(S) + 16);
   static constexpr int STAGE = LOAD_OWN ? BOX : Q * ROW;
   static constexpr int WBOX = r128(Q * 32 * (int)sizeof(S));
@@ -1209,6 +1208,13 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = lane; k < PSM_MAX_BODIES * 6; k += 32) s_ft[warp][k] = 0.0;
   const int TX = p.t.tx, TY = p.t.ty;
+  constexpr int CPT = L::CPT;
+  if (TX * TY != PSM_THREADS * CPT) {
+    // a tiling this instance was not built for: refuse before any wait or copy
+    if (threadIdx.x == 0 && p.err) atomicExch(p.err, 2);
+    return;
+  }
+  const int TYB = TY / CPT;  // rows of the tile covered by one cell per thread
   unsigned char* stages = base + 128;
   unsigned char* outs = stages + NST * L::STAGE;
   const int ntiles = (int)p.t.ntiles;
@@ -1244,7 +1250,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
     fence_proxy_async();
     if (L::LOAD_OWN) {
       if (lane == 0) {
-        mbar_expect_tx(bar, (unsigned)(Q * PSM_THREADS * (int)sizeof(S)));
+        mbar_expect_tx(bar, (unsigned)L::BOX_BYTES);
         tma_load_4d(st, &maps.tile, x0, y0, z, 0, bar);
       }
     } else {
@@ -1299,67 +1305,75 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
   auto tile_body = [&](auto gen_c, int tile, int k, int s, const int4 hd) {
     (void)tile;
     constexpr bool GEN = decltype(gen_c)::value;
-    const int x = hd.x + lx, y = hd.y + ly, z = hd.z;
-    const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
+    const int z = hd.z;
     ZGhost zg;
     zg.init(p.g, z);
     const unsigned char* st = stages + s * L::STAGE;
-    T f[Q];
+    // the thread's cells r = 0 .. CPT-1: (lx, ly + r TYB), one after the other
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (GEN && zg.from(lat_cz(i))) {
-        f[i] = cst<T>(p).ghost[i];
-      } else if (L::LOAD_OWN) {
-        f[i] = Store<S>::ld(reinterpret_cast<const S*>(st) + i * PSM_THREADS + threadIdx.x);
-      } else {
-        f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + i * L::ROW + 128) + (lx - lat_cx(i)));
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
-    // refill the stage of tile j = k - LAG (read by every warp by now, as a rule)
-    // with tile j + NST; warp j mod NW does it
-    const int j = k - LAG;
-    if (j >= 0 && warp == j % NW) {
-      const int next = tile + (NST - LAG) * gridDim.x;
-      if (next < ntiles) {
-        const int sj = j % NST;
-        // warp-uniform outcome (produce needs the whole warp)
-        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[sj], (unsigned)((j / NST) & 1)))) {
-          const int4 cur = s_walk[warp];
-          produce(cur, sj);
-          if (lane == 0) s_walk[warp] = tile_advance(p.t, cur, s_wstep);
+    for (int r = 0; r < CPT; ++r) {
+      const int x = hd.x + lx, y = hd.y + ly + r * TYB;
+      const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
+      T f[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (GEN && zg.from(lat_cz(i))) {
+          f[i] = cst<T>(p).ghost[i];
+        } else if (L::LOAD_OWN) {
+          f[i] = Store<S>::ld(reinterpret_cast<const S*>(st) + (i * CPT + r) * PSM_THREADS + threadIdx.x);
         } else {
-          s_abort = 1;
+          f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + i * L::ROW + 128) + (lx - lat_cx(i)));
         }
       }
-    }
-    int owner = -1;
-    bool solid_cell = false;
-    double ft[6] = {0, 0, 0, 0, 0, 0};
-    if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
-    else fluid_collide<T, Q, FL>(p, f);
-    if (L::STORE_TMA) {
-      // this warp's output box of tile k; lane 0 issued (and committed) the
-      // warp's earlier stores: the one NOUT tiles back must have read it
-      S* ow = reinterpret_cast<S*>(outs + (k % NOUT) * L::OUT + warp * L::WBOX);
-      if (lane == 0) bulk_wait_read<NOUT - 1>();
-      __syncwarp();
-#pragma unroll
-      for (int i = 0; i < Q; ++i) Store<S>::st(ow + lat_opp(i) * 32 + lane, f[i]);
-      fence_proxy_async();  // the generic-proxy writes above become visible to the TMA store
-      __syncwarp();
-      if (lane == 0) {
-        const int w0 = warp * 32;
-        tma_store_4d(&maps.dstw, hd.x + w0 % TX, hd.y + w0 / TX, z, 0, ow);
-        bulk_commit();
+      if (r == CPT - 1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        // refill the stage of tile j = k - LAG (read by every warp by now, as a
+        // rule) with tile j + NST; warp j mod NW does it
+        const int j = k - LAG;
+        if (j >= 0 && warp == j % NW) {
+          const int next = tile + (NST - LAG) * gridDim.x;
+          if (next < ntiles) {
+            const int sj = j % NST;
+            // warp-uniform outcome (produce needs the whole warp)
+            if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[sj], (unsigned)((j / NST) & 1)))) {
+              const int4 cur = s_walk[warp];
+              produce(cur, sj);
+              if (lane == 0) s_walk[warp] = tile_advance(p.t, cur, s_wstep);
+            } else {
+              s_abort = 1;
+            }
+          }
+        }
       }
-    } else {
-      Stencil sn;
-      sn.init(p.g, x, y, z, cell);
-      psm_store<S, Q, MODE, GEN>(p, sn, zg, cell, f);
+      int owner = -1;
+      bool solid_cell = false;
+      double ft[6] = {0, 0, 0, 0, 0, 0};
+      if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
+      else fluid_collide<T, Q, FL>(p, f);
+      if constexpr (L::STORE_TMA) {
+        static_assert(CPT == 1, "TMA stores write one cell per thread");
+        // this warp's output box of tile k; lane 0 issued (and committed) the
+        // warp's earlier stores: the one NOUT tiles back must have read it
+        S* ow = reinterpret_cast<S*>(outs + (k % NOUT) * L::OUT + warp * L::WBOX);
+        if (lane == 0) bulk_wait_read<NOUT - 1>();
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<S>::st(ow + lat_opp(i) * 32 + lane, f[i]);
+        fence_proxy_async();  // the generic-proxy writes above become visible to the TMA store
+        __syncwarp();
+        if (lane == 0) {
+          const int w0 = warp * 32;
+          tma_store_4d(&maps.dstw, hd.x + w0 % TX, hd.y + w0 / TX, z, 0, ow);
+          bulk_commit();
+        }
+      } else {
+        Stencil sn;
+        sn.init(p.g, x, y, z, cell);
+        psm_store<S, Q, MODE, GEN>(p, sn, zg, cell, f);
+      }
+      if (GEN) warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
     }
-    if (GEN) warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
   };
 
   int k = 0;

@@ -57,3 +57,16 @@ def ft_err(a, b, lever=1.0):
     eF = np.abs(fa[..., :3] - fb[..., :3]).max() / max(sF, 1e-300)
     eT = np.abs(fa[..., 3:] - fb[..., 3:]).max() / max(sT, 1e-300)
     return max(eF, eT)
+
+
+def assert_ft_same(fa, fb, storage):
+    """Force/torque series of two runs with bit-identical states.  Kernels with
+    the same tiling reduce in the same order and agree bit for bit; the TMA
+    kernel gives 2-byte storage tiles of two cells per thread, so its FP64 sums
+    (torque terms are products, not exact) run in another order: 1e-12 of the
+    largest component."""
+    fa, fb = np.asarray(fa), np.asarray(fb)
+    if storage in ("fp16", "bf16"):
+        assert np.abs(fa - fb).max() <= 1e-12 * np.abs(fb).max()
+    else:
+        assert np.array_equal(fa, fb)

@@ -13,7 +13,7 @@ and a linear solve), so agreement is a check of both.
 import numpy as np
 import pytest
 
-from helpers import ft_err, perm_lib_to_oracle, run_gpu, run_oracle, u_err
+from helpers import assert_ft_same, ft_err, perm_lib_to_oracle, run_gpu, run_oracle, u_err
 from paper_2502_20049_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -121,7 +121,7 @@ def test_tma_full_rows_equal_plain_bitwise(storage, streaming, bc_z):
     a.step(case.steps)
     b.step(case.steps)
     assert np.array_equal(a.get_state(), b.get_state())
-    assert np.array_equal(a.force_torque(0), b.force_torque(0))
+    assert_ft_same(a.force_torque(0), b.force_torque(0), storage)
 
 
 def test_full_rows_fp32_against_oracle():
