@@ -127,6 +127,10 @@ __device__ __forceinline__ float remap_eps(const DevBody& b, int x, int y, int z
   }
   int count = 0;
   const int nn = n * n;
+  // s <= 2 (one word per brick, bit (z n + y) n + x): rowrep has bit r n set
+  // for every row r < n^2, layrep bit l n^2 for every layer l < n
+  const unsigned long long rowrep = s == 2 ? 0x1111111111111111ull : (s == 1 ? 0x55ull : 1ull);
+  const unsigned long long layrep = s == 2 ? 0x0001000100010001ull : (s == 1 ? 0x11ull : 1ull);
   for (int sz = 0; sz < 2; ++sz) {
     if (sz == 1 && o[2] == 0) break;
     const int gz = gc[2] + sz;
@@ -146,10 +150,6 @@ __device__ __forceinline__ float remap_eps(const DevBody& b, int x, int y, int z
             b.bricks + ((long long)((long long)gz * b.gy + gy) * b.gx + gx) * b.wpb;
         const unsigned long long xm = low_bits(xb - xa) << xa;
         if (s <= 2) {
-          // one word: bit (z n + y) n + x
-          unsigned long long rowrep = 0, layrep = 0;
-          for (int r = 0; r < nn; ++r) rowrep |= 1ull << (r * n);
-          for (int l = 0; l < n; ++l) layrep |= 1ull << (l * nn);
           const unsigned long long ym = (low_bits(n * (yb - ya)) << (n * ya)) * layrep;
           const unsigned long long zm = low_bits(nn * (zb - za)) << (nn * za);
           const unsigned long long m = (xm * rowrep) & ym & zm;
@@ -656,7 +656,7 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
   T eps = T(epsf);
   if (p.delta) eps += T(p.delta[cell]);
   T Bw = eps;
-  if (p.weighting == PSM_B_TAU_WEIGHTED) {
+  if (p.weighting == PSM_B_TAU_WEIGHTED && eps != T(0)) {  // eps = 0 gives B = eps exactly
     const T t = C.tmh;
     Bw = eps * t / ((T(1) - eps) + t);
   }
