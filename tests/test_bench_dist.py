@@ -6,6 +6,8 @@ import socket
 
 import pytest
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
 
 def _free_port():
     with socket.socket() as s:
@@ -96,3 +98,23 @@ def test_single_rank_defaults(monkeypatch):
     assert replicas.env() == (0, 1, 0)
     assert replicas.init() is None
     assert replicas.max_over_ranks(None, 3.5) == 3.5
+
+
+@pytest.mark.parametrize("fluid", [None, "cumulant"])
+def test_reference_arm_line(fluid):
+    """bench.py --impl reference times the FP64 oracle on the host (no GPU) and
+    prints one JSON line with the contract's keys; --fluid selects the
+    operator of the workload it samples."""
+    import json
+    import subprocess
+    import sys
+
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3"]
+    if fluid:
+        cmd += ["--fluid", fluid]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert ("cumulant" in line["config"]["workload"]) == (fluid == "cumulant")
