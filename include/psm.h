@@ -336,8 +336,8 @@ int psm_series_capacity(psm_handle h, int64_t* out);
 int psm_mass(psm_handle h, double* out);
 
 /* Wait for all work of the handle.  PSM_ERR_CUDA if a step kernel gave up
- * waiting for its staged loads (it records this in a flag instead of
- * trapping). */
+ * waiting for its staged loads, or refused a tiling it was not built for (it
+ * records this in a flag instead of trapping). */
 int psm_synchronize(psm_handle h);
 
 /* Step-kernel variant: PSM_KERNEL_AUTO (default) uses the TMA-staged kernel
@@ -346,9 +346,13 @@ int psm_synchronize(psm_handle h);
  * PSM_KERNEL_PLAIN forces plain loads; PSM_KERNEL_TMA forces TMA staging for
  * every step the shape allows (PSM_ERR_UNSUPPORTED if it allows none).  TMA
  * shapes: with TX = min(256, nx): nx % TX == 0, 256 % nx == 0 when nx < 256,
- * TX >= 32, ny % (256 / TX) == 0, nx * sizeof(PDF) a multiple of 16 bytes,
- * staging buffers within the per-block shared memory; the AA odd step also
- * needs TX = 256.  All variants compute the same results, bit for bit. */
+ * TX >= 32, ny % (256 / TX) == 0 (ny % (512 / TX) == 0 for the D3Q19
+ * two-grid BGK/TRT step in FP16/BF16, whose tiles hold two cells per thread),
+ * nx * sizeof(PDF) a multiple of 16 bytes, staging buffers within the
+ * per-block shared memory; the AA odd step also needs TX = 256.  All variants
+ * compute the same states, bit for bit; the FP64 force/torque sums agree bit
+ * for bit where the variants tile alike and to rounding (summation order)
+ * otherwise. */
 /* ------------------------------------------------------------------------ */
 /* Differentiation (not in the paper): discrete adjoint of the step          */
 /* ------------------------------------------------------------------------ */
