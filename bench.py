@@ -55,25 +55,30 @@ def with_fluid(case, desc, fluid):
     return case.with_(fluid=fluid), desc.replace(FLUID_NAME[case.fluid], FLUID_NAME[fluid], 1)
 
 
-def workload(name: str, streaming: str, fluid: str | None = None):
+def workload(name: str, streaming: str, fluid: str | None = None, scale: float = 1.0):
+    """The named workload; scale < 1 shrinks the lattice and the bodies alike
+    (a small case of the same kernels, for profiling)."""
     from paper_2502_20049_gb300 import workloads as W
 
+    def dims(*d):
+        return tuple(int(round(v * scale)) for v in d)
+
     if name == "c2":
-        case = W.c2_ellipsoid()
-        desc = ("D3Q19 TRT FP32 256^3, inflow 0.05, tau 0.55, ellipsoid 40/20/8 rotating 2e-4 rad/step about z, "
-                "remap every step")
+        n = dims(256)[0]
+        case = W.c2_ellipsoid(scale=scale, n=n)
+        body = "40/20/8" if scale == 1.0 else f"40/20/8 x{scale:g}"
+        desc = (f"D3Q19 TRT FP32 {n}^3, inflow 0.05, tau 0.55, ellipsoid {body} rotating 2e-4 rad/step about z, "
+                f"remap every step")
     elif name == "c5":
-        case = W.c5_large()
-        desc = "D3Q19 BGK FP16-shifted 1024x1024x960, counter-rotating rotor x2, remap every step"
-    elif name == "c3_fp32":
-        case = W.c3_rotor("fp32")
-        desc = "D3Q27 BGK FP32 512x512x640, counter-rotating rotor, remap every step"
-    elif name == "c3_fp16":
-        case = W.c3_rotor("fp16")
-        desc = "D3Q27 BGK FP16-shifted 512x512x640, counter-rotating rotor, remap every step"
-    elif name == "c3_bf16":
-        case = W.c3_rotor("bf16")
-        desc = "D3Q27 BGK BF16-shifted 512x512x640, counter-rotating rotor, remap every step"
+        d = dims(1024, 1024, 960)
+        case = W.c5_large(dims=d)
+        desc = f"D3Q19 BGK FP16-shifted {d[0]}x{d[1]}x{d[2]}, counter-rotating rotor x2, remap every step"
+    elif name in ("c3_fp32", "c3_fp16", "c3_bf16"):
+        d = dims(512, 512, 640)
+        storage = name.split("_")[1]
+        case = W.c3_rotor(storage, scale=scale, dims=d)
+        desc = (f"D3Q27 BGK {storage.upper()}{'-shifted' if storage != 'fp32' else ''} {d[0]}x{d[1]}x{d[2]}, "
+                f"counter-rotating rotor, remap every step")
     else:
         raise SystemExit(f"unknown workload {name}")
     case = case.with_(streaming=streaming)
@@ -286,7 +291,7 @@ def run_ours(args):
         # the adjoint workload alone (for profiling the backward kernels)
         print(json.dumps({"adjoint": adjoint_cost(torch.cuda.current_stream())}), flush=True)
         return
-    case, desc = workload(args.workload, args.streaming, args.fluid)
+    case, desc = workload(args.workload, args.streaming, args.fluid, args.scale)
     if args.storage:
         case = case.with_(storage=args.storage)
         desc = desc.replace("FP32", args.storage.upper()).replace("FP16-shifted", args.storage.upper())
@@ -389,6 +394,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the variant and adjoint measurements")
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint cost measurement")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload's lattice and bodies (a small case for profiling; not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
