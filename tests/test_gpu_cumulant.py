@@ -153,3 +153,24 @@ def test_no_adjoint():
     with pytest.raises(psm.PSMError) as e:
         sol.record(8)
     assert e.value.code == -6  # PSM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("tau,rates", [(0.9, (1.0, 1.0, 1.0)), (0.505, (1.95, 0.05, 1.95)), (3.0, (0.05, 1.95, 0.05))])
+def test_no_body_and_single_cell_fp64(tau, rates):
+    """Pure LBM (no body, ragged grid, ghost planes) and a 1x1x1 periodic grid
+    (every population streams back into its own cell: one collision per step),
+    at rates near both ends of (0, 2) and tau near 1/2 (shear rate near 2)."""
+    case = W.Case("nobody_cum", 20, 9, 11, Q=19, storage="fp64", fluid="cumulant", tau=tau, cum_rates=rates,
+                  u_in=(0.0, 0.02, 0.03), steps=17)
+    g, o = run_gpu(case), oracle_cached(case)
+    perm = perm_lib_to_oracle(19)
+    assert np.abs(g["f"] - o["f"][perm]).max() <= 1e-13
+    one = W.Case("one_cum", 1, 1, 1, Q=19, storage="fp64", fluid="cumulant", tau=tau, cum_rates=rates, bc_z=0,
+                 u_in=(0.01, 0.0, 0.0), steps=5,
+                 bodies=[W.BodyCase(W.BOX, (0.3, 0.3, 0.3), 2, (0.5, 0.5, 0.5), v=(0.0, 0.01, 0.0))])
+    # a 0.6^3 box at s = 2 covers 8 of the cell's 64 sub-cells: eps = 1/8, so both
+    # the cumulant and the solid collision act
+    g, o = run_gpu(one), oracle_cached(one)
+    assert abs(o["sim"].eps()[0][0, 0, 0] - 0.125) < 1e-15
+    assert np.abs(g["f"] - o["f"][perm]).max() <= 1e-14
+    assert ft_err(g, o) <= 1e-12
