@@ -145,8 +145,12 @@ __device__ __forceinline__ T adj_fluid_cell(const ConstT<T>& C, int solid, T inv
   return bb;
 }
 
-template <class S, int Q, int TRT>
-__global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint(const __grid_constant__ AdjParams p) {
+// PART: 0 every tile; 1 the fluid-only tiles (no scalar sums: a lean kernel
+// that fits three blocks per SM); 2 the general tiles (with the FP64 sums).
+// A step launches 1 and 2 (disjoint cells) or 0.
+template <class S, int Q, int TRT, int PART>
+__global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ? 3 : 2))
+    k_adjoint(const __grid_constant__ AdjParams p) {
   using T = typename Store<S>::T;
   constexpr int NW = PSM_THREADS / 32;
   constexpr int NC = PSM_MAX_BODIES * 3 + 3;
@@ -423,9 +427,13 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : 2) k_adjoint
         gen = gen || (x0 < b.x1 && x0 + p.t.tx > b.x0 && y0 < b.y1 && y0 + p.t.ty > b.y0 && z >= b.z0 && z < b.z1);
       }
     }
-    if (gen) cell_body(BoolC<true>{}, x0 + lx, y0 + ly, z);
-    else cell_body(BoolC<false>{}, x0 + lx, y0 + ly, z);
+    if (gen) {
+      if (PART != 1) cell_body(BoolC<true>{}, x0 + lx, y0 + ly, z);
+    } else {
+      if (PART != 2) cell_body(BoolC<false>{}, x0 + lx, y0 + ly, z);
+    }
   }
+  if (PART == 1) return;
   __syncthreads();
   __shared__ double blk[NC];
   if ((int)threadIdx.x < ncomp) {
@@ -473,15 +481,33 @@ __global__ void __launch_bounds__(PSM_THREADS) k_adjoint_init(const __grid_const
   grid_reduce(blk, 3, p.partials, p.ticket, p.acc_out);
 }
 
+// Split launch of one adjoint step (PSM_ADJ_SPLIT, default on for D3Q19 with
+// 4-byte arithmetic; the D3Q27 fluid part would spill at 80 registers): the
+// fluid tiles at three blocks per SM, then the general tiles.
+#ifndef PSM_ADJ_SPLIT
+#define PSM_ADJ_SPLIT 1
+#endif
+template <class S, int Q, int TRT, int PART>
+cudaError_t launch_adjoint_part(const AdjParams& p, cudaStream_t st) {
+  static int blocks = persistent_blocks(k_adjoint<S, Q, TRT, PART>, 1ll << 40);
+  const int grid = (int)(p.t.ntiles < blocks ? p.t.ntiles : blocks);
+  k_adjoint<S, Q, TRT, PART><<<grid, PSM_THREADS, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <class S, int Q, int TRT>
+cudaError_t launch_adjoint_t(const AdjParams& p, cudaStream_t st) {
+  if constexpr (PSM_ADJ_SPLIT && sizeof(S) != 8 && Q == 19) {
+    const cudaError_t e = launch_adjoint_part<S, Q, TRT, 1>(p, st);
+    return e != cudaSuccess ? e : launch_adjoint_part<S, Q, TRT, 2>(p, st);
+  } else {
+    return launch_adjoint_part<S, Q, TRT, 0>(p, st);
+  }
+}
+
 template <class S, int Q>
 cudaError_t launch_adjoint_q(int trt, const AdjParams& p, cudaStream_t st) {
-  static int blocks_bgk = persistent_blocks(k_adjoint<S, Q, 0>, 1ll << 40);
-  static int blocks_trt = persistent_blocks(k_adjoint<S, Q, 1>, 1ll << 40);
-  const int b = trt ? blocks_trt : blocks_bgk;
-  const int grid = (int)(p.t.ntiles < b ? p.t.ntiles : b);
-  if (trt) k_adjoint<S, Q, 1><<<grid, PSM_THREADS, 0, st>>>(p);
-  else k_adjoint<S, Q, 0><<<grid, PSM_THREADS, 0, st>>>(p);
-  return cudaGetLastError();
+  return trt ? launch_adjoint_t<S, Q, 1>(p, st) : launch_adjoint_t<S, Q, 0>(p, st);
 }
 
 template <class S, int Q>
