@@ -205,188 +205,198 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
       if (GEN) epsf = cell_eps(p.body, nb, x, y, z, owner);
       T e = T(epsf);
       if (p.delta) e += T(p.delta[cell]);
-      T Bw = e, Bp = T(1);
-      if (p.weighting == PSM_B_TAU_WEIGHTED) {
-        const T t = C.tmh;
-        const T den = (T(1) - e) + t;
-        Bw = e * t / den;
-        Bp = t * (T(1) + t) / (den * den);
-      }
-      T drho = 0, jx = 0, jy = 0, jz = 0;
+      if (e == T(0) && !zg.lo && !zg.hi) {
+        // B = 0 and no ghost population (a cell of a general tile outside the
+        // bodies): the fluid-only reverse step, B'(0) for the gradient
+        T lam[Q];
+        const T bb = adj_fluid_cell<T, Q>(C, p.solid, inv_tau, f, mu, lam);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        drho += f[i];
-        if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
-        if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
-        if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
-      }
-      const T rho = C.rho0 + drho;
-      const T inv_rho = recip(rho);
-      const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-      const T uu = ux * ux + uy * uy + uz * uz;
-      T usx = 0, usy = 0, usz = 0;
-      double Rx = 0, Ry = 0, Rz = 0;
-      if (GEN && owner >= 0) {
-        const DevBody& b = p.body[owner];
-        Rx = (double)x + 0.5 - b.R[0];
-        Ry = (double)y + 0.5 - b.R[1];
-        Rz = (double)z + 0.5 - b.R[2];
-        T rx, ry, rz, wx, wy, wz, vx, vy, vz;
-        if constexpr (sizeof(T) == 4) {
-          rx = (T(x) + T(0.5)) - b.Rf[0];
-          ry = (T(y) + T(0.5)) - b.Rf[1];
-          rz = (T(z) + T(0.5)) - b.Rf[2];
-          wx = b.omegaf[0], wy = b.omegaf[1], wz = b.omegaf[2];
-          vx = b.vf[0], vy = b.vf[1], vz = b.vf[2];
-        } else {
-          rx = Rx, ry = Ry, rz = Rz;
-          wx = b.omega[0], wy = b.omega[1], wz = b.omega[2];
-          vx = b.v[0], vy = b.v[1], vz = b.v[2];
+        for (int i = 0; i < Q; ++i) static_cast<T*>(p.lout_slot[i])[cell] = lam[i];
+        grad[cell] = g_old + (double)(bb * Bp0);
+      } else {
+        T Bw = e, Bp = T(1);
+        if (p.weighting == PSM_B_TAU_WEIGHTED) {
+          const T t = C.tmh;
+          const T den = (T(1) - e) + t;
+          Bw = e * t / den;
+          Bp = t * (T(1) + t) / (den * den);
         }
-        usx = wy * rz - wz * ry + vx;
-        usy = wz * rx - wx * rz + vy;
-        usz = wx * ry - wy * rx + vz;
-      }
-      const T usus = usx * usx + usy * usy + usz * usz;
-      const T omB = T(1) - Bw;
-      // ---- adjoint of the force/torque terms: s = B sum_i Omega^S_i c_i ----
-      T sbx = 0, sby = 0, sbz = 0;
-      if (GEN && owner >= 0 && Bw > T(0) && p.w) {
-        const double* wv = p.w + owner * 6;
-        // J_n = sum_b w_F . F_b + w_T . T_b with F_b = -sum s, T_b = -sum r x s
-        sbx = T(-(wv[0] + (wv[4] * Rz - wv[5] * Ry)));
-        sby = T(-(wv[1] + (wv[5] * Rx - wv[3] * Rz)));
-        sbz = T(-(wv[2] + (wv[3] * Ry - wv[4] * Rx)));
-      }
-      // ---- reverse sweep over the rest population and the opposite pairs ----
-      T Bbar = 0, rhob = 0;
-      T ubx = 0, uby = 0, ubz = 0, usbx = 0, usby = 0, usbz = 0;
-      // Without an owner (the fast path), u_s = 0: G_i = f^eq_i(rho, 0) - w_i rho0
-      // = w_i drho, phi_i(0) = w_i, and there is no u_s adjoint to accumulate.
-      {
-        const T E0 = feq_shifted_nz<Q, T>(0, drho, rho, ux, uy, uz, uu);
-        const T G0 = GEN ? feq_shifted_nz<Q, T>(0, drho, rho, usx, usy, usz, usus) : T(lat_w<Q>(0)) * drho;
-        const T n0 = f[0] - E0, m0 = f[0] - G0;
-        const T of0 = -(om_a + om_b) * n0;
-        T os0;
-        if (p.solid == PSM_SC1) os0 = n0 - m0;
-        else if (p.solid == PSM_SC2) os0 = -m0 * inv_tau;
-        else os0 = T(0);
-        const T osb = Bw * mu[0], ofb = omB * mu[0];
-        Bbar += mu[0] * (os0 - of0);
-        T nb0 = -(om_a + om_b) * ofb, mb0;
-        if (p.solid == PSM_SC1) {
-          nb0 += osb;
-          mb0 = -osb;
-        } else if (p.solid == PSM_SC2) {
-          mb0 = -osb * inv_tau;
-        } else {
-          mb0 = T(0);
-        }
-        f[0] = mu[0] + nb0 + mb0;
-        const T Eb = -nb0, Gb = -mb0;
-        rhob += Eb * phi<Q, T>(0, T(0), uu) + Gb * (GEN ? phi<Q, T>(0, T(0), usus) : T(lat_w<Q>(0)));
-        const T ke = T(-3) * rho * T(lat_w<Q>(0)) * Eb;
-        ubx += ke * ux;
-        uby += ke * uy;
-        ubz += ke * uz;
-        if constexpr (GEN) {
-          const T kg = T(-3) * rho * T(lat_w<Q>(0)) * Gb;
-          usbx += kg * usx;
-          usby += kg * usy;
-          usbz += kg * usz;
-        }
-      }
+        T drho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-      for (int i = 1; i < Q; i += 2) {
-        const int j = i + 1;
-        const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
-        const T cu = cdot(i, ux, uy, uz);
-        const T cs = GEN ? cdot(i, usx, usy, usz) : T(0);
-        const T Ei = feq_shifted_nz<Q, T>(i, drho, rho, ux, uy, uz, uu);
-        const T Ej = feq_shifted_nz<Q, T>(j, drho, rho, ux, uy, uz, uu);
-        const T wd = T(lat_w<Q>(i)) * drho;
-        const T Gi = GEN ? feq_shifted_nz<Q, T>(i, drho, rho, usx, usy, usz, usus) : wd;
-        const T Gj = GEN ? feq_shifted_nz<Q, T>(j, drho, rho, usx, usy, usz, usus) : wd;
-        const T ni = f[i] - Ei, nj = f[j] - Ej, mi = f[i] - Gi, mj = f[j] - Gj;
-        const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
-        const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);
-        T osi, osj;
-        if (p.solid == PSM_SC1) {
-          osi = nj - mi;
-          osj = ni - mj;
-        } else if (p.solid == PSM_SC2) {
-          osi = -mi * inv_tau;
-          osj = -mj * inv_tau;
-        } else {
-          osi = mj - mi;
-          osj = mi - mj;
+        for (int i = 0; i < Q; ++i) {
+          drho += f[i];
+          if (lat_cx(i)) jx += T(lat_cx(i)) * f[i];
+          if (lat_cy(i)) jy += T(lat_cy(i)) * f[i];
+          if (lat_cz(i)) jz += T(lat_cz(i)) * f[i];
         }
-        const T sci = GEN ? cdot(i, sbx, sby, sbz) : T(0);  // sbar . c_i; c_j = -c_i
-        const T osbi = GEN ? Bw * (mu[i] + sci) : Bw * mu[i], osbj = GEN ? Bw * (mu[j] - sci) : Bw * mu[j];
-        const T ofbi = omB * mu[i], ofbj = omB * mu[j];
-        if constexpr (GEN) Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj) + sci * (osi - osj);
-        else Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj);
-        T nbi = TRT ? (-om_a * ofbi - om_b * ofbj) : (-om_a * ofbi);
-        T nbj = TRT ? (-om_a * ofbj - om_b * ofbi) : (-om_a * ofbj);
-        T mbi, mbj;
-        if (p.solid == PSM_SC1) {
-          nbi += osbj;
-          nbj += osbi;
-          mbi = -osbi;
-          mbj = -osbj;
-        } else if (p.solid == PSM_SC2) {
-          mbi = -osbi * inv_tau;
-          mbj = -osbj * inv_tau;
-        } else {
-          mbi = osbj - osbi;
-          mbj = osbi - osbj;
+        const T rho = C.rho0 + drho;
+        const T inv_rho = recip(rho);
+        const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+        const T uu = ux * ux + uy * uy + uz * uz;
+        T usx = 0, usy = 0, usz = 0;
+        double Rx = 0, Ry = 0, Rz = 0;
+        if (GEN && owner >= 0) {
+          const DevBody& b = p.body[owner];
+          Rx = (double)x + 0.5 - b.R[0];
+          Ry = (double)y + 0.5 - b.R[1];
+          Rz = (double)z + 0.5 - b.R[2];
+          T rx, ry, rz, wx, wy, wz, vx, vy, vz;
+          if constexpr (sizeof(T) == 4) {
+            rx = (T(x) + T(0.5)) - b.Rf[0];
+            ry = (T(y) + T(0.5)) - b.Rf[1];
+            rz = (T(z) + T(0.5)) - b.Rf[2];
+            wx = b.omegaf[0], wy = b.omegaf[1], wz = b.omegaf[2];
+            vx = b.vf[0], vy = b.vf[1], vz = b.vf[2];
+          } else {
+            rx = Rx, ry = Ry, rz = Rz;
+            wx = b.omega[0], wy = b.omega[1], wz = b.omega[2];
+            vx = b.v[0], vy = b.v[1], vz = b.v[2];
+          }
+          usx = wy * rz - wz * ry + vx;
+          usy = wz * rx - wx * rz + vy;
+          usz = wx * ry - wy * rx + vz;
         }
-        f[i] = mu[i] + nbi + mbi;
-        f[j] = mu[j] + nbj + mbj;
-        const T Ebi = -nbi, Ebj = -nbj, Gbi = -mbi, Gbj = -mbj;
-        if constexpr (GEN)
-          rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + Gbi * phi<Q, T>(i, cs, usus) +
-                  Gbj * phi<Q, T>(j, -cs, usus);
-        else
-          rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + (Gbi + Gbj) * T(lat_w<Q>(i));
-        // d f^eq_i / d v = rho w_i (3 c_i + 9 (c_i.v) c_i - 3 v), and c_j = -c_i
-        const T rw = rho * T(lat_w<Q>(i));
-        const T ae = rw * (T(3) * (Ebi - Ebj) + T(9) * cu * (Ebi + Ebj)), be = T(-3) * rw * (Ebi + Ebj);
-        ubx += cx ? csign(cx, ae) + be * ux : be * ux;
-        uby += cy ? csign(cy, ae) + be * uy : be * uy;
-        ubz += cz ? csign(cz, ae) + be * uz : be * uz;
-        if constexpr (GEN) {
-          const T ag = rw * (T(3) * (Gbi - Gbj) + T(9) * cs * (Gbi + Gbj)), bg = T(-3) * rw * (Gbi + Gbj);
-          usbx += cx ? csign(cx, ag) + bg * usx : bg * usx;
-          usby += cy ? csign(cy, ag) + bg * usy : bg * usy;
-          usbz += cz ? csign(cz, ag) + bg * usz : bg * usz;
+        const T usus = usx * usx + usy * usy + usz * usz;
+        const T omB = T(1) - Bw;
+        // ---- adjoint of the force/torque terms: s = B sum_i Omega^S_i c_i ----
+        T sbx = 0, sby = 0, sbz = 0;
+        if (GEN && owner >= 0 && Bw > T(0) && p.w) {
+          const double* wv = p.w + owner * 6;
+          // J_n = sum_b w_F . F_b + w_T . T_b with F_b = -sum s, T_b = -sum r x s
+          sbx = T(-(wv[0] + (wv[4] * Rz - wv[5] * Ry)));
+          sby = T(-(wv[1] + (wv[5] * Rx - wv[3] * Rz)));
+          sbz = T(-(wv[2] + (wv[3] * Ry - wv[4] * Rx)));
         }
-      }
-      // u = j / rho
-      const T jbx = ubx * inv_rho, jby = uby * inv_rho, jbz = ubz * inv_rho;
-      rhob -= (ubx * ux + uby * uy + ubz * uz) * inv_rho;
-      // ---- lambda^n = fbar + drho/df rhobar + dj/df . jbar ----
+        // ---- reverse sweep over the rest population and the opposite pairs ----
+        T Bbar = 0, rhob = 0;
+        T ubx = 0, uby = 0, ubz = 0, usbx = 0, usby = 0, usbz = 0;
+        // Without an owner (the fast path), u_s = 0: G_i = f^eq_i(rho, 0) - w_i rho0
+        // = w_i drho, phi_i(0) = w_i, and there is no u_s adjoint to accumulate.
+        {
+          const T E0 = feq_shifted_nz<Q, T>(0, drho, rho, ux, uy, uz, uu);
+          const T G0 = GEN ? feq_shifted_nz<Q, T>(0, drho, rho, usx, usy, usz, usus) : T(lat_w<Q>(0)) * drho;
+          const T n0 = f[0] - E0, m0 = f[0] - G0;
+          const T of0 = -(om_a + om_b) * n0;
+          T os0;
+          if (p.solid == PSM_SC1) os0 = n0 - m0;
+          else if (p.solid == PSM_SC2) os0 = -m0 * inv_tau;
+          else os0 = T(0);
+          const T osb = Bw * mu[0], ofb = omB * mu[0];
+          Bbar += mu[0] * (os0 - of0);
+          T nb0 = -(om_a + om_b) * ofb, mb0;
+          if (p.solid == PSM_SC1) {
+            nb0 += osb;
+            mb0 = -osb;
+          } else if (p.solid == PSM_SC2) {
+            mb0 = -osb * inv_tau;
+          } else {
+            mb0 = T(0);
+          }
+          f[0] = mu[0] + nb0 + mb0;
+          const T Eb = -nb0, Gb = -mb0;
+          rhob += Eb * phi<Q, T>(0, T(0), uu) + Gb * (GEN ? phi<Q, T>(0, T(0), usus) : T(lat_w<Q>(0)));
+          const T ke = T(-3) * rho * T(lat_w<Q>(0)) * Eb;
+          ubx += ke * ux;
+          uby += ke * uy;
+          ubz += ke * uz;
+          if constexpr (GEN) {
+            const T kg = T(-3) * rho * T(lat_w<Q>(0)) * Gb;
+            usbx += kg * usx;
+            usby += kg * usy;
+            usbz += kg * usz;
+          }
+        }
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const T l = f[i] + rhob + cdot(i, jbx, jby, jbz);
-        static_cast<T*>(p.lout_slot[i])[cell] = l;
-        if (GEN && zg.from(lat_cz(i))) {
-          // the population is the ghost value g_i(u_in)
-          au0 += (double)l * p.dghost[i][0];
-          au1 += (double)l * p.dghost[i][1];
-          au2 += (double)l * p.dghost[i][2];
-          has_u = true;
+        for (int i = 1; i < Q; i += 2) {
+          const int j = i + 1;
+          const int cx = lat_cx(i), cy = lat_cy(i), cz = lat_cz(i);
+          const T cu = cdot(i, ux, uy, uz);
+          const T cs = GEN ? cdot(i, usx, usy, usz) : T(0);
+          const T Ei = feq_shifted_nz<Q, T>(i, drho, rho, ux, uy, uz, uu);
+          const T Ej = feq_shifted_nz<Q, T>(j, drho, rho, ux, uy, uz, uu);
+          const T wd = T(lat_w<Q>(i)) * drho;
+          const T Gi = GEN ? feq_shifted_nz<Q, T>(i, drho, rho, usx, usy, usz, usus) : wd;
+          const T Gj = GEN ? feq_shifted_nz<Q, T>(j, drho, rho, usx, usy, usz, usus) : wd;
+          const T ni = f[i] - Ei, nj = f[j] - Ej, mi = f[i] - Gi, mj = f[j] - Gj;
+          const T ofi = TRT ? (-om_a * ni - om_b * nj) : (-om_a * ni);
+          const T ofj = TRT ? (-om_a * nj - om_b * ni) : (-om_a * nj);
+          T osi, osj;
+          if (p.solid == PSM_SC1) {
+            osi = nj - mi;
+            osj = ni - mj;
+          } else if (p.solid == PSM_SC2) {
+            osi = -mi * inv_tau;
+            osj = -mj * inv_tau;
+          } else {
+            osi = mj - mi;
+            osj = mi - mj;
+          }
+          const T sci = GEN ? cdot(i, sbx, sby, sbz) : T(0);  // sbar . c_i; c_j = -c_i
+          const T osbi = GEN ? Bw * (mu[i] + sci) : Bw * mu[i], osbj = GEN ? Bw * (mu[j] - sci) : Bw * mu[j];
+          const T ofbi = omB * mu[i], ofbj = omB * mu[j];
+          if constexpr (GEN) Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj) + sci * (osi - osj);
+          else Bbar += mu[i] * (osi - ofi) + mu[j] * (osj - ofj);
+          T nbi = TRT ? (-om_a * ofbi - om_b * ofbj) : (-om_a * ofbi);
+          T nbj = TRT ? (-om_a * ofbj - om_b * ofbi) : (-om_a * ofbj);
+          T mbi, mbj;
+          if (p.solid == PSM_SC1) {
+            nbi += osbj;
+            nbj += osbi;
+            mbi = -osbi;
+            mbj = -osbj;
+          } else if (p.solid == PSM_SC2) {
+            mbi = -osbi * inv_tau;
+            mbj = -osbj * inv_tau;
+          } else {
+            mbi = osbj - osbi;
+            mbj = osbi - osbj;
+          }
+          f[i] = mu[i] + nbi + mbi;
+          f[j] = mu[j] + nbj + mbj;
+          const T Ebi = -nbi, Ebj = -nbj, Gbi = -mbi, Gbj = -mbj;
+          if constexpr (GEN)
+            rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + Gbi * phi<Q, T>(i, cs, usus) +
+                    Gbj * phi<Q, T>(j, -cs, usus);
+          else
+            rhob += Ebi * phi<Q, T>(i, cu, uu) + Ebj * phi<Q, T>(j, -cu, uu) + (Gbi + Gbj) * T(lat_w<Q>(i));
+          // d f^eq_i / d v = rho w_i (3 c_i + 9 (c_i.v) c_i - 3 v), and c_j = -c_i
+          const T rw = rho * T(lat_w<Q>(i));
+          const T ae = rw * (T(3) * (Ebi - Ebj) + T(9) * cu * (Ebi + Ebj)), be = T(-3) * rw * (Ebi + Ebj);
+          ubx += cx ? csign(cx, ae) + be * ux : be * ux;
+          uby += cy ? csign(cy, ae) + be * uy : be * uy;
+          ubz += cz ? csign(cz, ae) + be * uz : be * uz;
+          if constexpr (GEN) {
+            const T ag = rw * (T(3) * (Gbi - Gbj) + T(9) * cs * (Gbi + Gbj)), bg = T(-3) * rw * (Gbi + Gbj);
+            usbx += cx ? csign(cx, ag) + bg * usx : bg * usx;
+            usby += cy ? csign(cy, ag) + bg * usy : bg * usy;
+            usbz += cz ? csign(cz, ag) + bg * usz : bg * usz;
+          }
         }
-      }
-      grad[cell] = g_old + (double)(Bbar * Bp);
-      if (GEN && owner >= 0) {
-        // u_s = omega x r + v  =>  d/d omega = r x usbar
-        const double a = (double)usbx, b = (double)usby, c = (double)usbz;
-        aw0 = Ry * c - Rz * b;
-        aw1 = Rz * a - Rx * c;
-        aw2 = Rx * b - Ry * a;
-        has_w = true;
+        // u = j / rho
+        const T jbx = ubx * inv_rho, jby = uby * inv_rho, jbz = ubz * inv_rho;
+        rhob -= (ubx * ux + uby * uy + ubz * uz) * inv_rho;
+        // ---- lambda^n = fbar + drho/df rhobar + dj/df . jbar ----
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const T l = f[i] + rhob + cdot(i, jbx, jby, jbz);
+          static_cast<T*>(p.lout_slot[i])[cell] = l;
+          if (GEN && zg.from(lat_cz(i))) {
+            // the population is the ghost value g_i(u_in)
+            au0 += (double)l * p.dghost[i][0];
+            au1 += (double)l * p.dghost[i][1];
+            au2 += (double)l * p.dghost[i][2];
+            has_u = true;
+          }
+        }
+        grad[cell] = g_old + (double)(Bbar * Bp);
+        if (GEN && owner >= 0) {
+          // u_s = omega x r + v  =>  d/d omega = r x usbar
+          const double a = (double)usbx, b = (double)usby, c = (double)usbz;
+          aw0 = Ry * c - Rz * b;
+          aw1 = Rz * a - Rx * c;
+          aw2 = Rx * b - Ry * a;
+          has_w = true;
+        }
       }
       }
     }
