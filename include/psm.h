@@ -427,6 +427,16 @@ int psm_set_kernel_variant(psm_handle h, int variant);
 /* The variant psm_step uses now (PSM_KERNEL_PLAIN or PSM_KERNEL_TMA). */
 int psm_kernel_variant(psm_handle h, int* out);
 
+/* Diagnostics (host only, no GPU needed): the shared-memory layout the
+ * TMA-staged step kernel is built with for `storage`, `stencil`, `mode`
+ * (0 two-grid, 1 AA even step, 2 AA odd step) and `fluid`:
+ *   out[0] dynamic shared memory per block (bytes), out[1] pipeline stages,
+ *   out[2] resident blocks per SM it is sized for, out[3] cells per thread.
+ * The stages fill 228 KB per SM over out[2] blocks, less 1 KB reserved and
+ * 6 KB of static shared memory per block.  PSM_ERR_ARG for an unknown value,
+ * PSM_ERR_UNSUPPORTED for the cumulant operator on D3Q27. */
+int psm_tma_layout(int storage, int stencil, int mode, int fluid, int* out);
+
 #ifdef __cplusplus
 }
 #endif

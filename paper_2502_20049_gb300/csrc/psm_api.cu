@@ -1415,6 +1415,23 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   return PSM_OK;
 }
 
+int psm_tma_layout(int storage, int stencil, int mode, int fluid, int* out) {
+  if (!out) return fail(PSM_ERR_ARG, "psm_tma_layout: NULL out");
+  if (storage < PSM_FP64 || storage > PSM_BF16_SHIFTED) return fail(PSM_ERR_ARG, "bad storage");
+  if (stencil != PSM_D3Q19 && stencil != PSM_D3Q27) return fail(PSM_ERR_ARG, "bad stencil");
+  if (mode < psm::MODE_TG || mode > psm::MODE_AA_ODD) return fail(PSM_ERR_ARG, "bad mode");
+  if (fluid != PSM_BGK && fluid != PSM_TRT && fluid != PSM_CUMULANT) return fail(PSM_ERR_ARG, "bad fluid collision");
+  if (fluid == PSM_CUMULANT && stencil != PSM_D3Q19)
+    return fail(PSM_ERR_UNSUPPORTED, "the cumulant operator is D3Q19 only");
+  switch (storage) {
+    case PSM_FP64: psm::tma_layout_fp64(stencil, mode, fluid, out); break;
+    case PSM_FP32: psm::tma_layout_fp32(stencil, mode, fluid, out); break;
+    case PSM_FP16_SHIFTED: psm::tma_layout_fp16(stencil, mode, fluid, out); break;
+    default: psm::tma_layout_bf16(stencil, mode, fluid, out); break;
+  }
+  return PSM_OK;
+}
+
 int psm_set_kernel_variant(psm_handle h, int variant) {
   if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_set_kernel_variant: NULL handle");
   if (variant != PSM_KERNEL_AUTO && variant != PSM_KERNEL_PLAIN && variant != PSM_KERNEL_TMA)

@@ -217,6 +217,7 @@ cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, i
   cudaError_t launch_step_tma_##NAME(int Q, int mode, int fl, const StepParams& p, const TmaMaps& m, \
                                      cudaStream_t st);                                    \
   int tma_smem_bytes_##NAME(int Q, int mode, int fl);                                             \
+  void tma_layout_##NAME(int Q, int mode, int fl, int* out);                                      \
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_##NAME(int Q, const IoParams& p, cudaStream_t st);            \
   cudaError_t launch_export_raw_##NAME(int Q, const IoParams& p, cudaStream_t st);        \

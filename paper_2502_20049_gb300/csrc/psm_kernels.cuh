@@ -1678,6 +1678,27 @@ int tma_smem_q(int mode, int fl) {
   return tma_smem_f<S, Q, 0>(mode);
 }
 
+// dynamic shared memory, stages, resident blocks aimed at, cells per thread
+template <class L>
+void tma_layout_of(int* out) {
+  out[0] = L::SMEM;
+  out[1] = L::NST;
+  out[2] = L::BLOCKS;
+  out[3] = L::CPT;
+}
+template <class S, int Q, int FL>
+void tma_layout_f(int mode, int* out) {
+  if (mode == MODE_TG) tma_layout_of<TmaLayout<S, Q, MODE_TG, FL>>(out);
+  else if (mode == MODE_AA_EVEN) tma_layout_of<TmaLayout<S, Q, MODE_AA_EVEN, FL>>(out);
+  else tma_layout_of<TmaLayout<S, Q, MODE_AA_ODD, FL>>(out);
+}
+template <class S, int Q>
+void tma_layout_q(int mode, int fl, int* out) {
+  if constexpr (Q == 19)
+    if (fl == PSM_CUMULANT) return tma_layout_f<S, Q, 2>(mode, out);
+  tma_layout_f<S, Q, 0>(mode, out);
+}
+
 template <class S, int Q, int MODE>
 cudaError_t launch_step_m(int fl, const StepParams& p, cudaStream_t st) {
   if (fl == PSM_TRT) return launch_step_t<S, Q, MODE, 1>(p, st);
@@ -1716,6 +1737,10 @@ inline int io_grid(const IoParams& p) {
   }                                                                                                     \
   int tma_smem_bytes_##NAME(int Q, int mode, int fl) {                                                  \
     return Q == 19 ? tma_smem_q<S, 19>(mode, fl) : tma_smem_q<S, 27>(mode, fl);                         \
+  }                                                                                                     \
+  void tma_layout_##NAME(int Q, int mode, int fl, int* out) {                                           \
+    if (Q == 19) tma_layout_q<S, 19>(mode, fl, out);                                                    \
+    else tma_layout_q<S, 27>(mode, fl, out);                                                            \
   }                                                                                                     \
   cudaError_t launch_import_##NAME(int Q, const IoParams& p, cudaStream_t st) {                         \
     if (Q == 19) k_import<S, 19><<<io_grid(p), PSM_THREADS, 0, st>>>(p);                                \

@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
                 "psm_record": (i, [H, i, i]),
                 "psm_backward": (i, [H, vp, vp, vp, vp]),
                 "psm_kernel_variant": (i, [H, P(i)]),
+                "psm_tma_layout": (i, [i, i, i, i, P(i)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -176,6 +177,14 @@ def lattice_velocities(Q: int):
                                        w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                        opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
     return c.astype(np.int64), w, opp.astype(np.int64)
+
+
+def tma_layout(storage: str, Q: int, mode: int, fluid: str = "bgk") -> dict:
+    """Shared-memory layout of the TMA-staged step kernel (psm_tma_layout; host
+    only): mode 0 two-grid, 1 AA even, 2 AA odd."""
+    out = (ctypes.c_int * 4)()
+    check(lib().psm_tma_layout(STORAGE[storage], Q, mode, FLUID[fluid], out))
+    return dict(smem=out[0], stages=out[1], blocks_per_sm=out[2], cells_per_thread=out[3])
 
 
 class Geometry:

@@ -165,3 +165,29 @@ def test_mesh_voxeliser_rejects_bad_meshes(psm, case):
     with pytest.raises(psm.PSMError) as ei:
         psm.voxelize_mesh(v, t, s)
     assert ei.value.code == -1
+
+
+def test_tma_stage_budget(psm):
+    """The TMA step kernel's stages fit the shared memory of the resident blocks
+    it is sized for (228 KB per SM, 1 KB reserved and 6 KB of static shared
+    memory per block; at most 227 KB per block), for every storage, stencil,
+    streaming step and fluid operator; two cells per thread exactly for the
+    D3Q19 two-grid BGK/TRT step in 2-byte storage.  Host only."""
+    for storage in ("fp64", "fp32", "fp16", "bf16"):
+        for Q in (19, 27):
+            for mode in (0, 1, 2):
+                for fluid in ("bgk", "trt", "cumulant"):
+                    if fluid == "cumulant" and Q == 27:
+                        with pytest.raises(psm.PSMError) as ei:
+                            psm.tma_layout(storage, Q, mode, fluid)
+                        assert ei.value.code == -6
+                        continue
+                    L = psm.tma_layout(storage, Q, mode, fluid)
+                    key = (storage, Q, mode, fluid, L)
+                    assert 2 <= L["stages"] <= 8, key
+                    assert L["smem"] <= 227 * 1024, key
+                    assert L["blocks_per_sm"] * (L["smem"] + 1024 + 6144) <= 228 * 1024, key
+                    two = storage in ("fp16", "bf16") and Q == 19 and mode == 0 and fluid != "cumulant"
+                    assert L["cells_per_thread"] == (2 if two else 1), key
+    with pytest.raises(psm.PSMError):
+        psm.tma_layout("fp32", 15, 0, "bgk")
