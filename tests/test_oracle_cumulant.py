@@ -255,3 +255,34 @@ def test_rejects_unsupported(oracle_mod):
         O.Sim(O.Config(nx=2, ny=2, nz=2, Q=27, fluid=2))
     with pytest.raises(ValueError):
         O.Sim(O.Config(nx=2, ny=2, nz=2, Q=19, fluid=2, force=(1e-5, 0.0, 0.0)))
+
+
+def test_relaxation_property_random(oracle_mod):
+    """The definition check over random states and rates (hypothesis)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    O = oracle_mod
+    c, w, _ = O.lattice(19)
+
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
+    @hyp.given(rho=st.floats(0.85, 1.15), u=st.tuples(*[st.floats(-0.12, 0.12)] * 3), noise=st.floats(0.0, 0.02),
+               seed=st.integers(0, 2 ** 31 - 1), tau=st.floats(0.51, 2.0),
+               rates=st.tuples(*[st.floats(0.05, 1.95)] * 3))
+    def check(rho, u, noise, seed, tau, rates):
+        rng = np.random.default_rng(seed)
+        f = np.array([O.feq(19, i, rho, u) for i in range(19)]) + noise * rng.standard_normal(19) * w
+        post = collide(oracle_cell(O, tau=tau, rates=rates), f)
+        K, Kp = cumulants(c, f), cumulants(c, post)
+        ws, wb, w3, w4 = 1.0 / tau, rates[0], rates[1], rates[2]
+        tol = 1e-11
+        assert abs(post.sum() - f.sum()) < 1e-13
+        for e in OFFDIAG:
+            assert abs(Kp[e] - (1 - ws) * K[e]) < tol
+        tr, trp = K[2, 0, 0] + K[0, 2, 0] + K[0, 0, 2], Kp[2, 0, 0] + Kp[0, 2, 0] + Kp[0, 0, 2]
+        assert abs(trp - (tr + wb * (3 * CS2 - tr))) < tol
+        for e in THIRD:
+            assert abs(Kp[e] - (1 - w3) * K[e]) < tol
+        for e in FOURTH:
+            assert abs(Kp[e] - (1 - w4) * K[e]) < tol
+
+    check()
