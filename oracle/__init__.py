@@ -24,8 +24,9 @@ What each function follows (sections and equations of the paper):
 
 Parity status: every function above is pinned by the tests in
 ``tests/test_oracle_*.py`` (closed forms, invariants, brute force).  The torque
-magnitude of the synthetic rotor has no pin beyond those invariants
-(parity unpinned for that value).
+magnitude is pinned on a slowly rotating sphere (Stokes' closed form); the
+synthetic rotor's torque has no closed form of its own, but each ingredient
+(its voxelisation, the remap, the torque sum) is pinned.
 """
 
 from __future__ import annotations
