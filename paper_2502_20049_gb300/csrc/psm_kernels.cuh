@@ -525,8 +525,6 @@ __device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T
   const T rux = ml(rho, ux), ruy = ml(rho, uy), ruz = ml(rho, uz);
   const T k200 = sb(m200, fm(rux, ux, dt)), k020 = sb(m020, fm(ruy, uy, dt)), k002 = sb(m002, fm(ruz, uz, dt));
   const T k110 = sb(Mxy, ml(rux, uy)), k101 = sb(Mxz, ml(rux, uz)), k011 = sb(Myz, ml(ruy, uz));
-  const T r0t = ml(C.rho0, third);
-  const T M200 = ad(m200, r0t), M020 = ad(m020, r0t), M002 = ad(m002, r0t);  // full raw c_a^2 moments
   const T uxx = ml(ux, ux), uyy = ml(uy, uy), uzz = ml(uz, uz);
   const T s1 = C.cum1[0];
   const T inv_rho = recip(rho);
