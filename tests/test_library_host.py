@@ -191,3 +191,32 @@ def test_tma_stage_budget(psm):
                     assert L["cells_per_thread"] == (2 if two else 1), key
     with pytest.raises(psm.PSMError):
         psm.tma_layout("fp32", 15, 0, "bgk")
+
+
+@pytest.mark.parametrize("compiler,flags", [("gcc", ["-x", "c", "-std=c99"]), ("g++", ["-x", "c++", "-std=c++17"])])
+def test_header_is_plain_c(tmp_path, compiler, flags):
+    """include/psm.h compiles as strict C99 (and as C++): plain types, no C++ in the
+    ABI.  A translation unit fills the structs and takes the address of every
+    declared function (compile only, no GPU)."""
+    import shutil
+    import subprocess
+
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not available")
+    names = declared_functions()
+    src = ['#include "psm.h"', "typedef void (*fnp)(void);",
+           "static const fnp table[] = {" + ", ".join(f"(fnp){n}" for n in names) + "};",
+           "int psm_header_check(void) {",
+           "  psm_grid g = {64, 64, 64, PSM_BC_EQ_INLET_OUTLET, 1.0, {0.0, 0.0, 0.05}};",
+           "  psm_lattice l = {PSM_D3Q19, PSM_STREAM_AA, PSM_FP16_SHIFTED};",
+           "  psm_collision c = {PSM_CUMULANT, 0.6, 0.1875, PSM_SC1, PSM_B_TAU_WEIGHTED, {1.0, 1.0, 1.0}};",
+           "  psm_handle h = 0;",
+           "  (void)g; (void)l; (void)c; (void)h;",
+           "  return (int)(sizeof table / sizeof table[0]);",
+           "}"]
+    f = tmp_path / "check.c"
+    f.write_text("\n".join(src) + "\n")
+    out = subprocess.run([compiler] + flags + ["-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                                               os.path.join(ROOT, "include"), "-c", str(f), "-o",
+                                               str(tmp_path / "check.o")], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
