@@ -206,7 +206,11 @@ int psm_geom_free(psm_geom_field* field);
 /* Solver                                                                   */
 /* ------------------------------------------------------------------------ */
 
-/* Create a solver on the current CUDA device.  stream: a cudaStream_t (NULL =
+/* Create a solver on the current CUDA device: the lattice of Sec. 2.2
+ * (D3Q19 / D3Q27), the fluid collision Omega^F (BGK Eq. 2, TRT, or the
+ * cumulant operator Sec. 2.2 / Sec. 5.1), the solid collision Omega^S
+ * (Eq. 7/8/9) and the weighting B (Eq. 5 / Eq. 6) of the PSM update Eq. 4,
+ * and the inflow of Sec. 5.1's flow set-ups.  stream: a cudaStream_t (NULL =
  * the legacy default stream) on which every kernel of this handle runs.
  * Validates tau > 1/2, |u_in| < 0.3, rho0 > 0, trt_lambda > 0, the grid size
  * and the enum values (PSM_ERR_ARG), allocates the PDF buffer(s) and the
@@ -223,7 +227,11 @@ int psm_create(const psm_grid* grid, const psm_lattice* lattice, const psm_colli
  * them and they must outlive the handle.  flags: 0 initialises the state to
  * f^eq(rho0, u_in) like psm_create; PSM_BUFFERS_KEEP keeps buffers[0]'s
  * contents as the state at step 0.  PSM_ERR_ARG for NULL, misaligned or equal
- * buffers or unknown flags (before any CUDA call). */
+ * buffers or unknown flags (before any CUDA call), and for a buffer that is
+ * not device memory of the current device (or managed memory) or whose
+ * allocation ends before Q * ncell elements (checked with
+ * cudaPointerGetAttributes and the driver's address range, before any
+ * launch: a host pointer would fault the kernels). */
 #define PSM_BUFFERS_KEEP 1
 int psm_create_with_buffers(const psm_grid* grid, const psm_lattice* lattice, const psm_collision* collision,
                             void* stream, void* const* buffers, int flags, psm_handle* out);
@@ -267,8 +275,10 @@ int psm_get_macroscopic(psm_handle h, double* rho, double* u);
 int psm_get_eps(psm_handle h, float* eps);
 
 /* Attach body `body` (0 <= body < PSM_MAX_BODIES; bodies are used in id order
- * and must be set contiguously from 0).  The field is copied to the device
- * once.  Motion: pose at step n is Q_n = Rot(omega/|omega|, |omega| n) Q0
+ * and must be set contiguously from 0): the super-sampled binary geometry
+ * field of Sec. 3, voxelised once and copied to the device once; every step
+ * maps it onto eps through the body's pose (Sec. 3: the cell centre rotated
+ * into the body frame and translated).  Motion: pose at step n is Q_n = Rot(omega/|omega|, |omega| n) Q0
  * (Rodrigues), R_n = R0 + v n; Q0 is row-major world <- body; R0 is the
  * reference point (centre of rotation, torque reference).  Solid velocity
  * u_s(x) = omega x (x - R_n) + v.  Replacing a body is allowed. */
@@ -315,14 +325,17 @@ int psm_body_state(psm_handle h, int body, double* out);
 int psm_set_remap(psm_handle h, int every_step);
 
 /* Run n >= 0 time steps asynchronously on the handle's stream (one fused
- * kernel launch per step; no host synchronisation). */
+ * kernel launch per step; no host synchronisation).  One step is the pose and
+ * remap of Sec. 3, the PSM collision Eq. 4 (with Eq. 2/3, Eq. 5/6, Eq. 7-9),
+ * streaming Eq. 1 and the force/torque sums Eq. 10/11, in that order. */
 int psm_step(psm_handle h, int n);
 
 /* Step counter (steps taken since creation). */
 int psm_step_count(psm_handle h, int64_t* out);
 
 /* Force (3) and torque (3) on body `body` for steps [step_from, step_from +
- * count): out[count][6] (FP64).  Synchronises the stream.  Only the last
+ * count): out[count][6] (FP64), the negatives of Eq. 10 / Eq. 11 (the sums
+ * over the cells the body owns with B > 0, torque about R_n).  Synchronises the stream.  Only the last
  * psm_series_capacity() steps are kept (PSM_ERR_ARG for older steps).
  * PSM_ERR_NONFINITE if any returned value is NaN or infinite. */
 int psm_force_torque(psm_handle h, int body, int64_t step_from, int64_t count, double* out);
@@ -362,7 +375,8 @@ int psm_synchronize(psm_handle h);
  * [nz][ny][nx], host or device, copied; NULL removes it. */
 int psm_set_eps_delta(psm_handle h, const float* delta);
 
-/* Start recording the trajectory for psm_backward at the current step n0:
+/* Start recording the trajectory for psm_backward at the current step n0 (the
+ * forward map recorded is the step of psm_step: Sec. 3, Eq. 1-11):
  * the state is checkpointed now and before every K-th later step (device
  * memory, stream-ordered allocation), and the buffers of psm_backward are
  * allocated.  K = 0 stops recording and frees the checkpoints.  With AA
@@ -411,14 +425,28 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
  *   stencil: PSM_D3Q19 or PSM_D3Q27;  ncell: 1 .. 2^30 (PSM_ERR_ARG beyond:
  *            the scratch holds 16384 partial sums of 65536 cells each);
  *   stream:  cudaStream_t (NULL = legacy default stream);
- *   out:     one double, host or device; the call synchronises the stream.
- * The summation order is fixed (deterministic).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) for that
- * device; make that first call before any stream capture.  All calls share
- * the one array: calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller. */
+ *   out:     one double, host or device.
+ * The call synchronises `stream` before it returns (it reads the result back
+ * to the host to test it).  PSM_ERR_ARG if f is not device memory of the
+ * current device (or managed memory) holding Q * ncell values (checked before
+ * the launch).  The summation order is fixed (deterministic).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) for
+ * that device and keeps it for the life of the process (do not use the
+ * function across a cudaDeviceReset); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller. */
 int psm_mass_noalloc(const void* f, int storage, int stencil, int64_t ncell, double rho0, void* stream,
                      double* out);
+
+/* Host-side check of a caller-owned buffer (no counterpart in the paper; the
+ * check psm_create_with_buffers and psm_mass_noalloc make): PSM_OK when p
+ * points into device memory of the current device, or managed memory, and
+ * its allocation holds at least `bytes` bytes from p on (where the driver
+ * reports the allocation's extent); PSM_ERR_ARG otherwise, with the reason in
+ * psm_last_error() (host memory, another device's memory, too small).
+ * Launches nothing and allocates nothing. */
+int psm_check_device_buffer(const void* p, int64_t bytes);
 
 #define PSM_KERNEL_AUTO 0
 #define PSM_KERNEL_PLAIN 1

@@ -14,10 +14,11 @@
 //     Eq. 2/TRT/cumulant, Eq. 7-9, weighting Eq. 5/6 -> force/torque Eq. 10/11 ->
 //     streaming Eq. 1 with periodic x/y and either periodic z or equilibrium
 //     ghost planes in z;
-//   * all arithmetic in double (or Dual<double> for the tangent-linear model),
-//     except the body-frame transform of the remap, which is float with a fixed
-//     operation order (the precision in which the CUDA kernel decides the
-//     sub-cell index; the paper states none).
+//   * all arithmetic in double (or Dual<double> for the tangent-linear model);
+//     the remap's body-frame transform and sub-cell decision are double
+//     operations in the order written, each rounded on its own (the file is
+//     compiled without floating-point contraction; the paper states no
+//     precision for them).
 //
 // The scalar type is a template parameter so that the same code, run on
 // forward-mode dual numbers, gives exact directional derivatives (tangent-linear
@@ -343,35 +344,28 @@ Pose pose_at(const double Q0[9], const double R0[3], const double om[3], const d
 }
 
 // Sec. 3 remap for one body and one cell: transform the cell centre into the
-// body frame, X = Q_n^T (x_c - R_n) (float, fixed order, no contraction), take
-// the cube of 2^s x 2^s x 2^s sub-cells whose lower corner is the sub-grid
-// point nearest to X - 1/2, and average its bits (bits outside the stored box
-// are 0).
+// body frame, X = Q_n^T (x_c - R_n), take the cube of 2^s x 2^s x 2^s sub-cells
+// whose lower corner is the sub-grid point nearest to X - 1/2, and average its
+// bits (bits outside the stored box are 0).  In sub-cell units of the stored
+// box the corner sits at ((X - 1/2) - lo) 2^s, so the first sub-cell index per
+// axis is a0 = floor(((X - 1/2) - lo) 2^s + 1/2), evaluated in double in
+// exactly that order (no contraction).
 double remap_cell(const uint8_t* sub, int nsx, int nsy, int nsz, int s, const double lo[3],
                   const Pose& P, int x, int y, int z) {
-  float Qf[9], Rf[3], Cf[3];
-  for (int k = 0; k < 9; ++k) Qf[k] = (float)P.Q[k];
-  for (int k = 0; k < 3; ++k) { Rf[k] = (float)P.R[k]; Cf[k] = (float)(lo[k] + 0.5); }
   const int n = 1 << s;
-  float xc[3] = {(float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f};
-  float d[3];
-  for (int k = 0; k < 3; ++k) d[k] = xc[k] - Rf[k];
-  int a0[3];
+  const double xc[3] = {double(x) + 0.5, double(y) + 0.5, double(z) + 0.5};
+  double d[3];
+  for (int k = 0; k < 3; ++k) d[k] = xc[k] - P.R[k];
+  long a0[3];
   for (int k = 0; k < 3; ++k) {
-    // column k of Q (world <- body) gives row k of Q^T
-    float p0 = Qf[0 * 3 + k] * d[0];
-    float p1 = Qf[1 * 3 + k] * d[1];
-    float p2 = Qf[2 * 3 + k] * d[2];
-    float X = (p0 + p1) + p2;
-    float t = X - Cf[k];
-    float q = t * (float)n;
-    float r = q + 0.5f;
-    a0[k] = (int)std::floor(r);
+    // column k of Q (world <- body) is row k of Q^T
+    const double X = (P.Q[0 * 3 + k] * d[0] + P.Q[1 * 3 + k] * d[1]) + P.Q[2 * 3 + k] * d[2];
+    a0[k] = (long)std::floor(((X - 0.5) - lo[k]) * double(n) + 0.5);
   }
   long count = 0;
-  for (int az = a0[2]; az < a0[2] + n; ++az)
-    for (int ay = a0[1]; ay < a0[1] + n; ++ay)
-      for (int ax = a0[0]; ax < a0[0] + n; ++ax) {
+  for (long az = a0[2]; az < a0[2] + n; ++az)
+    for (long ay = a0[1]; ay < a0[1] + n; ++ay)
+      for (long ax = a0[0]; ax < a0[0] + n; ++ax) {
         if (ax < 0 || ay < 0 || az < 0 || ax >= nsx || ay >= nsy || az >= nsz) continue;
         count += sub[((long)az * nsy + ay) * nsx + ax];
       }

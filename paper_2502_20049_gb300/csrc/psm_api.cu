@@ -149,6 +149,58 @@ namespace psm {
 
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+namespace {
+using MemRangeFn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+// cuMemGetAddressRange through the runtime's driver entry points (nullptr if
+// the driver does not provide it)
+MemRangeFn mem_range_fn() {
+  static MemRangeFn fn = [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &ptr, 3020, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      ptr = nullptr;
+    }
+    return reinterpret_cast<MemRangeFn>(ptr);
+  }();
+  return fn;
+}
+}  // namespace
+
+int check_device_buffer(const void* p, size_t bytes, const char* what) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PSM_ERR_ARG, "%s: cannot tell whether it is device memory (%s)", what, cudaGetErrorString(e));
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(PSM_ERR_ARG, "%s: not device memory (%s)", what,
+                a.type == cudaMemoryTypeHost ? "page-locked host memory" : "host memory");
+  int dev = -1;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PSM_ERR_ARG, "%s: no current device (%s)", what, cudaGetErrorString(e));
+  }
+  if (a.type == cudaMemoryTypeDevice && a.device != dev)
+    return fail(PSM_ERR_ARG, "%s: memory of device %d, the current device is %d", what, a.device, dev);
+  if (MemRangeFn fn = mem_range_fn()) {
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, (CUdeviceptr)(uintptr_t)p) == CUDA_SUCCESS) {
+      const unsigned long long q = (unsigned long long)(uintptr_t)p, b0 = (unsigned long long)base;
+      if (q < b0 || q - b0 > size || size - (q - b0) < bytes)
+        return fail(PSM_ERR_ARG, "%s: %llu bytes needed, its allocation holds %llu bytes from this address", what,
+                    (unsigned long long)bytes, (unsigned long long)(q >= b0 && q - b0 <= size ? size - (q - b0) : 0));
+    } else {
+      cudaGetLastError();
+    }
+  }
+  return PSM_OK;
+}
+
 void set_slots(StepParams& p, int storage, int Q) {
   const size_t b = storage == PSM_FP64 ? 8 : (storage == PSM_FP32 ? 4 : 2);
   char* src = static_cast<char*>(p.f);
@@ -265,8 +317,8 @@ cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, i
 // (thread b), from this step's force and torque on the body ft[b][6]:
 //   v += (F + Fext) / m,  R += v,  L += T + Text,
 //   Q <- Rot(w*) Q, w* = Q Ib^-1 Q^T L,  w = Q Ib^-1 Q^T L,
-// then the DevBody of the next step (pose rounded to float for the remap,
-// kinematics, the cell box of the rotated geometry box widened by 2.5 cells).
+// then the DevBody of the next step (kinematics, the cell box of the rotated
+// geometry box widened by 2.5 cells, the remap's pose and its float form).
 __device__ void q_ibinv_qt(const double* Q, const double* Ibinv, const double* L, double* w) {
   double a[3], b[3];
   for (int i = 0; i < 3; ++i) a[i] = Q[i] * L[0] + Q[3 + i] * L[1] + Q[6 + i] * L[2];
@@ -301,7 +353,6 @@ __global__ void k_body_update(BodyDyn* dyn, DevBody* dev, const double* ft, unsi
   }
   q_ibinv_qt(S.Q, S.Ibinv, S.L, S.w);
   DevBody& d = dev[b];
-  for (int k = 0; k < 9; ++k) d.Qf[k] = (float)S.Q[k];
   for (int k = 0; k < 3; ++k) {
     d.Rf[k] = (float)S.R[k];
     d.R[k] = S.R[k];
@@ -337,6 +388,7 @@ __global__ void k_body_update(BodyDyn* dyn, DevBody* dev, const double* ft, unsi
   d.y1 = hi_[1];
   d.z0 = lo_[2];
   d.z1 = hi_[2];
+  remap_setup(d, S.Q, S.R, S.lo);
 }
 
 cudaError_t launch_body_update(BodyDyn* dyn, DevBody* dev, const double* ft, unsigned mask, int nb, int nx, int ny,
@@ -390,10 +442,8 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
   d.gz = (int)b.gz;
   d.s = b.s;
   d.wpb = b.wpb;
-  for (int k = 0; k < 9; ++k) d.Qf[k] = (float)Q[k];
   for (int k = 0; k < 3; ++k) {
     d.Rf[k] = (float)R[k];
-    d.Cf[k] = (float)(b.lo[k] + 0.5);
     d.R[k] = R[k];
     d.omega[k] = b.omega[k];
     d.v[k] = b.v[k];
@@ -427,6 +477,7 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
   d.y1 = hi_[1];
   d.z0 = lo_[2];
   d.z1 = hi_[2];
+  psm::remap_setup(d, Q, R, b.lo);
   return d;
 }
 
@@ -701,6 +752,17 @@ int create_impl(const psm_grid* grid, const psm_lattice* lattice, const psm_coll
   if (collision->weighting != PSM_B_DIRECT && collision->weighting != PSM_B_TAU_WEIGHTED)
     return fail(PSM_ERR_ARG, "bad weighting");
 
+  if (user_bufs) {
+    // caller-owned buffers: device memory of the current device, large enough,
+    // checked before any launch (a host pointer would fault the kernels)
+    const size_t need = (size_t)lattice->stencil * (size_t)grid->nx * (size_t)grid->ny * (size_t)grid->nz *
+                        storage_bytes(lattice->storage);
+    const int nb = lattice->streaming == PSM_STREAM_TWO_GRID ? 2 : 1;
+    for (int b = 0; b < nb; ++b) {
+      const int rc = psm::check_device_buffer(user_bufs[b], need, b == 0 ? "PDF buffer 0" : "PDF buffer 1");
+      if (rc != PSM_OK) return rc;
+    }
+  }
   psm_solver* h = new (std::nothrow) psm_solver();
   if (!h) return fail(PSM_ERR_OOM, "host allocation failed");
   h->grid = *grid;
@@ -789,6 +851,12 @@ int psm_create_with_buffers(const psm_grid* grid, const psm_lattice* lattice, co
   }
   if (nbuf == 2 && buffers[0] == buffers[1]) return fail(PSM_ERR_ARG, "the two PDF buffers must differ");
   return create_impl(grid, lattice, collision, stream, buffers, (flags & PSM_BUFFERS_KEEP) != 0, out);
+}
+
+int psm_check_device_buffer(const void* p, int64_t bytes) {
+  if (!p) return fail(PSM_ERR_ARG, "psm_check_device_buffer: NULL pointer");
+  if (bytes < 0) return fail(PSM_ERR_ARG, "psm_check_device_buffer: negative size");
+  return psm::check_device_buffer(p, (size_t)bytes, "buffer");
 }
 
 int psm_destroy(psm_handle h) {

@@ -54,10 +54,21 @@ struct DevBody {
   int gx, gy, gz;
   int s;    // super-sampling depth
   int wpb;  // 64-bit words per brick
-  // pose of this step, rounded to float: the remap decides sub-cell indices in float
-  float Qf[9];  // world <- body, row-major
-  float Rf[3];  // reference point R_n
-  float Cf[3];  // lo + 1/2
+  // Pose of this step for the remap (Sec. 3).  The sub-cell block of a cell
+  // starts at a0_k = floor(((X_k - 1/2) - lo_k) 2^s + 1/2), X = Q^T (x_c - R),
+  // evaluated in double with separately rounded operations in that order.
+  // The kernels decide it from the float form below and fall back to that
+  // double evaluation for cells whose float value lies within rtol of a
+  // decision boundary (remap_setup, remap_eps).
+  double Qd[9];  // world <- body, row-major
+  double lod[3];  // geometry box origin (body frame)
+  // r_k = sum_j G_jk e_j + H_k with e = x - anchor, G = 2^s Q and H a constant
+  // of the pose; the high parts are exact in float for every cell of the box
+  float Ghi[9], Glo[9];  // [j * 3 + k]
+  float Hhi[3], Hlo[3];
+  int anchor[3];
+  float rtol;     // bound on |r_float - r_double| over the box (2: always double)
+  float Rf[3];    // reference point R_n rounded to float (FP32 lever arm)
   // kinematics in double (FP64 path, force/torque lever arm) and float (FP32 path)
   double R[3];
   double omega[3];
@@ -67,6 +78,67 @@ struct DevBody {
   // cells tested for this body: [x0, x1) x [y0, y1) x [z0, z1)
   int x0, x1, y0, y1, z0, z1;
 };
+
+// Float form of the remap's sub-cell decision for the pose (Q, R) of one
+// body and its bound, for the cells of the box [x0, x1) x [y0, y1) x [z0, z1)
+// set in d.  With an anchor cell a of the box, e = x - a and c = a + 1/2 - R,
+//   r_k = ((X_k - 1/2) - lo_k) 2^s + 1/2 = sum_j G_jk e_j + H_k,
+//   G = 2^s Q,  H_k = ((sum_j Q_jk c_j - 1/2) - lo_k) 2^s + 1/2.
+// G and H split into high parts on the grid 2^-m and float low parts; m is
+// the finest grid on which |H_hi| + sum_j |G_hi,jk| |e_j| stays below 2^(24-m)
+// over the box, so that every product and partial sum of the high parts is a
+// float exactly.  rtol bounds (twice, plus one float rounding of the distance
+// test) the first-order errors of the float evaluation (rounding of G_lo and
+// H_lo, three fma roundings of the low sum, one of the final add), of the
+// double evaluation against exact arithmetic, and of H itself.
+__host__ __device__ inline void remap_setup(DevBody& d, const double Q[9], const double R[3], const double lo[3]) {
+  const double n = (double)(1 << d.s);
+  const double U = 5.9604644775390625e-08;    // 2^-24, float unit round-off
+  const double Ud = 1.1102230246251565e-16;   // 2^-53, double unit round-off
+  const int b0[3] = {d.x0, d.y0, d.z0}, b1[3] = {d.x1, d.y1, d.z1};
+  double Be = 0.0, Bd = 0.0, lom = 0.0;  // sum_j max |e_j|, sum_j max |x_j + 1/2 - R_j|, max |lo_k|
+  for (int j = 0; j < 3; ++j) {
+    const int last = b1[j] > b0[j] ? b1[j] - 1 : b0[j];
+    d.anchor[j] = b0[j] + (last - b0[j]) / 2;
+    Be += fmax(fabs((double)(b0[j] - d.anchor[j])), fabs((double)(last - d.anchor[j])));
+    Bd += fmax(fabs((double)b0[j] + 0.5 - R[j]), fabs((double)last + 0.5 - R[j]));
+    lom = fmax(lom, fabs(lo[j]));
+  }
+  for (int k = 0; k < 9; ++k) d.Qd[k] = Q[k];
+  double H[3], Hmax = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    d.lod[k] = lo[k];
+    double X = 0.0;
+    for (int j = 0; j < 3; ++j) X += Q[3 * j + k] * (((double)d.anchor[j] + 0.5) - R[j]);
+    H[k] = ((X - 0.5) - lo[k]) * n + 0.5;
+    Hmax = fmax(Hmax, fabs(H[k]));
+  }
+  const double span = (Hmax + 1.0) + (n + 1.0) * Be;
+  int m = 20;
+  while (m >= 0 && span * (double)(1 << m) >= 16777216.0) --m;
+  if (m < 0 || !(span < 1e30)) {  // no exact float form: every cell takes the double decision
+    for (int k = 0; k < 9; ++k) d.Ghi[k] = d.Glo[k] = 0.0f;
+    for (int k = 0; k < 3; ++k) d.Hhi[k] = d.Hlo[k] = 0.0f;
+    d.rtol = 2.0f;  // above any distance to the nearest integer (<= 1/2)
+    return;
+  }
+  const double sc = (double)(1 << m), isc = 1.0 / sc;
+  for (int k = 0; k < 9; ++k) {
+    const double G = Q[k] * n;                     // exact (power of two)
+    const double gh = floor(G * sc + 0.5) * isc;   // on the grid 2^-m, |gh| 2^m < 2^24
+    d.Ghi[k] = (float)gh;
+    d.Glo[k] = (float)(G - gh);
+  }
+  for (int k = 0; k < 3; ++k) {
+    const double hh = floor(H[k] * sc + 0.5) * isc;
+    d.Hhi[k] = (float)hh;
+    d.Hlo[k] = (float)(H[k] - hh);
+  }
+  const double L = 0.5 * isc * (1.0 + Be);                  // bound on |low sum| and its partials
+  const double ef = U * 0.5 * isc * (1.0 + Be) + 3.0 * U * L + U * (1.0 + L);
+  const double ed = n * Ud * (7.0 * Bd + 3.0 * lom + 2.0) + Ud;  // double evaluation vs exact
+  d.rtol = (float)(2.0 * (ef + 2.0 * ed) + U);
+}
 
 // State of a body moving under the fluid's force and torque (two-way
 // coupling), integrated on the device after every step (FP64).
@@ -185,6 +257,12 @@ struct RemapParams {
 };
 
 constexpr int PSM_THREADS = 256;
+
+// Caller-owned memory: PSM_OK when p points into device memory of the current
+// device (or managed memory) with at least `bytes` bytes from p to the end of
+// its allocation (the allocation's extent is checked where the driver reports
+// it); otherwise PSM_ERR_ARG with a message naming `what`.  Launches nothing.
+int check_device_buffer(const void* p, size_t bytes, const char* what);
 
 Tiling make_tiling(int nx, int ny, int nz);
 // fills p.src_slot / p.dst_slot from p.f, p.f_dst (nullptr: in place), p.g.ncell

@@ -81,29 +81,56 @@ struct Store<__nv_bfloat16> {
 
 // ---------------------------------------------------------------------------
 // Remap of one body onto one cell (Sec. 3).  The cell centre is taken into the
-// body frame, X = Q_n^T (x_c - R_n), in float with a fixed order of separately
-// rounded operations; the 2^s sub-cells per axis whose block starts at the
-// sub-grid point nearest to X - 1/2 are counted in the brick-packed field.
+// body frame, X = Q_n^T (x_c - R_n); the 2^s sub-cells per axis whose block
+// starts at the sub-grid point nearest to X - 1/2 are counted in the
+// brick-packed field.  The start index a0_k = floor(r_k),
+// r_k = ((X_k - 1/2) - lo_k) 2^s + 1/2, is the double evaluation of r_k with
+// separately rounded operations in that order.  The kernel evaluates r_k in
+// float from the exact-split affine form of remap_setup (high part exact, low
+// part within rtol of the double value); a cell whose float r_k lies within
+// rtol of an integer on some axis takes the double evaluation itself, so the
+// decision always equals the double one (the fallback is rare: rtol is a few
+// float round-offs, so about 6 rtol of the cells in a body's box take it).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long low_bits(int w) { return w >= 64 ? ~0ull : ((1ull << w) - 1ull); }
+
+static __device__ __noinline__ int3 remap_start_double(const DevBody& b, int x, int y, int z) {
+  const double n = (double)(1 << b.s);
+  const double xc[3] = {(double)x + 0.5, (double)y + 0.5, (double)z + 0.5};
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = __dsub_rn(xc[k], b.R[k]);
+  int a0[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double X = __dadd_rn(__dadd_rn(__dmul_rn(b.Qd[k], d[0]), __dmul_rn(b.Qd[3 + k], d[1])),
+                               __dmul_rn(b.Qd[6 + k], d[2]));
+    a0[k] = (int)floor(__dadd_rn(__dmul_rn(__dsub_rn(__dsub_rn(X, 0.5), b.lod[k]), n), 0.5));
+  }
+  return make_int3(a0[0], a0[1], a0[2]);
+}
 
 __device__ __forceinline__ float remap_eps(const DevBody& b, int x, int y, int z) {
   const int s = b.s;
   const int n = 1 << s;
-  const float xc[3] = {__fadd_rn((float)x, 0.5f), __fadd_rn((float)y, 0.5f), __fadd_rn((float)z, 0.5f)};
-  float d[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) d[k] = __fsub_rn(xc[k], b.Rf[k]);
+  const float e0 = (float)(x - b.anchor[0]), e1 = (float)(y - b.anchor[1]), e2 = (float)(z - b.anchor[2]);
   int a0[3];
+  bool near = false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float p0 = __fmul_rn(b.Qf[0 * 3 + k], d[0]);
-    const float p1 = __fmul_rn(b.Qf[1 * 3 + k], d[1]);
-    const float p2 = __fmul_rn(b.Qf[2 * 3 + k], d[2]);
-    const float X = __fadd_rn(__fadd_rn(p0, p1), p2);
-    const float t = __fsub_rn(X, b.Cf[k]);
-    const float q = __fmul_rn(t, (float)n);
-    a0[k] = (int)floorf(__fadd_rn(q, 0.5f));
+    const float hi = __fmaf_rn(b.Ghi[6 + k], e2, __fmaf_rn(b.Ghi[3 + k], e1, __fmaf_rn(b.Ghi[k], e0, b.Hhi[k])));
+    const float lo = __fmaf_rn(b.Glo[6 + k], e2, __fmaf_rn(b.Glo[3 + k], e1, __fmaf_rn(b.Glo[k], e0, b.Hlo[k])));
+    const float fh = floorf(hi);
+    const float v = __fadd_rn(__fsub_rn(hi, fh), lo);  // hi - fh is exact
+    const float fv = floorf(v);
+    a0[k] = (int)fh + (int)fv;
+    near = near || fminf(__fsub_rn(v, fv), __fsub_rn(__fadd_rn(fv, 1.0f), v)) <= b.rtol;
+  }
+  if (near) {
+    const int3 a = remap_start_double(b, x, y, z);
+    a0[0] = a.x;
+    a0[1] = a.y;
+    a0[2] = a.z;
   }
   // per axis up to two coarse cells: [o, n) of g and [0, o) of g + 1
   int gc[3], o[3];

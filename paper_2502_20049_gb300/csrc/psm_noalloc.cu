@@ -21,6 +21,7 @@ constexpr int NOALLOC_MAX_BLOCKS = 16384;       // 16384 * 65536 = 2^30 cells at
 // int).  Every GPU that loads the library holds this array (128 KB + 16 B)
 // until the process exits.
 constexpr int NOALLOC_SCRATCH_DOUBLES = NOALLOC_MAX_BLOCKS + 2;
+static_assert(NOALLOC_SCRATCH_DOUBLES == NOALLOC_MAX_BLOCKS + 2, "partials, the result and the ticket");
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
 struct NoAllocScratch {
@@ -110,6 +111,11 @@ extern "C" int psm_mass_noalloc(const void* f, int storage, int stencil, int64_t
     return set_error(PSM_ERR_ARG,
                      "psm_mass_noalloc: ncell exceeds the static scratch limit of 2^30 cells "
                      "(16384 block partials of 65536 cells)");
+  const int bytes = storage == PSM_FP64 ? 8 : (storage == PSM_FP32 ? 4 : 2);
+  // f must be device memory of the current device holding Q * ncell values: a
+  // host pointer would fault the kernel
+  int rc = check_device_buffer(f, (size_t)stencil * (size_t)ncell * (size_t)bytes, "psm_mass_noalloc: f");
+  if (rc != PSM_OK) return rc;
   NoAllocScratch scr;
   cudaError_t e = scratch_for_current_device(&scr);
   if (e != cudaSuccess) {
@@ -117,25 +123,43 @@ extern "C" int psm_mass_noalloc(const void* f, int storage, int stencil, int64_t
     return set_error(PSM_ERR_CUDA, "psm_mass_noalloc: cannot resolve the static scratch address");
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int blocks = (int)((ncell + NOALLOC_CELLS_PER_BLOCK - 1) / NOALLOC_CELLS_PER_BLOCK);
+  const long long blocks = (ncell + NOALLOC_CELLS_PER_BLOCK - 1) / NOALLOC_CELLS_PER_BLOCK;
+  // one partial per block: the array holds NOALLOC_MAX_BLOCKS of them
+  if (blocks > NOALLOC_MAX_BLOCKS) return set_error(PSM_ERR_ARG, "psm_mass_noalloc: too many blocks for the scratch");
   // the ticket must start at zero (the last block also resets it)
   e = cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) {
     switch (storage) {
-      case PSM_FP64: e = launch_noalloc<double>(stencil, f, ncell, rho0, scr, blocks, st); break;
-      case PSM_FP32: e = launch_noalloc<float>(stencil, f, ncell, rho0, scr, blocks, st); break;
-      case PSM_FP16_SHIFTED: e = launch_noalloc<__half>(stencil, f, ncell, rho0, scr, blocks, st); break;
-      default: e = launch_noalloc<__nv_bfloat16>(stencil, f, ncell, rho0, scr, blocks, st); break;
+      case PSM_FP64: e = launch_noalloc<double>(stencil, f, ncell, rho0, scr, (int)blocks, st); break;
+      case PSM_FP32: e = launch_noalloc<float>(stencil, f, ncell, rho0, scr, (int)blocks, st); break;
+      case PSM_FP16_SHIFTED: e = launch_noalloc<__half>(stencil, f, ncell, rho0, scr, (int)blocks, st); break;
+      default: e = launch_noalloc<__nv_bfloat16>(stencil, f, ncell, rho0, scr, (int)blocks, st); break;
     }
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, scr.result, sizeof(double), cudaMemcpyDefault, st);
+  // the result is read once, on `stream`, into a host local; it is tested
+  // there and then written to out (a host store, or one more copy on `stream`
+  // when out is device memory)
+  double v = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, scr.result, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(PSM_ERR_CUDA, "psm_mass_noalloc: kernel or copy failed");
   }
-  double v = 0.0;
-  if (cudaMemcpy(&v, scr.result, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess && !std::isfinite(v))
-    return set_error(PSM_ERR_NONFINITE, "psm_mass_noalloc: the sum is NaN or Inf");
+  cudaPointerAttributes a;
+  const bool out_dev = cudaPointerGetAttributes(&a, out) == cudaSuccess &&
+                       (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  if (out_dev) {
+    e = cudaMemcpyAsync(out, &v, sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(PSM_ERR_CUDA, "psm_mass_noalloc: copy of the result failed");
+    }
+  } else {
+    *out = v;
+  }
+  if (!std::isfinite(v)) return set_error(PSM_ERR_NONFINITE, "psm_mass_noalloc: the sum is NaN or Inf");
   return PSM_OK;
 }

@@ -123,6 +123,8 @@ def lib() -> ctypes.CDLL:
                 "psm_backward": (i, [H, vp, vp, vp, vp]),
                 "psm_kernel_variant": (i, [H, P(i)]),
                 "psm_tma_layout": (i, [i, i, i, i, P(i)]),
+                "psm_check_device_buffer": (i, [vp, i64]),
+                "psm_mass_noalloc": (i, [vp, i, i, i64, d, vp, P(d)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -130,6 +132,13 @@ def lib() -> ctypes.CDLL:
                 fn.argtypes = args
             _LIB = L
     return _LIB
+
+
+def check_device_buffer(ptr: int, nbytes: int) -> tuple[int, str]:
+    """psm_check_device_buffer: (status, message) for a raw pointer and a size
+    in bytes (status 0 = device memory of the current device, large enough)."""
+    rc = lib().psm_check_device_buffer(ctypes.c_void_p(ptr), int(nbytes))
+    return rc, (lib().psm_last_error() or b"").decode() if rc else ""
 
 
 def check(rc: int):

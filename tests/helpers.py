@@ -50,13 +50,22 @@ def ft_err(a, b, lever=1.0):
     components relative to the largest |F| of b, and max |dT| relative to
     max(largest |T| of b, largest |F| of b x a lever arm of `lever` cells), so
     that components that vanish by symmetry are compared at the scale of the
-    ones that do not."""
+    ones that do not.  The torque about z (the one the adjoint's J is built on)
+    is also compared at its own scale, max |dT_z| / max |T_z| of b, wherever it
+    is at least a tenth of the largest torque component of that body in b."""
     fa, fb = np.asarray(a["ft"]), np.asarray(b["ft"])
     sF = np.abs(fb[..., :3]).max()
     sT = max(np.abs(fb[..., 3:]).max(), sF * lever)
     eF = np.abs(fa[..., :3] - fb[..., :3]).max() / max(sF, 1e-300)
     eT = np.abs(fa[..., 3:] - fb[..., 3:]).max() / max(sT, 1e-300)
-    return max(eF, eT)
+    eTz = 0.0
+    ta, tb = fa.reshape(-1, fa.shape[-2], 6) if fa.ndim == 3 else fa[:, None], \
+        fb.reshape(-1, fb.shape[-2], 6) if fb.ndim == 3 else fb[:, None]
+    for body in range(tb.shape[1]):
+        sTz = np.abs(tb[:, body, 5]).max()
+        if sTz > 0 and sTz >= 0.1 * np.abs(tb[:, body, 3:]).max():
+            eTz = max(eTz, np.abs(ta[:, body, 5] - tb[:, body, 5]).max() / sTz)
+    return max(eF, eT, eTz)
 
 
 def assert_ft_same(fa, fb, storage):

@@ -165,3 +165,52 @@ def test_force_torque_raw_is_the_printed_sign():
     ft = s.force_torque(0)
     assert np.abs(ft).max() > 0
     assert np.array_equal(s.force_torque_raw(0), -ft)
+
+
+def test_device_buffer_check_classifies_memory():
+    """psm_check_device_buffer (host only, launches nothing): host and
+    page-locked host memory are refused, device memory of the current device
+    is accepted, and a size beyond the allocation is refused."""
+    import torch
+
+    from paper_2502_20049_gb300 import psm
+
+    a = np.zeros(1000)
+    rc, msg = psm.check_device_buffer(a.ctypes.data, a.nbytes)
+    assert rc == -1 and "host memory" in msg, msg
+    p = torch.zeros(1000, dtype=torch.float64, pin_memory=True)
+    rc, msg = psm.check_device_buffer(p.data_ptr(), 8000)
+    assert rc == -1 and "page-locked" in msg, msg
+    d = torch.zeros(1000, dtype=torch.float64, device="cuda")
+    assert psm.check_device_buffer(d.data_ptr(), 8000)[0] == 0
+    rc, msg = psm.check_device_buffer(d.data_ptr(), 1 << 40)
+    assert rc == -1 and "bytes needed" in msg, msg
+
+
+def test_entry_points_refuse_host_and_short_buffers():
+    """psm_create_with_buffers and psm_mass_noalloc refuse host memory and a
+    device allocation shorter than Q * ncell values with PSM_ERR_ARG before
+    any launch.  Each pointer is first shown to be refused by the check alone,
+    so no kernel ever sees it."""
+    import ctypes
+
+    import torch
+
+    from paper_2502_20049_gb300 import psm
+
+    cfg = psm.SolverConfig(64, 64, 64, streaming="twogrid", storage="fp32")
+    need = 19 * 64 ** 3 * 4
+    host = [np.zeros(19 * 64 ** 3, dtype=np.float32) for _ in range(2)]
+    short = [torch.zeros(16, dtype=torch.float32, device="cuda") for _ in range(2)]
+    for ptrs, why in (([h.ctypes.data for h in host], "host memory"), ([t.data_ptr() for t in short], "bytes needed")):
+        for q in ptrs:
+            rc, msg = psm.check_device_buffer(q, need)
+            assert rc == -1 and why in msg, msg
+        with pytest.raises(psm.PSMError) as ei:
+            psm.Solver(cfg, buffers=ptrs)
+        assert ei.value.code == -1 and why in str(ei.value)
+        out = ctypes.c_double(3.0)
+        rc = psm.lib().psm_mass_noalloc(ctypes.c_void_p(ptrs[0]), psm.STORAGE["fp32"], 19, 64 ** 3, 1.0, None,
+                                        ctypes.byref(out))
+        assert rc == -1 and out.value == 3.0
+        assert why.encode() in psm.lib().psm_last_error()

@@ -6,8 +6,9 @@ Tolerances (velocity: max |u_gpu - u_oracle| / |u_in|):
   FP32                            <= 2e-5   (force/torque <= 1e-4 relative),
   FP16 shifted storage            <= 2e-3,
   BF16 shifted storage            reported (no bar), must stay finite.
-eps (Sec. 3) is compared bit for bit: both sides take the sub-cell decision in
-the same float arithmetic.
+eps (Sec. 3) is compared bit for bit: the kernel's sub-cell decision equals
+the oracle's double evaluation (the kernel re-evaluates it in double wherever
+its float estimate cannot decide).
 """
 
 import numpy as np
@@ -89,11 +90,14 @@ def test_eps_bitwise_every_step():
     from helpers import oracle_sim
 
     sim = oracle_sim(case)
+    mism = 0
     for n in range(0, 40):
         e_gpu = sol.eps()
         e_or, _ = sim.eps(n)
-        assert np.array_equal(e_gpu.astype(np.float64), e_or), n
+        mism += int((e_gpu.astype(np.float64) != e_or).sum())
         sol.step(1)
+    print(f"eps over 40 steps of the rotating ellipsoid: {mism} cells differ from the oracle's double decision")
+    assert mism == 0
     assert e_or.sum() > 10
 
 

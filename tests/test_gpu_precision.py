@@ -1,0 +1,115 @@
+"""Error of each storage precision against the FP64 oracle, field by field.
+
+PDFs stored in FP32, or shifted (f_i - w_i rho0) in FP16 / BF16, with the
+collision arithmetic in FP32 and the force/torque and mass sums in FP64, are
+run beside the oracle on two workloads: the rotating ellipsoid of the D3Q19
+TRT benchmark reduced to 64^3, and a D3Q27 BGK proxy of the counter-rotating
+rotor (96 x 96 x 120, rotor x0.2, turned at +-0.01 rad/step so that eps
+changes every few steps).  Reported per field:
+
+  rho      max |rho - rho_oracle| / rho0
+  u        max |u - u_oracle| / |u_in|            (the stated bars)
+  f~       max |f~ - f~_oracle| / max |f~_oracle|  (shifted PDFs)
+  F, T     max |dF| / max |F|, max |dT| / max |T|  (force/torque series)
+  T_z      max |dT_z| / max |T_z|                  (the torque J is built on)
+  mass     |M_N - M_0| / M_0 after the same steps on a periodic box
+
+Bars: velocity FP32 2e-5, FP16 2e-3, BF16 2e-2; force and torque (T_z on its
+own scale) 1e-4 for FP32.  The table is printed (run with -s).
+"""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+from helpers import perm_lib_to_oracle, run_gpu, run_oracle, u_err
+from paper_2502_20049_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U_BAR = {"fp32": 2e-5, "fp16": 2e-3, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+
+    g.build()
+
+
+def workload(name):
+    if name == "c2_64":
+        return W.c2_ellipsoid(scale=0.25, n=64, steps=200, omega_z=0.01).with_(streaming="aa")
+    case = W.c3_rotor("fp32", scale=0.2, dims=(96, 96, 120), steps=120).with_(streaming="aa")
+    bodies = [dataclasses.replace(b, omega=(0.0, 0.0, 0.01 * np.sign(b.omega[2]))) for b in case.bodies]
+    return case.with_(bodies=bodies)
+
+
+_ORACLE = {}
+
+
+def oracle_run(name, periodic=False):
+    key = (name, periodic)
+    if key not in _ORACLE:
+        case = workload(name)
+        if periodic:
+            case = case.with_(bc_z=0)
+        o = run_oracle(case)
+        if periodic:
+            sim = o["sim"]
+            o = {"mass": float(np.sum(sim.get_f()))}
+        _ORACLE[key] = o
+    return _ORACLE[key]
+
+
+def mass_drift_gpu(case):
+    from paper_2502_20049_gb300 import psm
+
+    sol = psm.Solver.from_case(case.with_(bc_z=0))
+    m0 = sol.mass()
+    sol.step(case.steps)
+    m1 = sol.mass()
+    sol.close()
+    return abs(m1 - m0) / m0
+
+
+@pytest.mark.parametrize("name", ["c2_64", "d3q27_rotor"])
+def test_error_per_field(name):
+    base = workload(name)
+    o = oracle_run(name)
+    rho0 = base.rho0
+    perm = perm_lib_to_oracle(base.Q)
+    from paper_2502_20049_gb300 import psm
+
+    w = psm.lattice_velocities(base.Q)[1].reshape(-1, 1, 1, 1)
+    fo = o["f"][perm] - w * rho0
+    m0_or = float(base.cells * rho0)
+    o_drift = abs(oracle_run(name, periodic=True)["mass"] - m0_or) / m0_or
+    rows = []
+    for storage in ("fp32", "fp16", "bf16"):
+        case = base.with_(storage=storage)
+        g = run_gpu(case)
+        fg = g["f"] - w * rho0
+        ft_g, ft_o = np.asarray(g["ft"]), np.asarray(o["ft"])
+        e = {
+            "rho": np.abs(g["rho"] - o["rho"]).max() / rho0,
+            "u": u_err(g, o, case),
+            "f~": np.abs(fg - fo).max() / np.abs(fo).max(),
+            "F": np.abs(ft_g[..., :3] - ft_o[..., :3]).max() / np.abs(ft_o[..., :3]).max(),
+            "T": np.abs(ft_g[..., 3:] - ft_o[..., 3:]).max() / np.abs(ft_o[..., 3:]).max(),
+            "T_z": np.abs(ft_g[..., 5] - ft_o[..., 5]).max() / np.abs(ft_o[..., 5]).max(),
+            "mass": mass_drift_gpu(case),
+        }
+        rows.append((storage, e))
+        assert all(np.isfinite(v) for v in e.values()), (storage, e)
+        assert e["u"] <= U_BAR[storage], (storage, e)
+        if storage == "fp32":
+            assert e["F"] <= 1e-4 and e["T"] <= 1e-4 and e["T_z"] <= 1e-4, e
+    print(f"\n{name} ({base.nx}x{base.ny}x{base.nz} D3Q{base.Q}, {base.steps} steps; oracle periodic mass drift "
+          f"{o_drift:.1e})")
+    print("| storage | rho | u | f~ | F | T | T_z | mass drift |")
+    print("|---|---|---|---|---|---|---|---|")
+    for storage, e in rows:
+        print(f"| {storage} | " + " | ".join(f"{e[k]:.1e}" for k in ("rho", "u", "f~", "F", "T", "T_z", "mass"))
+              + " |")

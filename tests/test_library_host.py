@@ -134,6 +134,35 @@ def test_create_with_buffers_rejects_bad_buffers(psm, bufs, flags):
     assert rc == -1 and not h.value
 
 
+def test_host_buffers_are_rejected_before_any_launch(psm):
+    """Caller-owned memory that is host memory (a numpy array passed through
+    ctypes) is refused with PSM_ERR_ARG by psm_check_device_buffer,
+    psm_create_with_buffers and psm_mass_noalloc.  Without a GPU the pointer
+    cannot be classified at all and the answer is the same; on a GPU the
+    reason is that it is host memory.  Nothing is launched either way."""
+    import ctypes
+
+    a = np.zeros(19 * 8 * 8 * 8, dtype=np.float64)
+    b = np.zeros_like(a)
+    rc, msg = psm.check_device_buffer(a.ctypes.data, a.nbytes)
+    assert rc == -1 and msg
+    cfg = psm.SolverConfig(8, 8, 8, streaming="twogrid", storage="fp64")
+    grid = psm.Grid(cfg.nx, cfg.ny, cfg.nz, cfg.bc_z, cfg.rho0, (ctypes.c_double * 3)(*cfg.u_in))
+    lat = psm.Lattice(cfg.Q, psm.STREAMING[cfg.streaming], psm.STORAGE[cfg.storage])
+    col = psm.Collision(psm.FLUID[cfg.fluid], cfg.tau, cfg.trt_lambda, cfg.solid, cfg.weighting)
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 2)(a.ctypes.data, b.ctypes.data)
+    rc = psm.lib().psm_create_with_buffers(ctypes.byref(grid), ctypes.byref(lat), ctypes.byref(col), None, arr, 1,
+                                           ctypes.byref(h))
+    assert rc == -1 and not h.value
+    assert b"PDF buffer 0" in psm.lib().psm_last_error()
+    out = ctypes.c_double(7.0)
+    rc = psm.lib().psm_mass_noalloc(ctypes.c_void_p(a.ctypes.data), psm.STORAGE["fp64"], 19, 512, 0.0, None,
+                                    ctypes.byref(out))
+    assert rc == -1 and out.value == 7.0
+    assert b"psm_mass_noalloc: f" in psm.lib().psm_last_error()
+
+
 def test_null_handle_calls_are_argument_errors(psm):
     import ctypes
 
