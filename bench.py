@@ -6,10 +6,15 @@ One "step" is one pass of the whole hot path on one batch of cells: body poses,
 remap of the geometry field onto eps, PSM collision (Eq. 4), streaming, and the
 FP64 force/torque reduction -- one fused kernel launch (libpsm, psm_step).
 
-Default workload: D3Q19 TRT, FP32 PDFs, 256^3 lattice, uniform inflow 0.05,
-tau 0.55, an ellipsoid (semi-axes 40/20/8) rotating at 2e-4 rad/step about z
-and remapped every step (synthetic data shaped like the paper's 256^3 GPU
-block).
+Default workload (the largest single-GPU configuration): D3Q19 BGK, FP16
+shifted PDF storage, AA pattern in place, 1024 x 1024 x 960 = 1.0e9 cells,
+uniform inflow 0.04, tau 0.55, a synthetic counter-rotating rotor pair (6 and
+5 twisted elliptic blades, span 240 cells) at +-3e-4 rad/step, remapped every
+step.  Beside it (``variants``, each with its own roofline fraction): the
+rotating-ellipsoid 256^3 D3Q19 TRT workload in FP32 / FP16 / BF16 / FP64 and
+with the cumulant operator, the D3Q27 rotor workload 512 x 512 x 640 in FP32 /
+FP16 / BF16, the 1e9-cell workload in FP32, FP16 / FP32 ratios per workload,
+and the adjoint / forward step cost on 128^3.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -29,6 +34,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -46,6 +53,14 @@ NCU_BYTES_PER_CELL = {
 
 
 FLUID_NAME = {"bgk": "BGK", "trt": "TRT", "cumulant": "cumulant"}
+
+# streaming of each workload as configured (the 256^3 two-grid: measured
+# faster than AA there; the D3Q27 and 1e9-cell runs in place)
+DEFAULT_STREAMING = {"c2": "twogrid", "c3_fp32": "aa", "c3_fp16": "aa", "c3_bf16": "aa", "c5": "aa"}
+
+# planes of the 1e9-cell workload the CPU oracle steps as its bounded sample:
+# the full 1024 x 1024 cross-section through the front rotor's hub and blades
+C5_SAMPLE_Z0, C5_SAMPLE_NZ = 358, 4
 
 
 def with_fluid(case, desc, fluid):
@@ -81,22 +96,50 @@ def workload(name: str, streaming: str, fluid: str | None = None, scale: float =
                 f"counter-rotating rotor, remap every step")
     else:
         raise SystemExit(f"unknown workload {name}")
-    case = case.with_(streaming=streaming)
+    case = case.with_(streaming=streaming or DEFAULT_STREAMING[name])
     return with_fluid(case, desc, fluid)
 
 
-def reference_sample(name: str, fluid: str | None = None):
-    """The bounded sample the CPU oracle runs per step: the same workload on a
-    48^3 lattice with the body scaled by 48/n (about 0.1 MLUP per step)."""
-    from paper_2502_20049_gb300 import workloads as W
+# the bounded sample the CPU oracle steps: planes [z0, z0 + nz) of the full
+# workload (the whole x-y cross-section through the first body), about 4.2e6
+# cells, with the bodies that reach those planes
+SAMPLE_PLANES = {"c2": (96, 64), "c3_fp32": (232, 16), "c3_fp16": (232, 16), "c3_bf16": (232, 16),
+                 "c5": (C5_SAMPLE_Z0, C5_SAMPLE_NZ)}
 
-    if name == "c2":
-        case = W.c2_ellipsoid(scale=48 / 256, n=48, steps=1)
-    elif name == "c5":
-        case = W.c5_large(dims=(48, 48, 48), steps=1)
-    else:
-        case = W.c3_rotor(name.split("_")[1], scale=48 / 512, dims=(48, 48, 60), steps=1)
-    return with_fluid(case, "", fluid)[0]
+
+def oracle_sample(name: str, fluid: str | None = None):
+    """(oracle Sim, description, cells) of the sample: the workload's own
+    lattice, collision and bodies on a slab of its planes (the oracle's z0
+    offset keeps world cell centres), FP64, equilibrium start."""
+    import oracle
+
+    case, desc = workload(name, None, fluid)
+    z0, nz = SAMPLE_PLANES[name]
+    cfg = oracle.Config(nx=case.nx, ny=case.ny, nz=nz, Q=case.Q, bc_z=0, rho0=case.rho0, u_in=tuple(case.u_in),
+                        fluid={"bgk": 0, "trt": 1, "cumulant": 2}[case.fluid], tau=case.tau,
+                        trt_lambda=case.trt_lambda, solid=case.solid, weighting=case.weighting,
+                        cum_rates=tuple(case.cum_rates), z0=z0)
+    sim = oracle.Sim(cfg)
+    kept = 0
+    for b in case.bodies:
+        dims, lo = oracle.shape_box(b.kind, b.params)
+        if (b.omega[0] == 0.0 and b.omega[1] == 0.0 and b.v[2] == 0.0
+                and tuple(b.Q0) == (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0)):
+            zlo, zhi = b.R0[2] + lo[2] - 2.0, b.R0[2] + lo[2] + dims[2] + 2.0  # turning about z only
+        else:
+            reach = float(np.linalg.norm(np.maximum(np.abs(lo), np.abs(np.asarray(lo) + dims)))) + 2.0
+            zlo, zhi = b.R0[2] - reach, b.R0[2] + reach
+        if zhi < z0 or zlo > z0 + nz:
+            continue  # never reaches the sampled planes
+        sub, blo = oracle.voxelize(b.kind, b.params, b.s)
+        sim.add_body(oracle.BodySpec(sub=sub, s=b.s, lo=blo, R0=tuple(b.R0), Q0=np.array(b.Q0),
+                                     omega=tuple(b.omega), v=tuple(b.v)))
+        kept += 1
+    sim.init_eq(case.rho0, case.u_in)
+    cells = case.nx * case.ny * nz
+    sdesc = (f"FP64 oracle, planes {z0}..{z0 + nz - 1} ({case.nx}x{case.ny}x{nz} cells, {kept} of "
+             f"{len(case.bodies)} bodies reach them) of: {desc}")
+    return sim, sdesc, cells
 
 
 def peaks():
@@ -165,19 +208,14 @@ class Clocks:
 
 
 def cpu_baseline(name: str, steps: int = 3, fluid: str | None = None):
-    """The oracle as it stands on this host's cores: `steps` steps of the full workload."""
-    from oracle.cases import sim_from_case as oracle_sim
-
-    case, _ = workload(name, "twogrid", fluid)
-    case = case.with_(storage="fp64")
-    sim = oracle_sim(case)
+    """The oracle as it stands on this host's cores: `steps` steps of the bounded sample."""
+    sim, sdesc, cells = oracle_sample(name, fluid)
     t0 = time.perf_counter()
     sim.step(steps)
     dt = time.perf_counter() - t0
-    mlups = case.cells * steps / dt / 1e6
+    mlups = cells * steps / dt / 1e6
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": sim.threads, "kind": "oracle",
-            "sample": f"{steps} steps of the full {case.nx}x{case.ny}x{case.nz} workload, FP64 two-grid, "
-                      f"{dt:.1f} s"}
+            "sample": f"{steps} steps of the {sdesc}; {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -186,23 +224,18 @@ def run_reference(args):
     rank, world, _ = replicas.env()
     if rank != 0:
         return
-    from oracle.cases import sim_from_case as oracle_sim
-
-    case = reference_sample(args.workload, args.fluid)
-    sim = oracle_sim(case)
+    sim, sdesc, cells = oracle_sample(args.workload, args.fluid)
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
     dt = time.perf_counter() - t0
-    mlups = case.cells * args.steps / dt / 1e6
-    _, desc = workload(args.workload, args.streaming, args.fluid)
+    mlups = cells * args.steps / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "sample_cells": case.cells},
+            "config": {"workload": sdesc, "sample_cells": cells},
             "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": sim.threads, "kind": "oracle",
-                             "sample": f"each step one oracle step of the workload on a "
-                                       f"{case.nx}x{case.ny}x{case.nz} lattice (body scaled to fit)"},
+                             "sample": f"each step one oracle step of the {sdesc}"},
             "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -221,21 +254,40 @@ def time_steps(sol, steps: int, stream) -> float:
     return ev0.elapsed_time(ev1) / 1e3
 
 
-def variant_mlups(name, streaming, storage, kernel, steps, warmup, stream, fluid=None):
-    """MLUPS of one storage / streaming / fluid-operator variant of the workload (same timing rules)."""
+def variant_mlups(name, streaming, storage, steps, warmup, stream, peak, fluid=None, geoms=None):
+    """MLUPS and HBM roofline fraction of one storage / streaming / fluid-operator
+    variant of a workload (same timing rules as the headline)."""
     from paper_2502_20049_gb300 import psm
 
     case, _ = workload(name, streaming, fluid)
     case = case.with_(storage=storage)
-    sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
-    if kernel != "auto":
-        sol.set_kernel_variant(kernel)
+    sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream), geoms=geoms)
     sol.step(warmup)
     t = time_steps(sol, steps, stream)
     v = sol.kernel_variant
+    bpc = sol.bytes_per_cell_update()
     sol.close()
-    return {"mlups": round(case.cells * steps / t / 1e6, 1), "kernel": v,
-            "hbm_gbs": round(2 * case.Q * psm.STORAGE_BYTES[storage] * case.cells * steps / t / 1e9, 1)}
+    gbs = bpc * case.cells * steps / t / 1e9
+    return {"mlups": round(case.cells * steps / t / 1e6, 1), "kernel": v, "streaming": case.streaming,
+            "hbm_gbs": round(gbs, 1), "frac": round(gbs / peak, 4), "bytes_per_cell": bpc, "steps": steps}
+
+
+# variants measured beside the headline: (key, workload, streaming, storage, fluid, steps)
+VARIANTS = [
+    ("c2/fp32/twogrid", "c2", "twogrid", "fp32", None, 200),
+    ("c2/fp16/twogrid", "c2", "twogrid", "fp16", None, 200),
+    ("c2/bf16/twogrid", "c2", "twogrid", "bf16", None, 200),
+    ("c2/fp64/twogrid", "c2", "twogrid", "fp64", None, 20),
+    ("c2/fp32/aa", "c2", "aa", "fp32", None, 200),
+    ("c2/fp16/aa", "c2", "aa", "fp16", None, 200),
+    ("c2/fp32/twogrid/cumulant", "c2", "twogrid", "fp32", "cumulant", 200),
+    ("c2/fp16/twogrid/cumulant", "c2", "twogrid", "fp16", "cumulant", 200),
+    ("c3/fp32/aa", "c3_fp32", "aa", "fp32", None, 20),
+    ("c3/fp16/aa", "c3_fp16", "aa", "fp16", None, 20),
+    ("c3/bf16/aa", "c3_bf16", "aa", "bf16", None, 20),
+    ("c5/fp32/aa", "c5", "aa", "fp32", None, 10),
+    ("c5/fp16/aa", "c5", "aa", "fp16", None, 10),
+]
 
 
 def adjoint_cost(stream, steps: int = 512, K: int = 64):
@@ -296,7 +348,8 @@ def run_ours(args):
         case = case.with_(storage=args.storage)
         desc = desc.replace("FP32", args.storage.upper()).replace("FP16-shifted", args.storage.upper())
     stream = torch.cuda.current_stream()
-    sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream))
+    geoms = {}
+    sol = psm.Solver.from_case(case, stream=int(stream.cuda_stream), geoms=geoms)
     if args.kernel != "auto":
         sol.set_kernel_variant(args.kernel)
     cells = case.cells
@@ -318,15 +371,16 @@ def run_ours(args):
     peak, peak_kind = peaks()
     key = f"{args.workload}/{case.streaming}/{case.storage}/{sol.kernel_variant}" + (
         f"/{args.fluid}" if args.fluid else "")
-    traffic = NCU_BYTES_PER_CELL.get(key)
+    traffic = NCU_BYTES_PER_CELL.get(key) if args.scale == 1.0 else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"hbm_gbs of {peak_kind}",
                 "traffic": None if traffic is None else round(traffic * cells),
                 "algorithmic_bytes_per_cell": bpc, "kernel": f"k_step ({sol.kernel_variant} loads)"}
 
     # end to end through the public API: every step one psm_step call (the
-    # pose rides in the launch parameters) and a synchronous read of that
-    # step's force/torque into pinned host memory
+    # bodies' poses travel as launch parameters) and a synchronous read of that
+    # step's force/torque of every body into pinned host memory; the PDF state
+    # is the solver's own and stays in HBM
     nb = len(case.bodies)
     out = torch.empty((1, 6), dtype=torch.float64, pin_memory=True)
     sol.synchronize()
@@ -337,9 +391,11 @@ def run_ours(args):
             sol.force_torque(b, sol.step_count - 1, 1, out=out)
     t_e2e = replicas.max_over_ranks(dist, time.perf_counter() - t0, device="cuda")
     e2e = {"value": round(replicas.aggregate_rate(cells * args.steps, world, t_e2e) / 1e6, 1), "unit": "MLUPS",
-           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 48 * nb,
-           "note": "per step: psm_step(h, 1) with the body poses as launch parameters, then psm_force_torque "
-                   "into pinned host memory (synchronising)"}
+           "h2d_bytes_per_step": 96 * nb, "d2h_bytes_per_step": 48 * nb,
+           "note": "per step: psm_step(h, 1), whose input is each body's pose (rotation and position, 12 doubles "
+                   "per body, computed on the host and passed as launch parameters), then psm_force_torque of "
+                   "every body into pinned host memory (synchronising); no PDF state is copied: it is the "
+                   "solver's state and stays in HBM"}
     sol.close()
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -355,21 +411,27 @@ def run_ours(args):
         line["clocks"] = ck
     if not args.no_extras:
         vs = {}
-        for streaming, storage in (("twogrid", "fp16"), ("twogrid", "bf16"), ("aa", "fp32"), ("aa", "fp16")):
-            if streaming == case.streaming and storage == case.storage:
+        for vkey, name, streaming, storage, fluid, steps in VARIANTS:
+            same = (name == args.workload and streaming == case.streaming and storage == case.storage
+                    and fluid == args.fluid and args.scale == 1.0)
+            if same:
+                vs[vkey] = {"mlups": round(cells * args.steps / t / 1e6, 1), "kernel": sol.kernel_variant,
+                            "streaming": case.streaming, "hbm_gbs": round(achieved, 1),
+                            "frac": round(achieved / peak, 4), "bytes_per_cell": bpc, "steps": args.steps,
+                            "note": "the headline run"}
                 continue
-            vs[f"{storage}/{streaming}"] = variant_mlups(args.workload, streaming, storage, "auto", 300, 5, stream,
-                                                         fluid=args.fluid)
-        # the cumulant operator (the paper's performance runs use it; D3Q19) on the same workload
-        if case.Q == 19 and case.fluid != "cumulant":
-            for streaming, storage in (("twogrid", "fp32"), ("twogrid", "fp16"), ("aa", "fp16")):
-                vs[f"{storage}/{streaming}/cumulant"] = variant_mlups(args.workload, streaming, storage, "auto", 300,
-                                                                       5, stream, fluid="cumulant")
+            vs[vkey] = variant_mlups(name, streaming, storage, steps, 3, stream, peak, fluid=fluid, geoms=geoms)
         line["variants"] = vs
-        # FP16-shifted storage against this storage, same streaming, one GPU each
-        other = "fp16/" + case.streaming
-        if case.storage == "fp32" and other in vs:
-            line["fp16_over_fp32"] = round(vs[other]["mlups"] / (cells * args.steps / t / 1e6), 3)
+        # FP16-shifted storage against FP32, same workload and streaming, one GPU each
+        ratios = {}
+        for wl, st in (("c2", "twogrid"), ("c2", "aa"), ("c3", "aa"), ("c5", "aa")):
+            a, b = vs.get(f"{wl}/fp16/{st}"), vs.get(f"{wl}/fp32/{st}")
+            if a and b:
+                ratios[f"{wl}/{st}"] = round(a["mlups"] / b["mlups"], 3)
+        a, b = vs.get("c2/fp16/twogrid/cumulant"), vs.get("c2/fp32/twogrid/cumulant")
+        if a and b:
+            ratios["c2/twogrid/cumulant"] = round(a["mlups"] / b["mlups"], 3)
+        line["fp16_over_fp32"] = ratios
         line["adjoint"] = adjoint_cost(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, fluid=args.fluid)
@@ -382,11 +444,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5", "c3_fp32", "c3_fp16", "c3_bf16"])
-    ap.add_argument("--streaming", default="twogrid", choices=["aa", "twogrid"])
+    ap.add_argument("--workload", default="c5", choices=["c2", "c5", "c3_fp32", "c3_fp16", "c3_bf16"])
+    ap.add_argument("--streaming", default=None, choices=["aa", "twogrid"],
+                    help="default: the workload's own (two-grid for c2, AA for c3 and c5)")
     ap.add_argument("--storage", default=None, choices=["fp64", "fp32", "fp16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--fluid", default=None, choices=["bgk", "trt", "cumulant"],

@@ -285,6 +285,15 @@ int psm_get_eps(psm_handle h, float* eps);
 int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const double Q0[9], const double R0[3],
                      const double omega[3], const double v[3]);
 
+/* Angular velocity of body `body` in its solid velocity u_s = omega x (x - R_n)
+ * + v (Eq. 7-9) from the next step on, while its pose sequence (Sec. 3) keeps
+ * the omega of psm_set_geometry: the geometry stays frozen when u_s's omega
+ * changes, which is how psm_backward differentiates with respect to omega
+ * (central differences of J in this omega check grad_omega).
+ * psm_set_geometry resets it to the pose's omega.  PSM_ERR_ARG for a bad body
+ * or non-finite values; PSM_ERR_STATE for a two-way coupled body. */
+int psm_set_us_omega(psm_handle h, int body, const double omega[3]);
+
 /* Number of bodies attached. */
 int psm_num_bodies(psm_handle h, int* out);
 
@@ -366,6 +375,43 @@ int psm_synchronize(psm_handle h);
  * compute the same states, bit for bit; the FP64 force/torque sums agree bit
  * for bit where the variants tile alike and to rounding (summation order)
  * otherwise. */
+/* ------------------------------------------------------------------------ */
+/* z-slab decomposition (Sec. 5.2 runs one block of the lattice per GPU and    */
+/* exchanges the populations that cross block faces every step)              */
+/* ------------------------------------------------------------------------ */
+
+/* Declare the handle's lattice the planes [z0, z0 + nz) of a larger domain:
+ * cell centres (the remap, u_s, the torque lever arm) use the world z + z0;
+ * force, torque and mass are then this slab's part of the sums (add them over
+ * the slabs).  A slab is created with bc_z = PSM_BC_PERIODIC: the periodic
+ * wrap puts the populations that leave through one face into the slots of the
+ * opposite face, from where the caller's exchange moves them to the
+ * neighbouring slab between steps (psm_slot_plane; after every two-grid step,
+ * before and after every odd AA step), or replaces them with the inflow
+ * equilibrium at the domain's own z ends (psm_fill_slot_plane).  PSM_ERR_ARG
+ * for z0 < 0 or z0 + nz > 2^30; PSM_ERR_STATE while recording or with
+ * two-way coupled bodies; afterwards psm_record and psm_set_body_dynamics
+ * refuse the handle (the adjoint and the free-body update are not
+ * decomposed). */
+int psm_set_z_offset(psm_handle h, int64_t z0);
+
+/* Device address of slot `slot` (0 <= slot < Q, the library's direction
+ * order) of plane z (0 <= z < nz) in the buffer the next step reads: nx * ny
+ * contiguous values of the storage type, stored as the step kernels keep them
+ * (shifted; the AA pattern's swapped layout after an odd step).  Valid until
+ * the next psm_step (two-grid streaming alternates buffers); for the face
+ * exchange of a slab decomposition (a peer copy or NCCL send/recv into each
+ * GPU's own buffers). */
+int psm_slot_plane(psm_handle h, int slot, int z, void** out);
+
+/* Set slot `slot` of plane z, in the buffer the next step reads, to the
+ * inflow equilibrium f^eq_dir(rho0, u_in) of direction `dir` held by the
+ * ghost planes (shifted, rounded to the storage type), asynchronously on the
+ * handle's stream.  dir = slot in the natural layout; in the AA pattern's
+ * swapped layout slot opp(i) holds population i, so dir = opp(slot).  Used at
+ * the ends of a decomposed domain whose z is bounded by ghost planes. */
+int psm_fill_slot_plane(psm_handle h, int slot, int z, int dir);
+
 /* ------------------------------------------------------------------------ */
 /* Differentiation (not in the paper): discrete adjoint of the step          */
 /* ------------------------------------------------------------------------ */

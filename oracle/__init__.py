@@ -133,6 +133,7 @@ class _Cfg(ctypes.Structure):
         ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("u_in", ctypes.c_double * 3),
         ("fluid", ctypes.c_int), ("tau", ctypes.c_double), ("trt_lambda", ctypes.c_double),
         ("solid", ctypes.c_int), ("weighting", ctypes.c_int), ("cum_rates", ctypes.c_double * 3),
+        ("z0", ctypes.c_int),
     ]
 
 
@@ -146,6 +147,8 @@ class Config:
     ``solid``: 1/2/3 = Eq. 7/8/9.
     ``weighting``: 0 Eq. 5, 1 Eq. 6.  ``walls_y`` and ``force`` are oracle-only
     (half-way bounce-back walls and a Guo body force, used by the pins).
+    ``z0``: world z index of plane 0 (the grid is the slab [z0, z0 + nz) of a
+    larger domain; the geometry uses world cell centres).
     """
 
     nx: int
@@ -165,6 +168,7 @@ class Config:
     wall_u_hi: tuple = (0.0, 0.0, 0.0)
     force: tuple = (0.0, 0.0, 0.0)
     cum_rates: tuple = (1.0, 1.0, 1.0)
+    z0: int = 0
 
     def _c(self):
         c = _Cfg()
@@ -178,6 +182,7 @@ class Config:
             c.cum_rates[k] = self.cum_rates[k]
         c.rho0, c.fluid, c.tau, c.trt_lambda = self.rho0, self.fluid, self.tau, self.trt_lambda
         c.solid, c.weighting = self.solid, self.weighting
+        c.z0 = self.z0
         return c
 
 
@@ -481,3 +486,48 @@ class TangentSim:
         t = np.zeros(self.shape)
         _lib().ort_get_f(self._h, _dp(v), _dp(t))
         return v, t
+
+
+def tangent_gradient(cfg: Config, bodies, steps: int, rho0: float, u_in, weights=None, threads: int = 1):
+    """FP64 gradient of J = sum_{n, b, k} w[n, b, k] FT[n, b, k] over `steps`
+    steps from the equilibrium f^eq(rho0, u_in), as directional derivatives of
+    the tangent-linear model, one run per direction (the definition of each
+    partial derivative, no reverse sweep):
+      grad_delta[z, y, x]: seed e_c on the per-cell perturbation delta of cell c,
+      grad_omega[b, k]:    seed on component k of body b's angular velocity
+                           (through u_s; the geometry sequence is frozen),
+      grad_u_in[k]:        seed on component k of the inflow, in the ghost
+                           planes and in the initial state.
+    bodies: BodySpec list; weights [steps, nbodies, 6] (None: mean T_z of
+    body 0).  Test infrastructure, like the rest of this package."""
+    nb = len(bodies)
+    if weights is None:
+        weights = np.zeros((steps, nb, 6))
+        weights[:, 0, 5] = 1.0 / steps
+    weights = np.asarray(weights, dtype=np.float64).reshape(steps, nb, 6)
+
+    def run(d_delta=None, d_omega=None, d_u=(0.0, 0.0, 0.0)):
+        sim = TangentSim(cfg, d_u_in=d_u, threads=threads)
+        for b, spec in enumerate(bodies):
+            sim.add_body(spec, d_omega=(0.0, 0.0, 0.0) if d_omega is None or d_omega[0] != b else d_omega[1])
+        sim.init_eq(rho0, u_in, du=d_u)
+        if d_delta is not None:
+            sim.set_delta(None, d_delta)
+        sim.step(steps)
+        v, t = sim.force_torque()
+        return float((v * weights).sum()), float((t * weights).sum())
+
+    n = cfg.nx * cfg.ny * cfg.nz
+    J = run()[0]
+    g_delta = np.zeros(n)
+    e = np.zeros(n)
+    for c in range(n):
+        e[c] = 1.0
+        g_delta[c] = run(d_delta=e)[1]
+        e[c] = 0.0
+    g_omega = np.zeros((nb, 3))
+    for b in range(nb):
+        for k in range(3):
+            g_omega[b, k] = run(d_omega=(b, tuple(1.0 if j == k else 0.0 for j in range(3))))[1]
+    g_u = np.array([run(d_u=tuple(1.0 if j == k else 0.0 for j in range(3)))[1] for k in range(3)])
+    return J, g_delta.reshape(cfg.nz, cfg.ny, cfg.nx), g_omega, g_u

@@ -253,6 +253,8 @@ typedef struct {
   int solid;             // 1, 2, 3: SC1 (Eq. 7), SC2 (Eq. 8), SC3 (Eq. 9)
   int weighting;         // 0: B = eps (Eq. 5); 1: tau-weighted (Eq. 6)
   double cum_rates[3];   // cumulant (fluid 2): omega_bulk, omega_3, omega_4
+  int z0;                // world z index of plane 0: the lattice is the slab [z0, z0 + nz) of a larger
+                         // domain (cell centres, hence the remap, u_s and the torque lever arm, use z + z0)
 } or_config;
 
 }  // extern "C"
@@ -433,7 +435,7 @@ struct Sim {
       for (int z = 0; z < cfg.nz; ++z)
         for (int y = 0; y < cfg.ny; ++y)
           for (int x = 0; x < cfg.nx; ++x) {
-            double e = remap_cell(B.sub.data(), B.nsx, B.nsy, B.nsz, B.s, B.lo, P, x, y, z);
+            double e = remap_cell(B.sub.data(), B.nsx, B.nsy, B.nsz, B.s, B.lo, P, x, y, z + cfg.z0);
             long c = cell(x, y, z);
             eps[c] += e;
             if (e > best[c]) { best[c] = e; owner[c] = (int)b; }
@@ -487,7 +489,7 @@ struct Sim {
     owner_c = -1;
     for (size_t b = 0; b < bodies.size(); ++b) {
       const Body<T>& B = bodies[b];
-      double e = remap_cell(B.sub.data(), B.nsx, B.nsy, B.nsz, B.s, B.lo, poses[b], x, y, z);
+      double e = remap_cell(B.sub.data(), B.nsx, B.nsy, B.nsz, B.s, B.lo, poses[b], x, y, z + cfg.z0);
       sum += e;
       if (e > best) { best = e; owner_c = (int)b; }
     }
@@ -534,7 +536,7 @@ struct Sim {
     if (owner_c >= 0) {
       const Body<T>& Bd = bodies[owner_c];
       T r[3] = {T(x + 0.5 - poses[owner_c].R[0]), T(y + 0.5 - poses[owner_c].R[1]),
-                T(z + 0.5 - poses[owner_c].R[2])};
+                T((z + cfg.z0) + 0.5 - poses[owner_c].R[2])};
       us[0] = Bd.omega[1] * r[2] - Bd.omega[2] * r[1] + Bd.v[0];
       us[1] = Bd.omega[2] * r[0] - Bd.omega[0] * r[2] + Bd.v[1];
       us[2] = Bd.omega[0] * r[1] - Bd.omega[1] * r[0] + Bd.v[2];
@@ -671,7 +673,8 @@ struct Sim {
             if (!delta.empty()) e = e + delta[c];
             T Bw = weighting<T>(cfg.weighting, e, tau);
             if (!(val(Bw) > 0.0)) continue;
-            T r[3] = {T(x + 0.5 - poses[b].R[0]), T(y + 0.5 - poses[b].R[1]), T(z + 0.5 - poses[b].R[2])};
+            T r[3] = {T(x + 0.5 - poses[b].R[0]), T(y + 0.5 - poses[b].R[1]),
+                      T((z + cfg.z0) + 0.5 - poses[b].R[2])};
             const T* gc = &g[3 * c];
             for (int k = 0; k < 3; ++k) SF[k] += gc[k];
             ST[0] += r[1] * gc[2] - r[2] * gc[1];

@@ -63,6 +63,9 @@ struct HostBody {
   double R0[3] = {0, 0, 0};
   double omega[3] = {0, 0, 0};
   double v[3] = {0, 0, 0};
+  // angular velocity in u_s = omega x r + v (psm_set_us_omega); the pose
+  // sequence keeps `omega`
+  double us_omega[3] = {0, 0, 0};
 };
 
 // Pose at step n: Q_n = Rot(k, th) Q0 with k = omega/|omega|, th = |omega| n
@@ -133,6 +136,8 @@ struct psm_solver {
   BufMaps maps[2];
   // trajectory recording for psm_backward: checkpoints every rec_K steps from rec_n0
   bool recording = false;
+  // psm_set_z_offset was called: the lattice is a z-slab of a larger domain
+  bool slab = false;
   int rec_K = 0;
   int rec_flags = 0;
   int64_t rec_n0 = 0;
@@ -211,10 +216,14 @@ void set_slots(StepParams& p, int storage, int Q) {
   }
 }
 
+// Tiles of tx x ty = PSM_THREADS cells (one per thread): tx is the smallest
+// power of two >= nx from 32 up to PSM_THREADS, so that ty = PSM_THREADS / tx
+// leaves no thread without a cell of its own tile (a tx that does not divide
+// the block, such as 96, would give the spare threads cells of the next tile).
 Tiling make_tiling(int nx, int ny, int nz) {
   Tiling t;
-  int tx = ((nx + 31) / 32) * 32;
-  if (tx > PSM_THREADS) tx = PSM_THREADS;
+  int tx = 32;
+  while (tx < nx && tx < PSM_THREADS) tx *= 2;
   t.tx = tx;
   t.ty = PSM_THREADS / tx;
   t.ntx = (nx + t.tx - 1) / t.tx;
@@ -278,8 +287,16 @@ __global__ void k_remap(const __grid_constant__ RemapParams p) {
     const long long r = idx % plane;
     const int y = (int)(r / p.g.nx), x = (int)(r % p.g.nx);
     int owner;
-    p.eps_out[idx] = cell_eps(p.body, p.nbodies, x, y, z, owner);
+    p.eps_out[idx] = cell_eps(p.body, p.nbodies, x, y, z + p.g.z0, owner);
   }
+}
+
+// every element of dst[0, n) = v in the storage type (psm_fill_slot_plane)
+template <class S>
+__global__ void k_fill_plane(S* dst, long long n, double v) {
+  const S sv = Store<S>::from_double(v);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = sv;
 }
 
 // one thread per occupancy cell c in [-1, g - 1]^3
@@ -445,9 +462,9 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
   for (int k = 0; k < 3; ++k) {
     d.Rf[k] = (float)R[k];
     d.R[k] = R[k];
-    d.omega[k] = b.omega[k];
+    d.omega[k] = b.us_omega[k];
     d.v[k] = b.v[k];
-    d.omegaf[k] = (float)b.omega[k];
+    d.omegaf[k] = (float)b.us_omega[k];
     d.vf[k] = (float)b.v[k];
   }
   double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
@@ -461,11 +478,13 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
       mx[r] = std::fmax(mx[r], w);
     }
   }
-  const int64_t dims[3] = {h->grid.nx, h->grid.ny, h->grid.nz};
+  // world cells of this grid: [0, nx) x [0, ny) x [z0, z0 + nz)
+  const int64_t first[3] = {0, 0, h->g.z0};
+  const int64_t dims[3] = {h->grid.nx, h->grid.ny, h->g.z0 + h->grid.nz};
   int lo_[3], hi_[3];
   for (int k = 0; k < 3; ++k) {
     double a = std::floor(mn[k] - 2.5), e = std::ceil(mx[k] + 2.5) + 1.0;
-    if (a < 0) a = 0;
+    if (a < (double)first[k]) a = (double)first[k];
     if (e > (double)dims[k]) e = (double)dims[k];
     if (e < a) e = a;
     lo_[k] = (int)a;
@@ -479,6 +498,14 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
   d.z1 = hi_[2];
   psm::remap_setup(d, Q, R, b.lo);
   return d;
+}
+
+// slot `slot` of plane z in the buffer the next step reads
+void* slot_plane_addr(const psm_solver* h, int slot, int z) {
+  void* buf = h->lat.streaming == PSM_STREAM_TWO_GRID ? h->buf[h->cur] : h->buf[0];
+  const size_t plane = (size_t)h->grid.nx * (size_t)h->grid.ny;
+  return static_cast<char*>(buf) + ((size_t)slot * (size_t)h->g.ncell + (size_t)z * plane) *
+                                       storage_bytes(h->lat.storage);
 }
 
 int layout_of(const psm_solver* h) {
@@ -775,6 +802,7 @@ int create_impl(const psm_grid* grid, const psm_lattice* lattice, const psm_coll
   h->g.nz = (int)grid->nz;
   h->g.ncell = (long long)grid->nx * grid->ny * grid->nz;
   h->g.bc_z = grid->bc_z;
+  h->g.z0 = 0;
   h->tiling = psm::make_tiling(h->g.nx, h->g.ny, h->g.nz);
   fill_ghost(h);
 
@@ -1163,11 +1191,22 @@ int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const 
     b.lo[k] = field->lo[k];
     b.R0[k] = R0[k];
     b.omega[k] = omega[k];
+    b.us_omega[k] = omega[k];
     b.v[k] = v[k];
   }
   for (int k = 0; k < 9; ++k) b.Q0[k] = Q0[k];
   h->free_mask &= ~(1u << body);  // prescribed motion again
   if (body == h->nbodies) h->nbodies++;
+  return PSM_OK;
+}
+
+int psm_set_us_omega(psm_handle h, int body, const double omega[3]) {
+  if (!valid_handle(h) || !omega) return fail(PSM_ERR_ARG, "psm_set_us_omega: NULL argument");
+  if (body < 0 || body >= h->nbodies) return fail(PSM_ERR_ARG, "no body %d", body);
+  if ((h->free_mask >> body) & 1u) return fail(PSM_ERR_STATE, "body %d moves under the fluid's load", body);
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(omega[k])) return fail(PSM_ERR_ARG, "omega must be finite");
+  for (int k = 0; k < 3; ++k) h->body[body].us_omega[k] = omega[k];
   return PSM_OK;
 }
 
@@ -1299,6 +1338,7 @@ int psm_record(psm_handle h, int K, int flags) {
   if (flags & ~PSM_RECORD_INIT_FROM_INFLOW) return fail(PSM_ERR_ARG, "unknown record flags");
   if (h->col.fluid == PSM_CUMULANT)
     return fail(PSM_ERR_UNSUPPORTED, "psm_backward supports BGK and TRT (no adjoint of the cumulant operator)");
+  if (h->slab) return fail(PSM_ERR_UNSUPPORTED, "psm_backward of a z-slab (the adjoint is not decomposed)");
   if (h->free_mask)
     return fail(PSM_ERR_STATE, "psm_backward supports prescribed motion only (two-way coupled bodies attached)");
   {
@@ -1585,11 +1625,49 @@ int psm_set_remap(psm_handle h, int every_step) {
   return PSM_OK;
 }
 
+int psm_set_z_offset(psm_handle h, int64_t z0) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_set_z_offset: NULL handle");
+  if (z0 < 0 || z0 + h->grid.nz > (int64_t)(1 << 30)) return fail(PSM_ERR_ARG, "z0 must be in [0, 2^30 - nz]");
+  if (h->recording) return fail(PSM_ERR_STATE, "psm_set_z_offset while recording for psm_backward");
+  if (h->free_mask) return fail(PSM_ERR_STATE, "psm_set_z_offset with two-way coupled bodies");
+  h->g.z0 = (int)z0;
+  h->slab = true;
+  return PSM_OK;
+}
+
+int psm_slot_plane(psm_handle h, int slot, int z, void** out) {
+  if (!valid_handle(h) || !out) return fail(PSM_ERR_ARG, "psm_slot_plane: NULL argument");
+  if (slot < 0 || slot >= h->Q) return fail(PSM_ERR_ARG, "slot %d out of range (Q = %d)", slot, h->Q);
+  if (z < 0 || z >= h->grid.nz) return fail(PSM_ERR_ARG, "plane %d out of range (nz = %d)", z, (int)h->grid.nz);
+  *out = slot_plane_addr(h, slot, z);
+  return PSM_OK;
+}
+
+int psm_fill_slot_plane(psm_handle h, int slot, int z, int dir) {
+  if (!valid_handle(h)) return fail(PSM_ERR_ARG, "psm_fill_slot_plane: NULL handle");
+  if (slot < 0 || slot >= h->Q) return fail(PSM_ERR_ARG, "slot %d out of range (Q = %d)", slot, h->Q);
+  if (dir < 0 || dir >= h->Q) return fail(PSM_ERR_ARG, "direction %d out of range (Q = %d)", dir, h->Q);
+  if (z < 0 || z >= h->grid.nz) return fail(PSM_ERR_ARG, "plane %d out of range (nz = %d)", z, (int)h->grid.nz);
+  void* dst = slot_plane_addr(h, slot, z);
+  const long long n = (long long)h->grid.nx * h->grid.ny;
+  const int blocks = (int)std::min<long long>((n + psm::PSM_THREADS - 1) / psm::PSM_THREADS, 1024);
+  const double v = h->ghost[dir];
+  switch (h->lat.storage) {
+    case PSM_FP64: psm::k_fill_plane<double><<<blocks, psm::PSM_THREADS, 0, h->stream>>>((double*)dst, n, v); break;
+    case PSM_FP32: psm::k_fill_plane<float><<<blocks, psm::PSM_THREADS, 0, h->stream>>>((float*)dst, n, v); break;
+    case PSM_FP16_SHIFTED: psm::k_fill_plane<__half><<<blocks, psm::PSM_THREADS, 0, h->stream>>>((__half*)dst, n, v); break;
+    default: psm::k_fill_plane<__nv_bfloat16><<<blocks, psm::PSM_THREADS, 0, h->stream>>>((__nv_bfloat16*)dst, n, v); break;
+  }
+  PSM_CUDA(cudaGetLastError(), "plane fill launch");
+  return PSM_OK;
+}
+
 int psm_set_body_dynamics(psm_handle h, int body, const psm_body_dynamics* dyn) {
   if (!valid_handle(h) || !dyn) return fail(PSM_ERR_ARG, "psm_set_body_dynamics: NULL argument");
   if (body < 0 || body >= h->nbodies) return fail(PSM_ERR_ARG, "no body %d", body);
   if (h->recording) return fail(PSM_ERR_STATE, "two-way coupling while recording for psm_backward");
   if (h->remap_frozen) return fail(PSM_ERR_STATE, "two-way coupling with the remap frozen");
+  if (h->slab) return fail(PSM_ERR_STATE, "two-way coupling of a z-slab (each slab sees part of the force)");
   const double* I = dyn->inertia;
   bool ok = dyn->mass > 0.0 && std::isfinite(dyn->mass);
   for (int k = 0; k < 9; ++k) ok = ok && std::isfinite(I[k]);

@@ -75,7 +75,7 @@ struct DevBody {
   double v[3];
   float omegaf[3];
   float vf[3];
-  // cells tested for this body: [x0, x1) x [y0, y1) x [z0, z1)
+  // cells tested for this body: [x0, x1) x [y0, y1) x [z0, z1), world cell indices
   int x0, x1, y0, y1, z0, z1;
 };
 
@@ -154,6 +154,8 @@ struct Grid3 {
   int nx, ny, nz;
   long long ncell;
   int bc_z;  // PSM_BC_PERIODIC / PSM_BC_EQ_INLET_OUTLET
+  int z0;    // world z of plane 0 (a z-slab of a larger domain; 0 otherwise): cell centres are
+             // (x + 1/2, y + 1/2, z + z0 + 1/2) for the remap, u_s and the torque lever arm
 };
 
 struct Tiling {

@@ -673,6 +673,7 @@ __device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T
 template <class T, int Q, int FL>
 __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* bodies, T (&f)[Q], int x, int y,
                                             int z, unsigned cell, int& owner, bool& solid_cell, double (&ft)[6]) {
+  // (x, y, z): world cell indices (z includes the slab offset); cell: this grid's index
   const ConstT<T>& C = cst<T>(p);
   const T om_a = C.om_a, om_b = C.om_b;
   const T inv_tau = C.inv_tau;
@@ -950,11 +951,12 @@ __device__ __forceinline__ void load_bodies(const StepParams& p, DevBody* s_body
 __device__ __forceinline__ bool tile_general(const StepParams& p, const DevBody* bodies, int x0, int y0, int z, int TX,
                                              int TY) {
   bool gen = p.delta != nullptr || (p.g.bc_z == PSM_BC_EQ_INLET_OUTLET && (z == 0 || z == p.g.nz - 1));
+  const int zw = z + p.g.z0;  // world z of the plane (the body boxes are in world cells)
 #pragma unroll
   for (int bi = 0; bi < PSM_MAX_BODIES; ++bi) {
     if (bi < p.nbodies) {
       const DevBody& b = bodies[bi];
-      gen = gen || (x0 < b.x1 && x0 + TX > b.x0 && y0 < b.y1 && y0 + TY > b.y0 && z >= b.z0 && z < b.z1);
+      gen = gen || (x0 < b.x1 && x0 + TX > b.x0 && y0 < b.y1 && y0 + TY > b.y0 && zw >= b.z0 && zw < b.z1);
     }
   }
   return gen;
@@ -1008,7 +1010,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
       zg.init(p.g, z);
       T f[Q];
       psm_load<S, Q, MODE, GEN>(p, sn, zg, cell, f);
-      if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
+      if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z + p.g.z0, cell, owner, solid_cell, ft);
       else fluid_collide<T, Q, FL>(p, f);
       if (MODE == MODE_AA_ODD) {
         // rebuild the stencil for the stores rather than keep it live through
@@ -1374,7 +1376,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
       int owner = -1;
       bool solid_cell = false;
       double ft[6] = {0, 0, 0, 0, 0, 0};
-      if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z, cell, owner, solid_cell, ft);
+      if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z + p.g.z0, cell, owner, solid_cell, ft);
       else fluid_collide<T, Q, FL>(p, f);
       if constexpr (L::STORE_TMA) {
         static_assert(CPT == 1, "TMA stores write one cell per thread");

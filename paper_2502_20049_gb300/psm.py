@@ -124,6 +124,10 @@ def lib() -> ctypes.CDLL:
                 "psm_kernel_variant": (i, [H, P(i)]),
                 "psm_tma_layout": (i, [i, i, i, i, P(i)]),
                 "psm_check_device_buffer": (i, [vp, i64]),
+                "psm_set_z_offset": (i, [H, i64]),
+                "psm_set_us_omega": (i, [H, i, P(d)]),
+                "psm_slot_plane": (i, [H, i, i, P(vp)]),
+                "psm_fill_slot_plane": (i, [H, i, i, i]),
                 "psm_mass_noalloc": (i, [vp, i, i, i64, d, vp, P(d)]),
             }
             for name, (res, args) in sig.items():
@@ -320,14 +324,25 @@ class Solver:
         self._geoms = []
 
     @classmethod
-    def from_case(cls, case: "W.Case", stream: int | None = None, init: bool = True) -> "Solver":
+    def from_case(cls, case: "W.Case", stream: int | None = None, init: bool = True,
+                  geoms: dict | None = None) -> "Solver":
+        """A solver for a workload case.  geoms: a dict that caches the
+        voxelised fields by (kind, params, s) across solvers (the field is
+        copied to the device by psm_set_geometry, so one host field serves
+        any number of handles)."""
         cfg = SolverConfig(case.nx, case.ny, case.nz, Q=case.Q, streaming=case.streaming, storage=case.storage,
                            fluid=case.fluid, tau=case.tau, trt_lambda=case.trt_lambda, solid=case.solid,
                            weighting=case.weighting, bc_z=case.bc_z, rho0=case.rho0, u_in=tuple(case.u_in),
                            cum_rates=tuple(case.cum_rates))
         s = cls(cfg, stream=stream)
         for bi, b in enumerate(case.bodies):
-            g = voxelize(b.kind, b.params, b.s)
+            key = (b.kind, tuple(b.params), b.s)
+            if geoms is not None and key in geoms:
+                g = geoms[key]
+            else:
+                g = voxelize(b.kind, b.params, b.s)
+                if geoms is not None:
+                    geoms[key] = g
             s.set_geometry(bi, g, b.Q0, b.R0, b.omega, b.v)
         if init:
             s.init_equilibrium(case.rho0, case.u_in)
@@ -431,6 +446,11 @@ class Solver:
         finally:
             g.field.bricks = ctypes.POINTER(ctypes.c_uint64)()  # numpy owns the words
         self._geoms.pop()
+
+    def set_us_omega(self, body: int, omega):
+        """Angular velocity of body's u_s (the pose keeps its own; psm_set_us_omega)."""
+        a, p = _d(omega, 3)
+        check(lib().psm_set_us_omega(self._h, int(body), p))
 
     @property
     def num_bodies(self) -> int:
@@ -561,3 +581,35 @@ class Solver:
     def bytes_per_cell_update(self) -> int:
         """Algorithmic bytes per cell update: one read and one write of every PDF."""
         return 2 * self.cfg.Q * STORAGE_BYTES[self.cfg.storage]
+
+    # ---- z-slab decomposition (psm_set_z_offset, psm_slot_plane, psm_fill_slot_plane) ----
+
+    def set_z_offset(self, z0: int):
+        """This handle's lattice is the planes [z0, z0 + nz) of a larger domain."""
+        check(lib().psm_set_z_offset(self._h, int(z0)))
+
+    def slot_plane_ptr(self, slot: int, z: int) -> int:
+        """Device address of slot `slot` of plane z in the buffer the next step reads."""
+        p = ctypes.c_void_p()
+        check(lib().psm_slot_plane(self._h, int(slot), int(z), ctypes.byref(p)))
+        return p.value
+
+    def slot_plane(self, slot: int, z: int):
+        """A torch view [ny, nx] of slot `slot` of plane z (no copy; valid until the next step)."""
+        import torch
+
+        c = self.cfg
+        typestr = {"fp64": "<f8", "fp32": "<f4", "fp16": "<f2", "bf16": "<f2"}[c.storage]
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (c.ny, c.nx), "typestr": typestr,
+                                        "data": (self.slot_plane_ptr(slot, z), False), "version": 3}
+
+        t = torch.as_tensor(_View(), device="cuda")
+        return t.view(torch.bfloat16) if c.storage == "bf16" else t
+
+    def fill_slot_plane(self, slot: int, z: int, direction: int | None = None):
+        """Set slot `slot` of plane z to the inflow equilibrium of `direction`
+        (default: the slot's own; stream-ordered)."""
+        d = slot if direction is None else direction
+        check(lib().psm_fill_slot_plane(self._h, int(slot), int(z), int(d)))

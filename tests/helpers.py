@@ -52,7 +52,8 @@ def ft_err(a, b, lever=1.0):
     that components that vanish by symmetry are compared at the scale of the
     ones that do not.  The torque about z (the one the adjoint's J is built on)
     is also compared at its own scale, max |dT_z| / max |T_z| of b, wherever it
-    is at least a tenth of the largest torque component of that body in b."""
+    is at least a tenth of that body's torque scale above (a torque that is
+    only round-off, as on a sphere in axial flow, is not)."""
     fa, fb = np.asarray(a["ft"]), np.asarray(b["ft"])
     sF = np.abs(fb[..., :3]).max()
     sT = max(np.abs(fb[..., 3:]).max(), sF * lever)
@@ -63,7 +64,8 @@ def ft_err(a, b, lever=1.0):
         fb.reshape(-1, fb.shape[-2], 6) if fb.ndim == 3 else fb[:, None]
     for body in range(tb.shape[1]):
         sTz = np.abs(tb[:, body, 5]).max()
-        if sTz > 0 and sTz >= 0.1 * np.abs(tb[:, body, 3:]).max():
+        scale = max(np.abs(tb[:, body, 3:]).max(), np.abs(tb[:, body, :3]).max() * lever)
+        if sTz > 0 and sTz >= 0.1 * scale:
             eTz = max(eTz, np.abs(ta[:, body, 5] - tb[:, body, 5]).max() / sTz)
     return max(eF, eT, eTz)
 

@@ -109,7 +109,8 @@ def test_reference_arm_line(fluid):
     import subprocess
     import sys
 
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3"]
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c2", "--steps", "1",
+           "--warmup", "3"]
     if fluid:
         cmd += ["--fluid", fluid]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)

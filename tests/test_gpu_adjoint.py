@@ -79,6 +79,59 @@ def test_adjoint_fp64_matches_tangent_linear(kw):
     assert abs(gu[2] - du) <= 1e-9 * abs(du)
 
 
+def tiny_case(fluid="trt", solid=1, weighting=1, streaming="aa", bc_z=1, at_ghost=False, steps=12):
+    """6 x 6 x 8 cells, a rotating ellipsoid (at_ghost: low in z, covering the
+    planes next to the lower ghost plane, and a second, translating box)."""
+    z = 1.4 if at_ghost else 4.0
+    bodies = [W.BodyCase(W.ELLIPSOID, (2.2, 1.5, 1.2), 2, (3.0, 3.1, z), omega=(0.01, -0.02, 0.05))]
+    if at_ghost:
+        bodies.append(W.BodyCase(W.BOX, (1.0, 1.0, 1.0), 1, (3.2, 2.8, 6.3), omega=(0.0, 0.03, 0.0),
+                                 v=(0.01, 0.0, -0.02)))
+    return W.Case("adj_tiny", 6, 6, 8, Q=19, storage="fp64", streaming=streaming, fluid=fluid, tau=0.62,
+                  solid=solid, weighting=weighting, bc_z=bc_z, u_in=(0.004, -0.003, 0.03), steps=steps,
+                  bodies=bodies)
+
+
+def oracle_gradient(case):
+    import oracle
+
+    cfg = oracle.Config(nx=case.nx, ny=case.ny, nz=case.nz, Q=case.Q, bc_z=case.bc_z, rho0=case.rho0,
+                        u_in=tuple(case.u_in), fluid={"bgk": 0, "trt": 1}[case.fluid], tau=case.tau,
+                        trt_lambda=case.trt_lambda, solid=case.solid, weighting=case.weighting)
+    specs = []
+    for b in case.bodies:
+        sub, lo = oracle.voxelize(b.kind, b.params, b.s)
+        specs.append(oracle.BodySpec(sub=sub, s=b.s, lo=lo, R0=b.R0, Q0=np.array(b.Q0), omega=b.omega, v=b.v))
+    return oracle.tangent_gradient(cfg, specs, case.steps, case.rho0, tuple(case.u_in))
+
+
+PER_CELL = [dict(), dict(fluid="bgk"), dict(solid=2), dict(solid=3), dict(weighting=0), dict(streaming="twogrid"),
+            dict(bc_z=0), dict(at_ghost=True), dict(at_ghost=True, streaming="twogrid", solid=3)]
+
+
+@pytest.mark.parametrize("kw", PER_CELL)
+def test_adjoint_fp64_every_cell_matches_oracle(kw):
+    """The GPU FP64 gradient, cell by cell, against the oracle's FP64 gradient
+    (one tangent-linear run per cell; pinned against central differences of
+    the plain oracle in test_oracle_tangent.py): 1e-9 relative per cell plus
+    1e-11 of max |grad|; grad_omega and grad_u_in component by component."""
+    case = tiny_case(**kw)
+    J, ge, gw, gu = gpu_grad(case, K=4)
+    J_or, gd, gw_or, gu_or = oracle_gradient(case)
+    assert abs(J - J_or) <= 1e-12 * abs(J_or)
+    scale = np.abs(gd).max()
+    err = np.abs(ge - gd)
+    bound = 1e-9 * np.abs(gd) + 1e-11 * scale
+    worst = int(np.argmax(err - bound))
+    print(f"{kw}: max |grad_gpu - grad_oracle| = {err.max():.3e} (max |grad| {scale:.3e}); "
+          f"omega {np.abs(gw - gw_or[:len(gw)]).max():.3e}, u_in {np.abs(gu - gu_or).max():.3e}")
+    assert np.all(err <= bound), (np.unravel_index(worst, ge.shape), ge.reshape(-1)[worst], gd.reshape(-1)[worst])
+    assert (np.abs(gd) > 1e-6 * scale).sum() > case.cells // 4
+    gscale = np.abs(gw_or).max()
+    assert np.all(np.abs(gw - gw_or) <= 1e-9 * np.abs(gw_or) + 1e-11 * gscale), (gw, gw_or)
+    assert np.all(np.abs(gu - gu_or) <= 1e-9 * np.abs(gu_or) + 1e-11 * np.abs(gu_or).max()), (gu, gu_or)
+
+
 @pytest.mark.parametrize("solid", [1, 2, 3])
 @pytest.mark.parametrize("fluid", ["trt", "bgk"])
 def test_adjoint_fluid_tiles_match_tangent_linear(solid, fluid):
@@ -206,6 +259,53 @@ def test_adjoint_c4_full_vs_fp64_fd(storage):
         assert fp64_ok and worst_scaled <= 1e-6
     else:
         assert worst_rel <= 1e-2 and worst_scaled <= 1e-3
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_adjoint_c4_full_omega_and_inflow_vs_fp64_fd(storage):
+    """The adjoint workload at full size (128^3, 512 steps, checkpoint every 64):
+    d J / d omega_z and d J / d u_in,z against central differences of the FP64
+    GPU forward at the relative step h = 1e-4 of the configuration, Richardson
+    extrapolated.  omega is varied in u_s only (psm_set_us_omega: the geometry
+    sequence stays the nominal one, as the adjoint defines the derivative);
+    u_in in the ghost planes and the initial equilibrium (the recording
+    declares the initial state f^eq(rho0, u_in)).  FP64: 1e-6 relative; FP32
+    forward and adjoint: 1e-2."""
+    from paper_2502_20049_gb300 import psm
+
+    case = W.c4_adjoint().with_(storage=storage)
+    J, ge, gw, gu = gpu_grad(case, K=64)
+    c64 = case.with_(storage="fp64")
+    w0 = np.array(c64.bodies[0].omega, dtype=float)
+    u0 = np.array(c64.u_in, dtype=float)
+
+    def J_of(omega=None, u_in=None):
+        c = c64 if u_in is None else c64.with_(u_in=tuple(u_in))
+        sol = psm.Solver.from_case(c)
+        if omega is not None:
+            sol.set_us_omega(0, omega)
+        sol.step(c.steps)
+        j = sol.force_torque(0)[:, 5].mean()
+        sol.close()
+        return j
+
+    def rich(f, x0, k, hrel):
+        h = hrel * abs(x0[k])
+
+        def D(hh):
+            e = np.zeros(3)
+            e[k] = hh
+            return (f(x0 + e) - f(x0 - e)) / (2 * hh)
+
+        return (4 * D(h / 2) - D(h)) / 3
+
+    fd_w = rich(lambda w: J_of(omega=w), w0, 2, 1e-4)
+    fd_u = rich(lambda u: J_of(u_in=u), u0, 2, 1e-4)
+    ew, eu = abs(gw[0, 2] - fd_w) / abs(fd_w), abs(gu[2] - fd_u) / abs(fd_u)
+    print(f"C4 128^3 {storage}: dJ/domega_z adjoint {gw[0, 2]:.9e} fd {fd_w:.9e} rel {ew:.2e}; "
+          f"dJ/du_in,z adjoint {gu[2]:.9e} fd {fd_u:.9e} rel {eu:.2e}")
+    tol = 1e-6 if storage == "fp64" else 1e-2
+    assert ew <= tol and eu <= tol
 
 
 def test_autograd_function_fp64():

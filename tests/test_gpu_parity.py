@@ -113,6 +113,9 @@ RAGGED = [
     dict(nx=37, ny=23, nz=19, solid=2, weighting=0, bc_z=1),
     dict(nx=37, ny=23, nz=19, solid=3, weighting=1, bc_z=0),
     dict(nx=33, ny=5, nz=7, solid=1, weighting=1, bc_z=1),
+    # row lengths between powers of two (96, 161): tiles of 128 x 2 and 256 x 1 cells
+    dict(nx=96, ny=6, nz=9, solid=1, weighting=1, bc_z=1),
+    dict(nx=161, ny=3, nz=5, solid=3, weighting=0, bc_z=0),
 ]
 
 
