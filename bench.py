@@ -396,6 +396,7 @@ def run_ours(args):
                    "per body, computed on the host and passed as launch parameters), then psm_force_torque of "
                    "every body into pinned host memory (synchronising); no PDF state is copied: it is the "
                    "solver's state and stays in HBM"}
+    kernel = sol.kernel_variant
     sol.close()
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -415,7 +416,7 @@ def run_ours(args):
             same = (name == args.workload and streaming == case.streaming and storage == case.storage
                     and fluid == args.fluid and args.scale == 1.0)
             if same:
-                vs[vkey] = {"mlups": round(cells * args.steps / t / 1e6, 1), "kernel": sol.kernel_variant,
+                vs[vkey] = {"mlups": round(cells * args.steps / t / 1e6, 1), "kernel": kernel,
                             "streaming": case.streaming, "hbm_gbs": round(achieved, 1),
                             "frac": round(achieved / peak, 4), "bytes_per_cell": bpc, "steps": args.steps,
                             "note": "the headline run"}

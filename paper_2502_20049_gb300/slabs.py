@@ -25,6 +25,12 @@ step, and before an AA odd step its lo/UP) take the inflow equilibrium
 instead, of the slot's own direction in the natural layout and of the
 opposite direction in the AA swapped layout.
 
+A slab's own state is the domain's state on its planes after every
+two-grid step and after every even number of AA steps (natural layout); in
+the AA swapped layout, after an odd number of steps, a face cell's incoming
+populations still sit in the neighbouring slab's slots until the next odd
+step's exchange, so export the slabs (psm_get_state) after an even number.
+
 Per exchange a face moves |UP| = 5 (D3Q19) or 9 (D3Q27) planes of nx * ny
 values each way.  The force, torque and mass of the domain are the sums of the
 slabs' (FP64, ``allreduce``).
