@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_fp16.h>
 
 #include "psm_internal.h"
@@ -288,11 +289,20 @@ __device__ __forceinline__ int tile_coords(const Tiling& t, int tile, int& x, in
   return 0;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class V>
+__device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
   return v;
 }
+
+// Type of one cell's force/torque contribution and of its warp partial sum:
+// the compute precision (FP64 arithmetic for FP64 storage; FP32 otherwise).
+// The per-warp partials are added into FP64 block slots, and the block and
+// grid sums are FP64 (on GB300 an FP64 instruction costs about 64 FP32 ones,
+// so the 32-cell partials stay in the arithmetic's own precision).
+template <class T>
+using ft_t = typename std::conditional<sizeof(T) == 8, double, float>::type;
 
 // Block-wide ordered reduction of per-block values v[0..ncomp) held in shared
 // memory `blk` into partials[blockIdx.x]; the last block to finish sums all
@@ -672,7 +682,7 @@ __device__ __forceinline__ void cumulant_relax(const ConstT<T>& C, T (&f)[19], T
 // B = 0 takes exactly the arithmetic of fluid_relax.
 template <class T, int Q, int FL>
 __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* bodies, T (&f)[Q], int x, int y,
-                                            int z, unsigned cell, int& owner, bool& solid_cell, double (&ft)[6]) {
+                                            int z, unsigned cell, int& owner, bool& solid_cell, ft_t<T> (&ft)[6]) {
   // (x, y, z): world cell indices (z includes the slab offset); cell: this grid's index
   const ConstT<T>& C = cst<T>(p);
   const T om_a = C.om_a, om_b = C.om_b;
@@ -772,10 +782,20 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
     if (lat_cz(i)) gz += T(lat_cz(i)) * d;
   }
   if (owner >= 0) {
-    // Eq. 10 / 11 per cell; the body receives minus the solid's momentum transfer
-    const double Gx = (double)(Bw * gx), Gy = (double)(Bw * gy), Gz = (double)(Bw * gz);
+    // Eq. 10 / 11 per cell, in the arithmetic's precision (ft_t); the body
+    // receives minus the solid's momentum transfer
+    const T Gx = Bw * gx, Gy = Bw * gy, Gz = Bw * gz;
     const DevBody& b = bodies[owner];
-    const double Rx = (double)x + 0.5 - b.R[0], Ry = (double)y + 0.5 - b.R[1], Rz = (double)z + 0.5 - b.R[2];
+    T Rx, Ry, Rz;
+    if constexpr (sizeof(T) == 4) {
+      Rx = (T(x) + T(0.5)) - b.Rf[0];
+      Ry = (T(y) + T(0.5)) - b.Rf[1];
+      Rz = (T(z) + T(0.5)) - b.Rf[2];
+    } else {
+      Rx = (double)x + 0.5 - b.R[0];
+      Ry = (double)y + 0.5 - b.R[1];
+      Rz = (double)z + 0.5 - b.R[2];
+    }
     ft[0] = -Gx;
     ft[1] = -Gy;
     ft[2] = -Gz;
@@ -858,9 +878,11 @@ __device__ __forceinline__ void psm_load(const StepParams& p, const Stencil& sn,
 }
 
 // Per-warp force/torque accumulation into s_ft[warp] (fixed order: warp
-// butterfly, then in tile order).  All 32 lanes must call it.
+// butterfly in the contribution's precision, then added in FP64 in tile
+// order).  All 32 lanes must call it.
+template <class V>
 __device__ __forceinline__ void warp_ft(double (*s_ft)[PSM_MAX_BODIES * 6], int nb, bool contributes, int owner,
-                                        const double (&ft)[6]) {
+                                        const V (&ft)[6]) {
   if (nb == 0 || !__any_sync(0xffffffffu, contributes)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int bi = 0; bi < nb; ++bi) {
@@ -868,8 +890,8 @@ __device__ __forceinline__ void warp_ft(double (*s_ft)[PSM_MAX_BODIES * 6], int 
     if (!__any_sync(0xffffffffu, mine)) continue;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const double v = warp_sum(mine ? ft[k] : 0.0);
-      if (lane == 0) s_ft[warp][bi * 6 + k] += v;
+      const V v = warp_sum(mine ? ft[k] : V(0));
+      if (lane == 0) s_ft[warp][bi * 6 + k] += (double)v;
     }
   }
 }
@@ -1001,7 +1023,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
     const bool active = x < p.g.nx && y < p.g.ny;
     int owner = -1;
     bool solid_cell = false;
-    double ft[6] = {0, 0, 0, 0, 0, 0};
+    ft_t<T> ft[6] = {0, 0, 0, 0, 0, 0};
     if (active) {
       const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
       Stencil sn;
@@ -1375,7 +1397,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
       }
       int owner = -1;
       bool solid_cell = false;
-      double ft[6] = {0, 0, 0, 0, 0, 0};
+      ft_t<T> ft[6] = {0, 0, 0, 0, 0, 0};
       if (GEN) psm_collide<T, Q, FL>(p, s_body, f, x, y, z + p.g.z0, cell, owner, solid_cell, ft);
       else fluid_collide<T, Q, FL>(p, f);
       if constexpr (L::STORE_TMA) {

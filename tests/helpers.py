@@ -73,11 +73,12 @@ def ft_err(a, b, lever=1.0):
 def assert_ft_same(fa, fb, storage):
     """Force/torque series of two runs with bit-identical states.  Kernels with
     the same tiling reduce in the same order and agree bit for bit; the TMA
-    kernel gives 2-byte storage tiles of two cells per thread, so its FP64 sums
-    (torque terms are products, not exact) run in another order: 1e-12 of the
-    largest component."""
+    kernel gives 2-byte storage tiles of two cells per thread, so its warps
+    hold other cells and their FP32 partial sums (32 cells, then added in
+    FP64) round differently: 1e-6 of the largest component (a few FP32
+    round-offs of a warp's terms)."""
     fa, fb = np.asarray(fa), np.asarray(fb)
     if storage in ("fp16", "bf16"):
-        assert np.abs(fa - fb).max() <= 1e-12 * np.abs(fb).max()
+        assert np.abs(fa - fb).max() <= 1e-6 * np.abs(fb).max()
     else:
         assert np.array_equal(fa, fb)
