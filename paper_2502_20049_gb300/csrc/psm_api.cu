@@ -56,6 +56,7 @@ struct BufMaps {
 struct HostBody {
   unsigned long long* d_bricks = nullptr;
   unsigned char* d_occ = nullptr;  // occupancy (DevBody::occ)
+  unsigned* d_occ8 = nullptr;      // block occupancy bits (DevBody::occ8)
   int64_t gx = 0, gy = 0, gz = 0;
   int s = 0, wpb = 1;
   double lo[3] = {0, 0, 0};
@@ -321,6 +322,33 @@ __global__ void k_occupancy(const unsigned long long* __restrict__ bricks, int g
   }
 }
 
+// one thread per block of 8^3 occupancy bytes: its bit is set iff a byte is
+__global__ void k_occupancy8(const unsigned char* __restrict__ occ, int ox, int oy, int oz, unsigned* occ8) {
+  const int bx = (ox + 7) / 8, by = (oy + 7) / 8, bz = (oz + 7) / 8;
+  const long long n = (long long)bx * by * bz;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(idx % bx), iy = (int)((idx / bx) % by), iz = (int)(idx / ((long long)bx * by));
+    bool any = false;
+    for (int z = iz * 8; z < iz * 8 + 8 && z < oz && !any; ++z)
+      for (int y = iy * 8; y < iy * 8 + 8 && y < oy && !any; ++y)
+        for (int x = ix * 8; x < ix * 8 + 8 && x < ox; ++x)
+          if (occ[((long long)z * oy + y) * ox + x]) {
+            any = true;
+            break;
+          }
+    if (any) atomicOr(occ8 + (idx >> 5), 1u << (idx & 31));
+  }
+}
+
+cudaError_t launch_occupancy8(const unsigned char* occ, int ox, int oy, int oz, unsigned* occ8, cudaStream_t st) {
+  const long long n = (long long)((ox + 7) / 8) * ((oy + 7) / 8) * ((oz + 7) / 8);
+  long long b = (n + PSM_THREADS - 1) / PSM_THREADS;
+  if (b > 4096) b = 4096;
+  k_occupancy8<<<(int)(b < 1 ? 1 : b), PSM_THREADS, 0, st>>>(occ, ox, oy, oz, occ8);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, int gz, int wpb, unsigned char* occ,
                              cudaStream_t st) {
   const long long n = (long long)(gx + 1) * (gy + 1) * (gz + 1);
@@ -454,6 +482,9 @@ DevBody dev_body(const psm_solver* h, int bi, int64_t n) {
   body_pose(b, h->remap_frozen ? h->frozen_step : n, Q, R);
   d.bricks = b.d_bricks;
   d.occ = b.d_occ;
+  d.occ8 = b.d_occ8;
+  d.o8x = (int)((b.gx + 1 + 7) / 8);
+  d.o8y = (int)((b.gy + 1 + 7) / 8);
   d.gx = (int)b.gx;
   d.gy = (int)b.gy;
   d.gz = (int)b.gz;
@@ -895,6 +926,7 @@ int psm_destroy(psm_handle h) {
   for (int b = 0; b < PSM_MAX_BODIES; ++b) {
     cudaFree(h->body[b].d_bricks);
     cudaFree(h->body[b].d_occ);
+    cudaFree(h->body[b].d_occ8);
   }
   cudaFree(h->d_partials);
   cudaFree(h->d_ticket);
@@ -1181,6 +1213,16 @@ int psm_set_geometry(psm_handle h, int body, const psm_geom_field* field, const 
   PSM_CUDA(cudaMalloc(&b.d_occ, nocc), "geometry occupancy allocation");
   PSM_CUDA(psm::launch_occupancy(b.d_bricks, (int)field->gx, (int)field->gy, (int)field->gz, wpb, b.d_occ, h->stream),
            "geometry occupancy kernel");
+  cudaFree(b.d_occ8);
+  b.d_occ8 = nullptr;
+  {
+    const int ox = (int)field->gx + 1, oy = (int)field->gy + 1, oz = (int)field->gz + 1;
+    const size_t nb8 = (size_t)((ox + 7) / 8) * ((oy + 7) / 8) * ((oz + 7) / 8);
+    const size_t words8 = (nb8 + 31) / 32;
+    PSM_CUDA(cudaMalloc(&b.d_occ8, words8 * sizeof(unsigned)), "geometry block occupancy allocation");
+    PSM_CUDA(cudaMemsetAsync(b.d_occ8, 0, words8 * sizeof(unsigned), h->stream), "geometry block occupancy");
+    PSM_CUDA(psm::launch_occupancy8(b.d_occ, ox, oy, oz, b.d_occ8, h->stream), "geometry block occupancy kernel");
+  }
   PSM_CUDA(cudaStreamSynchronize(h->stream), "geometry occupancy");
   b.gx = field->gx;
   b.gy = field->gy;

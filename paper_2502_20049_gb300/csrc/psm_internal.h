@@ -51,6 +51,12 @@ struct DevBody {
   // occupancy [gz + 1][gy + 1][gx + 1] bytes, index c + 1 for c = -1 .. g - 1 per
   // axis: non-zero iff a brick in {c, c + 1}^3 has a set bit (nullptr: none)
   const unsigned char* occ;
+  // occupancy of blocks of 8^3 occupancy cells, one bit each (index
+  // (bz o8y + by) o8x + bx for occupancy index c + 1 = 8 b + 0..7 per axis):
+  // set iff an occupancy byte of the block is (nullptr: none); a small array
+  // that stays in L1, tested before the occupancy byte itself
+  const unsigned* occ8;
+  int o8x, o8y;
   int gx, gy, gz;
   int s;    // super-sampling depth
   int wpb;  // 64-bit words per brick
@@ -291,6 +297,9 @@ cudaError_t launch_body_update(BodyDyn* dyn, DevBody* dev, const double* ft, uns
 // occupancy of a geometry field (DevBody::occ) from its bricks (device)
 cudaError_t launch_occupancy(const unsigned long long* bricks, int gx, int gy, int gz, int wpb, unsigned char* occ,
                              cudaStream_t st);
+// block occupancy bits (DevBody::occ8, zeroed by the caller) from the occupancy
+// bytes of a (gx + 1) x (gy + 1) x (gz + 1) array
+cudaError_t launch_occupancy8(const unsigned char* occ, int ox, int oy, int oz, unsigned* occ8, cudaStream_t st);
 
 #define PSM_DECLARE_STORAGE(NAME)                                                          \
   cudaError_t launch_step_##NAME(int Q, int mode, int fl, const StepParams& p, cudaStream_t st); \

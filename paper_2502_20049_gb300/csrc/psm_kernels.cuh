@@ -148,7 +148,13 @@ __device__ __forceinline__ float remap_eps(const DevBody& b, int x, int y, int z
     if (glast < 0 || gc[k] >= dims[k]) return 0.0f;
   }
   // the block touches coarse cells {gc, gc + 1}^3 at most: none holds a set bit
-  // where the occupancy byte is zero (then eps is exactly 0)
+  // where the occupancy byte is zero (then eps is exactly 0); the block bit of
+  // 8^3 occupancy bytes is tested first (a small array that stays in L1,
+  // where the bytes come from L2 or memory)
+  if (b.occ8) {
+    const long long bi = ((long long)((gc[2] + 1) >> 3) * b.o8y + ((gc[1] + 1) >> 3)) * b.o8x + ((gc[0] + 1) >> 3);
+    if (!((__ldg(b.occ8 + (bi >> 5)) >> (unsigned)(bi & 31)) & 1u)) return 0.0f;
+  }
   if (b.occ) {
     const long long oi = ((long long)(gc[2] + 1) * (b.gy + 1) + (gc[1] + 1)) * (long long)(b.gx + 1) + (gc[0] + 1);
     if (!__ldg(b.occ + oi)) return 0.0f;
@@ -735,51 +741,96 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
     fluid_relax<T, Q, FL>(C, fc, drho, rho, ux, uy, uz, uu);
   }
   T gx = 0, gy = 0, gz = 0;
-  {
-    const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
-    const T m0 = f[0] - feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
-    T of;
-    if constexpr (FL == 2) of = fc[0] - f[0];
-    else of = -(om_a + om_b) * n0;
-    T os;
-    if (p.solid == PSM_SC1) os = n0 - m0;
-    else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
-    else os = T(0);
-    f[0] = f[0] + omB * of + Bw * os;
-  }
+  if constexpr (FL == 2) {
+    {
+      const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
+      const T m0 = f[0] - feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
+      const T of = fc[0] - f[0];
+      T os;
+      if (p.solid == PSM_SC1) os = n0 - m0;
+      else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
+      else os = T(0);
+      f[0] = f[0] + omB * of + Bw * os;
+    }
 #pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    const int j = i + 1;
-    const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
-    const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
-    const T mi = f[i] - feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
-    const T mj = f[j] - feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
-    T ofi, ofj;
-    if constexpr (FL == 2) {
-      ofi = fc[i] - f[i];
-      ofj = fc[j] - f[j];
-    } else {
-      ofi = FL == 1 ? (-om_a * ni - om_b * nj) : (-om_a * ni);
-      ofj = FL == 1 ? (-om_a * nj - om_b * ni) : (-om_a * nj);
+    for (int i = 1; i < Q; i += 2) {
+      const int j = i + 1;
+      const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
+      const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
+      const T mi = f[i] - feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
+      const T mj = f[j] - feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
+      const T ofi = fc[i] - f[i], ofj = fc[j] - f[j];
+      T osi, osj;
+      if (p.solid == PSM_SC1) {
+        osi = nj - mi;
+        osj = ni - mj;
+      } else if (p.solid == PSM_SC2) {
+        osi = -mi * inv_tau;
+        osj = -mj * inv_tau;
+      } else {
+        osi = mj - mi;
+        osj = mi - mj;
+      }
+      f[i] = f[i] + omB * ofi + Bw * osi;
+      f[j] = f[j] + omB * ofj + Bw * osj;
+      // c_j = -c_i: sum_i Omega^S_i c_i over the pair
+      const T d = osi - osj;
+      if (lat_cx(i)) gx += T(lat_cx(i)) * d;
+      if (lat_cy(i)) gy += T(lat_cy(i)) * d;
+      if (lat_cz(i)) gz += T(lat_cz(i)) * d;
     }
-    T osi, osj;
-    if (p.solid == PSM_SC1) {
-      osi = nj - mi;
-      osj = ni - mj;
-    } else if (p.solid == PSM_SC2) {
-      osi = -mi * inv_tau;
-      osj = -mj * inv_tau;
-    } else {
-      osi = mj - mi;
-      osj = mi - mj;
+  } else {
+    // BGK / TRT in pair form (c_j = -c_i).  With s = f_i + f_j, d = f_i - f_j
+    // and the equilibria split into even and odd parts, f^eq_i,j - w rho0 =
+    // ev +- od at u and evs +- ods at u_s, the half sums and differences
+    //   n+ = s/2 - ev, n- = d/2 - od,  m+ = s/2 - evs, m- = d/2 - ods
+    // give Omega^F_i,j = -omega+ n+ -+ omega- n- and
+    //   SC1: Omega^S_i,j = n_j - m_i, n_i - m_j = (n+ - m+) +- (-n- - m-),
+    //   SC2: -(m+ +- m-) / tau,   SC3: m_j - m_i, m_i - m_j = +-(-2 m-);
+    // then f*_i,j = P +- M with P = s/2 + (1 - B) OmF+ + B OmS+ and
+    // M = d/2 + (1 - B) OmF- + B OmS-, and the pair adds 2 OmS- c_i to
+    // sum_i Omega^S_i c_i.
+    const T wp = om_a + om_b, wm = om_a - om_b;
+    const T bu = drho - T(1.5) * rho * uu, bs = drho - T(1.5) * rho * usus;
+    {
+      const T w0 = T(lat_w<Q>(0));
+      const T n0 = f[0] - w0 * bu, m0 = f[0] - w0 * bs;
+      T os;
+      if (p.solid == PSM_SC1) os = n0 - m0;
+      else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
+      else os = T(0);
+      f[0] = f[0] + omB * (-wp * n0) + Bw * os;
     }
-    f[i] = f[i] + omB * ofi + Bw * osi;
-    f[j] = f[j] + omB * ofj + Bw * osj;
-    // c_j = -c_i: sum_i Omega^S_i c_i over the pair
-    const T d = osi - osj;
-    if (lat_cx(i)) gx += T(lat_cx(i)) * d;
-    if (lat_cy(i)) gy += T(lat_cy(i)) * d;
-    if (lat_cz(i)) gz += T(lat_cz(i)) * d;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const int j = i + 1;
+      const T w = T(lat_w<Q>(i));
+      const T wr = w * rho;
+      const T cu = cdot(i, ux, uy, uz), cs = cdot(i, usx, usy, usz);
+      const T ev = w * bu + T(4.5) * wr * cu * cu, od = T(3) * wr * cu;
+      const T evs = w * bs + T(4.5) * wr * cs * cs, ods = T(3) * wr * cs;
+      const T hs = T(0.5) * (f[i] + f[j]), hd = T(0.5) * (f[i] - f[j]);
+      const T np = hs - ev, nm = hd - od, mp = hs - evs, mm = hd - ods;
+      T sp, sm;
+      if (p.solid == PSM_SC1) {
+        sp = np - mp;
+        sm = -nm - mm;
+      } else if (p.solid == PSM_SC2) {
+        sp = -mp * inv_tau;
+        sm = -mm * inv_tau;
+      } else {
+        sp = T(0);
+        sm = T(-2) * mm;
+      }
+      const T P = hs + omB * (-wp * np) + Bw * sp;
+      const T M = hd + omB * (-wm * nm) + Bw * sm;
+      f[i] = P + M;
+      f[j] = P - M;
+      const T d = T(2) * sm;
+      if (lat_cx(i)) gx += T(lat_cx(i)) * d;
+      if (lat_cy(i)) gy += T(lat_cy(i)) * d;
+      if (lat_cz(i)) gz += T(lat_cz(i)) * d;
+    }
   }
   if (owner >= 0) {
     // Eq. 10 / 11 per cell, in the arithmetic's precision (ft_t); the body
