@@ -1220,10 +1220,10 @@ __device__ __forceinline__ int lat_c_rt(unsigned long long bits, int i) { return
 //   input, own-cell modes (two-grid, AA even): one [Q][TY][TX] box per tile
 //     (TX TY = 256 CPT): slot i of cell r of thread t at element
 //     256 CPT i + 256 r + t;
-//   input, AA odd (TX = 256, TY = 1): per direction i a record of ROW bytes
-//     holding, from byte 128, the 256 values of slot opp(i) at x - c_i for the
-//     tile's cells, preceded and followed by a 16-byte x-edge chunk, so that
-//     cell lx reads element lx - c_x of it with no branch;
+//   input, AA odd (TX = 256, TY = 1): per direction i the 256 values of slot
+//     opp(i) at x - c_i for the tile's cells at byte 128 + i ROW, preceded and
+//     followed by a 16-byte x-edge chunk, so that cell lx reads element
+//     lx - c_x of it with no branch;
 //   output (AA even): per warp a [Q][32] box of its 32 cells (WBOX bytes),
 //     written back by the warp's own TMA tensor store.
 // The stage count NST fills the shared memory of the resident blocks the
@@ -1241,8 +1241,12 @@ struct TmaLayout {
   static constexpr int r128(int b) { return ((b + 127) / 128) * 128; }
   static constexpr int BOX_BYTES = Q * PSM_THREADS * CPT * (int)sizeof(S);
   static constexpr int BOX = r128(BOX_BYTES);
-  static constexpr int ROW = r128(128 + PSM_THREADS * (int)sizeof(S) + 16);
-  static constexpr int STAGE = LOAD_OWN ? BOX : Q * ROW;
+  // AA odd records: direction i's row of 256 values at byte 128 + i ROW of the
+  // stage (128-byte aligned), its 16-byte edge chunks right before and after
+  // it; ROW >= row + 32 bytes keeps the chunk after one row clear of the chunk
+  // before the next (which sits in the last 16 bytes below that row)
+  static constexpr int ROW = r128(PSM_THREADS * (int)sizeof(S) + 32);
+  static constexpr int STAGE = LOAD_OWN ? BOX : r128(Q * ROW + 16);
   static constexpr int WBOX = r128(Q * 32 * (int)sizeof(S));
   static constexpr int OUT = STORE_TMA ? (PSM_THREADS / 32) * WBOX : 0;
   static constexpr int SM_SMEM = 233472;
@@ -1286,7 +1290,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
 #ifdef PSM_TMA_REFILL_LAG
   constexpr int LAG = PSM_TMA_REFILL_LAG < NST - 1 ? PSM_TMA_REFILL_LAG : NST - 2;
 #else
-  constexpr int LAG = NST >= 4 ? 2 : NST - 2;
+  constexpr int LAG = NST >= 5 ? 2 : (NST >= 3 ? 1 : 0);
 #endif
   constexpr int EP = L::EP;
   __shared__ double s_ft[PSM_THREADS / 32][PSM_MAX_BODIES * 6];
