@@ -254,6 +254,41 @@ def time_steps(sol, steps: int, stream) -> float:
     return ev0.elapsed_time(ev1) / 1e3
 
 
+def e2e_with_output(sol, args, cells, world, dist, nb, ft_out):
+    """The end-to-end loop of the headline plus, every `--e2e-output-every`
+    steps, the density and velocity of every cell (psm_get_macroscopic, FP64)
+    copied into pinned host buffers allocated before the timed region.  None
+    when the buffers would take more than a quarter of the host's free memory."""
+    import torch
+
+    from paper_2502_20049_gb300 import replicas
+
+    k = args.e2e_output_every
+    need = 32 * cells
+    free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    if k <= 0 or need > free // 4:
+        return {"skipped": f"needs {need / 1e9:.1f} GB of pinned host memory, {free / 1e9:.1f} GB free"}
+    rho = torch.empty(cells, dtype=torch.float64, pin_memory=True)
+    u = torch.empty(3 * cells, dtype=torch.float64, pin_memory=True)
+    sol.synchronize()
+    t0 = time.perf_counter()
+    exports = 0
+    for s in range(args.steps):
+        sol.step(1)
+        for b in range(nb):
+            sol.force_torque(b, sol.step_count - 1, 1, out=ft_out)
+        if (s + 1) % k == 0:
+            sol.macroscopic(rho, u)
+            exports += 1
+    t = replicas.max_over_ranks(dist, time.perf_counter() - t0, device="cuda")
+    assert bool(torch.isfinite(rho[:: max(1, cells // 4096)]).all())
+    return {"value": round(replicas.aggregate_rate(cells * args.steps, world, t) / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": 96 * nb, "d2h_bytes_per_step": round(48 * nb + need * exports / args.steps),
+            "note": f"as e2e, and every {k} steps the density and velocity of every cell (psm_get_macroscopic, "
+                    f"FP64, {need / 1e9:.2f} GB) copied to pinned host memory; {exports} exports in the timed "
+                    f"region"}
+
+
 def variant_mlups(name, streaming, storage, steps, warmup, stream, peak, fluid=None, geoms=None):
     """MLUPS and HBM roofline fraction of one storage / streaming / fluid-operator
     variant of a workload (same timing rules as the headline)."""
@@ -396,6 +431,7 @@ def run_ours(args):
                    "per body, computed on the host and passed as launch parameters), then psm_force_torque of "
                    "every body into pinned host memory (synchronising); no PDF state is copied: it is the "
                    "solver's state and stays in HBM"}
+    e2e_out = e2e_with_output(sol, args, cells, world, dist, nb, out)
     kernel = sol.kernel_variant
     sol.close()
 
@@ -406,7 +442,7 @@ def run_ours(args):
                        "stencil": f"D3Q{case.Q}", "parallelism": f"replicas x{world}",
                        "l2": f"PDF working set {cells * case.Q * psm.STORAGE_BYTES[case.storage] / 1e9:.2f} GB "
                              f"> 129 MB L2, no flush"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps}
+            "roofline": roofline, "e2e": e2e, "e2e_output": e2e_out, "gpu_launches": args.steps}
     ck = clk.summary()
     if ck:
         line["clocks"] = ck
@@ -456,6 +492,8 @@ def main():
     ap.add_argument("--fluid", default=None, choices=["bgk", "trt", "cumulant"],
                     help="fluid operator (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-output-every", type=int, default=100,
+                    help="steps between the macroscopic exports of the second end-to-end loop (0: skip it)")
     ap.add_argument("--no-extras", action="store_true", help="skip the variant and adjoint measurements")
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint cost measurement")
     ap.add_argument("--scale", type=float, default=1.0,

@@ -163,6 +163,8 @@ def _ptr(out, dtype, count):
     if hasattr(out, "data_ptr"):  # torch tensor, host or device
         if out.numel() != count:
             raise ValueError(f"expected {count} elements, got {out.numel()}")
+        if str(out.dtype).replace("torch.", "") != np.dtype(dtype).name or not out.is_contiguous():
+            raise ValueError(f"expected a contiguous {np.dtype(dtype).name} tensor, got {out.dtype}")
         return ctypes.c_void_p(out.data_ptr()), out
     if not isinstance(out, np.ndarray) or out.dtype != dtype or out.size != count or not out.flags.c_contiguous:
         raise ValueError(f"expected a C-contiguous {dtype} array of {count} elements")
@@ -513,11 +515,15 @@ class Solver:
                                   ctypes.c_void_p(out.ctypes.data)))
         return out
 
-    def macroscopic(self):
+    def macroscopic(self, rho=None, u=None):
+        """(rho[nz, ny, nx], u[nz, ny, nx, 3]) in FP64, into new numpy arrays or
+        the given ones (numpy or torch, host or device)."""
         c = self.cfg
-        rho = np.zeros((c.nz, c.ny, c.nx))
-        u = np.zeros((c.nz, c.ny, c.nx, 3))
-        check(lib().psm_get_macroscopic(self._h, ctypes.c_void_p(rho.ctypes.data), ctypes.c_void_p(u.ctypes.data)))
+        rho = np.zeros((c.nz, c.ny, c.nx)) if rho is None else rho
+        u = np.zeros((c.nz, c.ny, c.nx, 3)) if u is None else u
+        pr, kr = _ptr(rho, np.float64, self.ncell)
+        pu, ku = _ptr(u, np.float64, 3 * self.ncell)
+        check(lib().psm_get_macroscopic(self._h, pr, pu))
         return rho, u
 
     def eps(self):

@@ -249,3 +249,20 @@ def test_header_is_plain_c(tmp_path, compiler, flags):
                                                os.path.join(ROOT, "include"), "-c", str(f), "-o",
                                                str(tmp_path / "check.o")], capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
+
+
+def test_binding_checks_output_buffers(psm):
+    """The binding refuses torch outputs of the wrong dtype, shape or layout
+    before it hands a pointer to the library."""
+    import torch
+
+    with pytest.raises(ValueError):
+        psm._ptr(torch.zeros(8, dtype=torch.float32), np.float64, 8)
+    with pytest.raises(ValueError):
+        psm._ptr(torch.zeros(7, dtype=torch.float64), np.float64, 8)
+    with pytest.raises(ValueError):
+        psm._ptr(torch.zeros(4, 4, dtype=torch.float64).t(), np.float64, 16)
+    with pytest.raises(ValueError):
+        psm._ptr(np.zeros(8, dtype=np.float32), np.float64, 8)
+    p, keep = psm._ptr(torch.zeros(8, dtype=torch.float64), np.float64, 8)
+    assert p.value == keep.data_ptr()
