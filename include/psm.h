@@ -449,7 +449,11 @@ int psm_record(psm_handle h, int K, int flags);
  * Adjoint arithmetic is FP32 (FP64 for PSM_FP64 storage); sums are FP64.
  * Its buffers (K - 1 recompute states, two adjoint fields, the FP64
  * gradient) are allocated by psm_record and kept by the handle until
- * psm_destroy or a recording with another K.
+ * psm_destroy or a recording with another K.  Where a second set of K - 1
+ * states fits with a sixteenth of the device memory left free, psm_record
+ * allocates it too, with a stream of the handle's own: psm_backward then
+ * recomputes the segment before the current one on that stream while the
+ * adjoint sweeps the current one (same results, bit for bit).
  * Synchronises; the handle keeps its state and step counter.
  * PSM_ERR_STATE without a recorded forward. */
 int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* grad_omega, double* grad_uin);

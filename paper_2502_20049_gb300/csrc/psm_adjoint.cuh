@@ -16,8 +16,10 @@
 //                    ghost plane (g_i = f^eq_i(rho0, u_in)).
 // The eps sequence is the forward's (frozen geometry: eps is piecewise
 // constant in omega).  All arithmetic is in the compute precision T (FP32 for
-// FP32/FP16/BF16 storage, FP64 for FP64); the scalar gradients are summed in
-// FP64 in a fixed order.
+// FP32/FP16/BF16 storage, FP64 for FP64), the per-cell terms of the scalar
+// gradients and their 32-cell warp partials included (on GB300 an FP64
+// instruction costs about 64 FP32 ones); the warp partials are added into FP64
+// block slots and summed in FP64 in a fixed order.
 #pragma once
 
 #include "psm_kernels.cuh"
@@ -36,6 +38,7 @@ struct AdjParams {
   const float* delta;
   const double* w;      // [nbodies][6] weights of this step's force/torque in J (null: none)
   double dghost[27][3]; // d g_i / d u_in
+  float dghostf[27][3]; // the same in FP32
   double* partials;
   unsigned int* ticket;
   double* acc_out;      // [nbodies * 3 + 3]: dJ/d omega per body, dJ/d u_in
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
   auto cell_body = [&](auto gen_c, int x, int y, int z) {
     constexpr bool GEN = decltype(gen_c)::value;
     const bool active = x < p.g.nx && y < p.g.ny;
-    double aw0 = 0, aw1 = 0, aw2 = 0, au0 = 0, au1 = 0, au2 = 0;
+    T aw0 = 0, aw1 = 0, aw2 = 0, au0 = 0, au1 = 0, au2 = 0;
     bool has_w = false, has_u = false;
     int owner = -1;
     if (active) {
@@ -234,12 +237,9 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
         const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
         const T uu = ux * ux + uy * uy + uz * uz;
         T usx = 0, usy = 0, usz = 0;
-        double Rx = 0, Ry = 0, Rz = 0;
+        T Rx = 0, Ry = 0, Rz = 0;
         if (GEN && owner >= 0) {
           const DevBody& b = p.body[owner];
-          Rx = (double)x + 0.5 - b.R[0];
-          Ry = (double)y + 0.5 - b.R[1];
-          Rz = (double)z + 0.5 - b.R[2];
           T rx, ry, rz, wx, wy, wz, vx, vy, vz;
           if constexpr (sizeof(T) == 4) {
             rx = (T(x) + T(0.5)) - b.Rf[0];
@@ -248,10 +248,13 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
             wx = b.omegaf[0], wy = b.omegaf[1], wz = b.omegaf[2];
             vx = b.vf[0], vy = b.vf[1], vz = b.vf[2];
           } else {
-            rx = Rx, ry = Ry, rz = Rz;
+            rx = (double)x + 0.5 - b.R[0];
+            ry = (double)y + 0.5 - b.R[1];
+            rz = (double)z + 0.5 - b.R[2];
             wx = b.omega[0], wy = b.omega[1], wz = b.omega[2];
             vx = b.v[0], vy = b.v[1], vz = b.v[2];
           }
+          Rx = rx, Ry = ry, Rz = rz;
           usx = wy * rz - wz * ry + vx;
           usy = wz * rx - wx * rz + vy;
           usz = wx * ry - wy * rx + vz;
@@ -263,9 +266,10 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
         if (GEN && owner >= 0 && Bw > T(0) && p.w) {
           const double* wv = p.w + owner * 6;
           // J_n = sum_b w_F . F_b + w_T . T_b with F_b = -sum s, T_b = -sum r x s
-          sbx = T(-(wv[0] + (wv[4] * Rz - wv[5] * Ry)));
-          sby = T(-(wv[1] + (wv[5] * Rx - wv[3] * Rz)));
-          sbz = T(-(wv[2] + (wv[3] * Ry - wv[4] * Rx)));
+          const T w0 = T(wv[0]), w1 = T(wv[1]), w2 = T(wv[2]), w3 = T(wv[3]), w4 = T(wv[4]), w5 = T(wv[5]);
+          sbx = -(w0 + (w4 * Rz - w5 * Ry));
+          sby = -(w1 + (w5 * Rx - w3 * Rz));
+          sbz = -(w2 + (w3 * Ry - w4 * Rx));
         }
         // ---- reverse sweep over the rest population and the opposite pairs ----
         T Bbar = 0, rhob = 0;
@@ -382,16 +386,22 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
           static_cast<T*>(p.lout_slot[i])[cell] = l;
           if (GEN && zg.from(lat_cz(i))) {
             // the population is the ghost value g_i(u_in)
-            au0 += (double)l * p.dghost[i][0];
-            au1 += (double)l * p.dghost[i][1];
-            au2 += (double)l * p.dghost[i][2];
+            if constexpr (sizeof(T) == 4) {
+              au0 += l * p.dghostf[i][0];
+              au1 += l * p.dghostf[i][1];
+              au2 += l * p.dghostf[i][2];
+            } else {
+              au0 += l * p.dghost[i][0];
+              au1 += l * p.dghost[i][1];
+              au2 += l * p.dghost[i][2];
+            }
             has_u = true;
           }
         }
         grad[cell] = g_old + (double)(Bbar * Bp);
         if (GEN && owner >= 0) {
           // u_s = omega x r + v  =>  d/d omega = r x usbar
-          const double a = (double)usbx, b = (double)usby, c = (double)usbz;
+          const T a = usbx, b = usby, c = usbz;
           aw0 = Ry * c - Rz * b;
           aw1 = Rz * a - Rx * c;
           aw2 = Rx * b - Ry * a;
@@ -400,26 +410,26 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
       }
       }
     }
-    // ---- per-warp FP64 sums in a fixed order ----
+    // ---- per-warp partials in T, added into the FP64 block slots in a fixed order ----
     if (!GEN) return;
     if (__any_sync(0xffffffffu, has_w)) {
       for (int bi = 0; bi < nb; ++bi) {
         const bool mine = has_w && owner == bi;
         if (!__any_sync(0xffffffffu, mine)) continue;
-        const double v0 = warp_sum(mine ? aw0 : 0.0), v1 = warp_sum(mine ? aw1 : 0.0), v2 = warp_sum(mine ? aw2 : 0.0);
+        const T v0 = warp_sum(mine ? aw0 : T(0)), v1 = warp_sum(mine ? aw1 : T(0)), v2 = warp_sum(mine ? aw2 : T(0));
         if (lane == 0) {
-          s_acc[warp][bi * 3 + 0] += v0;
-          s_acc[warp][bi * 3 + 1] += v1;
-          s_acc[warp][bi * 3 + 2] += v2;
+          s_acc[warp][bi * 3 + 0] += (double)v0;
+          s_acc[warp][bi * 3 + 1] += (double)v1;
+          s_acc[warp][bi * 3 + 2] += (double)v2;
         }
       }
     }
     if (__any_sync(0xffffffffu, has_u)) {
-      const double v0 = warp_sum(au0), v1 = warp_sum(au1), v2 = warp_sum(au2);
+      const T v0 = warp_sum(au0), v1 = warp_sum(au1), v2 = warp_sum(au2);
       if (lane == 0) {
-        s_acc[warp][nb * 3 + 0] += v0;
-        s_acc[warp][nb * 3 + 1] += v1;
-        s_acc[warp][nb * 3 + 2] += v2;
+        s_acc[warp][nb * 3 + 0] += (double)v0;
+        s_acc[warp][nb * 3 + 1] += (double)v1;
+        s_acc[warp][nb * 3 + 2] += (double)v2;
       }
     }
   };

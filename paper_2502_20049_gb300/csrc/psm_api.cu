@@ -147,6 +147,15 @@ struct psm_solver {
   // between calls, and their tensor maps
   std::vector<void*> rec_slots;
   std::vector<BufMaps> rec_maps;
+  // a second set of recompute buffers and its stream: psm_backward recomputes
+  // the segment before the current one while the adjoint sweeps the current
+  // one (allocated when the device has room; otherwise one set, in sequence);
+  // the recompute's force/torque sums go to their own grid-reduction scratch
+  std::vector<void*> rec_slots2;
+  std::vector<BufMaps> rec_maps2;
+  cudaStream_t rec_stream = nullptr;
+  double* d_partials2 = nullptr;
+  unsigned int* d_ticket2 = nullptr;
   void* rec_lam[2] = {nullptr, nullptr};  // the two adjoint fields
   double* rec_grad = nullptr;             // dJ/d delta accumulator
 };
@@ -936,6 +945,10 @@ int psm_destroy(psm_handle h) {
   cudaFree(h->d_err);
   for (void* c : h->ckpt) cudaFree(c);
   for (void* c : h->rec_slots) cudaFree(c);
+  for (void* c : h->rec_slots2) cudaFree(c);
+  cudaFree(h->d_partials2);
+  cudaFree(h->d_ticket2);
+  if (h->rec_stream) cudaStreamDestroy(h->rec_stream);
   cudaFree(h->d_dyn);
   cudaFree(h->d_dev_bodies);
   cudaFree(h->rec_lam[0]);
@@ -1340,6 +1353,47 @@ int psm_set_eps_delta(psm_handle h, const float* delta) {
 // Buffers of psm_backward, allocated when recording starts (a one-time cost
 // outside the backward sweep) and kept by the handle: K - 1 recompute states
 // with their tensor maps, two adjoint fields, the gradient accumulator.
+// The second recompute set of psm_backward (K - 1 states, their tensor maps,
+// the recompute stream and its reduction scratch), allocated only while at
+// least a sixteenth of the device memory stays free; without it psm_backward
+// recomputes and sweeps each segment in turn on the solver's stream.
+static void ensure_second_recompute_set(psm_solver* h, int K) {
+  for (void* c : h->rec_slots2) cudaFree(c);
+  h->rec_slots2.clear();
+  h->rec_maps2.clear();
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if ((size_t)(K - 1) * state_bytes(h) + total_b / 16 > free_b) return;
+  std::vector<void*> slots((size_t)K, nullptr);
+  std::vector<BufMaps> maps((size_t)K, BufMaps{});
+  bool ok = true;
+  for (int k = 1; k < K && ok; ++k) {
+    ok = cudaMalloc(&slots[k], state_bytes(h)) == cudaSuccess;
+    if (ok && h->tma_tg_ok) ok = encode_maps(h, slots[k], maps[k], h->tma_tiling_tg);
+  }
+  if (ok && !h->rec_stream) ok = cudaStreamCreateWithFlags(&h->rec_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok && !h->d_partials2)
+    ok = cudaMalloc(&h->d_partials2, sizeof(double) * (size_t)h->max_blocks * PSM_MAX_BODIES * 6) == cudaSuccess;
+  if (ok && !h->d_ticket2) {
+    ok = cudaMalloc(&h->d_ticket2, sizeof(unsigned int)) == cudaSuccess;
+    if (ok) ok = cudaMemsetAsync(h->d_ticket2, 0, sizeof(unsigned int), h->stream) == cudaSuccess;
+    if (!ok) {
+      cudaFree(h->d_ticket2);
+      h->d_ticket2 = nullptr;
+    }
+  }
+  if (!ok) {
+    cudaGetLastError();  // an allocation that failed is not an error of the call
+    for (void* c : slots) cudaFree(c);
+    return;
+  }
+  h->rec_slots2 = slots;
+  h->rec_maps2 = maps;
+}
+
 int ensure_backward_buffers(psm_solver* h, int K) {
   const size_t ncell = (size_t)h->g.ncell;
   const size_t tb = h->lat.storage == PSM_FP64 ? 8 : 4;
@@ -1365,6 +1419,7 @@ int ensure_backward_buffers(psm_solver* h, int K) {
     if (!h->rec_lam[k]) e = cudaMalloc(&h->rec_lam[k], (size_t)h->Q * ncell * tb);
   if (e == cudaSuccess && !h->rec_grad) e = cudaMalloc((void**)&h->rec_grad, ncell * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "backward buffers");
+  if (K > 1 && h->rec_slots2.size() != (size_t)K) ensure_second_recompute_set(h, K);
   return PSM_OK;
 }
 
@@ -1421,8 +1476,11 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
     const int rc = ensure_backward_buffers(h, K);
     if (rc != PSM_OK) return rc;
   }
-  std::vector<void*> slots(h->rec_slots);
-  std::vector<BufMaps> smaps(h->rec_maps);
+  // one or two recompute sets (set 1: the segment before the current one,
+  // recomputed on the recompute stream while the adjoint sweeps the current)
+  const bool overlap = M > 1 && h->rec_slots2.size() == (size_t)K && h->rec_stream;
+  std::vector<void*> slots[2] = {h->rec_slots, h->rec_slots2};
+  std::vector<BufMaps> smaps[2] = {h->rec_maps, h->rec_maps2};
   const bool tma_rec = h->tma_tg_ok && h->variant != PSM_KERNEL_PLAIN;
   void* lam0 = h->rec_lam[0];
   void* lam1 = h->rec_lam[1];
@@ -1484,37 +1542,66 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
       const double wi = h->Q == 19 ? psm::lat_w<19>(i) : psm::lat_w<27>(i);
       const double c[3] = {(double)psm::lat_cx(i), (double)psm::lat_cy(i), (double)psm::lat_cz(i)};
       const double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
-      for (int k = 0; k < 3; ++k) ap.dghost[i][k] = wi * h->grid.rho0 * (3.0 * c[k] + 9.0 * cu * c[k] - 3.0 * u[k]);
+      for (int k = 0; k < 3; ++k) {
+        ap.dghost[i][k] = wi * h->grid.rho0 * (3.0 * c[k] + 9.0 * cu * c[k] - 3.0 * u[k]);
+        ap.dghostf[i][k] = (float)ap.dghost[i][k];
+      }
     }
   }
   void* la = lam0;  // lambda^{n+1}
   void* lb = lam1;  // lambda^n
-  for (int64_t m = M - 1; m >= 0 && e == cudaSuccess; --m) {
+  cudaStream_t rs = overlap ? h->rec_stream : st;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, recomputed[2], swept[2]
+  bool swept_pending[2] = {false, false};
+  if (overlap) {
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    // the recompute stream starts after everything queued on the solver's stream
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, ev[0], 0);
+  }
+  StepParams rp = sp;  // the recompute's own reduction scratch when it runs beside the adjoint
+  if (overlap) {
+    rp.partials = h->d_partials2;
+    rp.ticket = h->d_ticket2;
+  }
+  // recompute f^{ns+1} .. f^{ne-1} of segment m into set q
+  auto recompute = [&](int64_t m, int q) {
+    if (e != cudaSuccess) return;
+    if (overlap && swept_pending[q]) e = cudaStreamWaitEvent(rs, ev[3 + q], 0);  // set q read by the adjoint
     const int64_t ns = h->rec_n0 + m * K;
     const int64_t ne = std::min<int64_t>(ns + K, h->step);
-    slots[0] = h->ckpt[(size_t)m];
-    if (tma_rec && ne - ns > 1 && !encode_maps(h, slots[0], smaps[0], h->tma_tiling_tg)) e = cudaErrorInvalidValue;
-    // recompute f^{ns+1} .. f^{ne-1} into the slots
+    std::vector<void*>& sl = slots[q];
+    std::vector<BufMaps>& sm = smaps[q];
+    sl[0] = h->ckpt[(size_t)m];
+    if (e == cudaSuccess && tma_rec && ne - ns > 1 && !encode_maps(h, sl[0], sm[0], h->tma_tiling_tg))
+      e = cudaErrorInvalidValue;
     for (int64_t n = ns; n + 1 < ne && e == cudaSuccess; ++n) {
-      for (int b = 0; b < nb; ++b) sp.body[b] = dev_body(h, b, n);
+      for (int b = 0; b < nb; ++b) rp.body[b] = dev_body(h, b, n);
       const size_t a = (size_t)(n - ns), c = a + 1;
-      sp.f = slots[a];
-      sp.f_dst = slots[c];
-      psm::set_slots(sp, h->lat.storage, h->Q);
+      rp.f = sl[a];
+      rp.f_dst = sl[c];
+      psm::set_slots(rp, h->lat.storage, h->Q);
       if (tma_rec) {
         psm::TmaMaps tm;
-        tm.tile = smaps[a].tile;
-        tm.row1 = smaps[a].row1;
-        tm.dstw = smaps[c].warpq;
-        e = psm::launch_step_tma(h->lat.storage, h->Q, psm::MODE_TG, sp, tm, st);
+        tm.tile = sm[a].tile;
+        tm.row1 = sm[a].row1;
+        tm.dstw = sm[c].warpq;
+        e = psm::launch_step_tma(h->lat.storage, h->Q, psm::MODE_TG, rp, tm, rs);
       } else {
-        e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, sp, st);
+        e = psm::launch_step(h->lat.storage, h->Q, psm::MODE_TG, rp, rs);
       }
     }
-    // adjoint steps ne-1 .. ns
+    if (overlap && e == cudaSuccess) e = cudaEventRecord(ev[1 + q], rs);
+  };
+  // adjoint steps ne-1 .. ns of segment m from set q
+  auto sweep = [&](int64_t m, int q) {
+    if (e != cudaSuccess) return;
+    if (overlap) e = cudaStreamWaitEvent(st, ev[1 + q], 0);
+    const int64_t ns = h->rec_n0 + m * K;
+    const int64_t ne = std::min<int64_t>(ns + K, h->step);
     for (int64_t n = ne - 1; n >= ns && e == cudaSuccess; --n) {
       for (int b = 0; b < nb; ++b) ap.body[b] = dev_body(h, b, n);
-      ap.f = slots[(size_t)(n - ns)];
+      ap.f = slots[q][(size_t)(n - ns)];
       ap.lam_in = la;
       ap.lam_out = lb;
       {
@@ -1531,6 +1618,31 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
       e = launch_adjoint(h->lat.storage, h->Q, ap.trt, ap, st);
       std::swap(la, lb);
     }
+    if (overlap && e == cudaSuccess) {
+      e = cudaEventRecord(ev[3 + q], st);
+      swept_pending[q] = true;
+    }
+  };
+  if (overlap) {
+    // segment m in set (M - 1 - m) mod 2; segment m - 1 is recomputed while m is swept
+    recompute(M - 1, 0);
+    for (int64_t m = M - 1; m >= 0; --m) {
+      const int q = (int)((M - 1 - m) & 1);
+      if (m >= 1) recompute(m - 1, q ^ 1);
+      sweep(m, q);
+    }
+  } else {
+    for (int64_t m = M - 1; m >= 0; --m) {
+      recompute(m, 0);
+      sweep(m, 0);
+    }
+  }
+  if (overlap) {
+    // whatever happened, the solver's stream ends after the recompute stream
+    cudaEventRecord(ev[0], rs);
+    cudaStreamWaitEvent(st, ev[0], 0);
+    for (int k = 0; k < 5; ++k)
+      if (ev[k]) cudaEventDestroy(ev[k]);
   }
   if (e == cudaSuccess && (h->rec_flags & PSM_RECORD_INIT_FROM_INFLOW)) {
     ap.lam_in = la;  // lambda^{n0}
