@@ -482,10 +482,9 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
  * the launch).  The summation order is fixed (deterministic).  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) for
  * that device and keeps it for the life of the process (do not use the
- * function across a cudaDeviceReset); make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the
- * caller. */
+ * function across a cudaDeviceReset).  All calls share the one array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller. */
 int psm_mass_noalloc(const void* f, int storage, int stencil, int64_t ncell, double rho0, void* stream,
                      double* out);
 
