@@ -430,9 +430,12 @@ int psm_set_eps_delta(psm_handle h, const float* delta);
  * PSM_RECORD_INIT_FROM_INFLOW declares that the state at n0 is
  * f^eq(rho0, u_in) (psm_create or psm_init_equilibrium(rho0, u_in)), so that
  * the gradient with respect to u_in includes the initial state.
+ * PSM_RECORD_SEQUENTIAL keeps psm_backward to one set of recompute buffers
+ * (no second set, see psm_backward; a set allocated before is freed).
  * PSM_ERR_UNSUPPORTED for the cumulant operator (the adjoint step is written
  * for BGK and TRT). */
 #define PSM_RECORD_INIT_FROM_INFLOW 1
+#define PSM_RECORD_SEQUENTIAL 2
 int psm_record(psm_handle h, int K, int flags);
 
 /* Gradient of J = sum_{n, body, k} w[n][body][k] * FT[n][body][k] over the

@@ -1394,7 +1394,7 @@ static void ensure_second_recompute_set(psm_solver* h, int K) {
   h->rec_maps2 = maps;
 }
 
-int ensure_backward_buffers(psm_solver* h, int K) {
+int ensure_backward_buffers(psm_solver* h, int K, bool second) {
   const size_t ncell = (size_t)h->g.ncell;
   const size_t tb = h->lat.storage == PSM_FP64 ? 8 : 4;
   cudaError_t e = cudaSuccess;
@@ -1419,7 +1419,13 @@ int ensure_backward_buffers(psm_solver* h, int K) {
     if (!h->rec_lam[k]) e = cudaMalloc(&h->rec_lam[k], (size_t)h->Q * ncell * tb);
   if (e == cudaSuccess && !h->rec_grad) e = cudaMalloc((void**)&h->rec_grad, ncell * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "backward buffers");
-  if (K > 1 && h->rec_slots2.size() != (size_t)K) ensure_second_recompute_set(h, K);
+  if (!second) {
+    for (void* c : h->rec_slots2) cudaFree(c);
+    h->rec_slots2.clear();
+    h->rec_maps2.clear();
+  } else if (K > 1 && h->rec_slots2.size() != (size_t)K) {
+    ensure_second_recompute_set(h, K);
+  }
   return PSM_OK;
 }
 
@@ -1432,14 +1438,14 @@ int psm_record(psm_handle h, int K, int flags) {
   if (h->lat.streaming == PSM_STREAM_AA && ((K & 1) || (h->step & 1)))
     return fail(PSM_ERR_ARG, "AA streaming: record from an even step with an even K (checkpoints need the "
                              "natural layout)");
-  if (flags & ~PSM_RECORD_INIT_FROM_INFLOW) return fail(PSM_ERR_ARG, "unknown record flags");
+  if (flags & ~(PSM_RECORD_INIT_FROM_INFLOW | PSM_RECORD_SEQUENTIAL)) return fail(PSM_ERR_ARG, "unknown record flags");
   if (h->col.fluid == PSM_CUMULANT)
     return fail(PSM_ERR_UNSUPPORTED, "psm_backward supports BGK and TRT (no adjoint of the cumulant operator)");
   if (h->slab) return fail(PSM_ERR_UNSUPPORTED, "psm_backward of a z-slab (the adjoint is not decomposed)");
   if (h->free_mask)
     return fail(PSM_ERR_STATE, "psm_backward supports prescribed motion only (two-way coupled bodies attached)");
   {
-    const int rc = ensure_backward_buffers(h, K);
+    const int rc = ensure_backward_buffers(h, K, !(flags & PSM_RECORD_SEQUENTIAL));
     if (rc != PSM_OK) return rc;
   }
   h->rec_K = K;
@@ -1473,12 +1479,13 @@ int psm_backward(psm_handle h, const double* dJ_dFT, double* grad_eps, double* g
   // recompute buffers, adjoint fields and gradient accumulator: allocated by
   // psm_record (ensure_backward_buffers)
   {
-    const int rc = ensure_backward_buffers(h, K);
+    const int rc = ensure_backward_buffers(h, K, !(h->rec_flags & PSM_RECORD_SEQUENTIAL));
     if (rc != PSM_OK) return rc;
   }
   // one or two recompute sets (set 1: the segment before the current one,
   // recomputed on the recompute stream while the adjoint sweeps the current)
-  const bool overlap = M > 1 && h->rec_slots2.size() == (size_t)K && h->rec_stream;
+  const bool overlap =
+      !(h->rec_flags & PSM_RECORD_SEQUENTIAL) && M > 1 && h->rec_slots2.size() == (size_t)K && h->rec_stream;
   std::vector<void*> slots[2] = {h->rec_slots, h->rec_slots2};
   std::vector<BufMaps> smaps[2] = {h->rec_maps, h->rec_maps2};
   const bool tma_rec = h->tma_tg_ok && h->variant != PSM_KERNEL_PLAIN;

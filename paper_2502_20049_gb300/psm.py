@@ -548,9 +548,12 @@ class Solver:
             p, keep = _ptr(d, np.float32, self.ncell)
         check(lib().psm_set_eps_delta(self._h, p))
 
-    def record(self, K: int, init_from_inflow: bool = False):
-        """Checkpoint the trajectory every K steps from now on (K = 0 stops)."""
-        check(lib().psm_record(self._h, int(K), 1 if init_from_inflow else 0))
+    def record(self, K: int, init_from_inflow: bool = False, sequential: bool = False):
+        """Checkpoint the trajectory every K steps from now on (K = 0 stops);
+        sequential: one set of recompute buffers (psm_backward recomputes and
+        sweeps each segment in turn)."""
+        flags = (1 if init_from_inflow else 0) | (2 if sequential else 0)
+        check(lib().psm_record(self._h, int(K), flags))
 
     def backward(self, dJ_dFT=None, grad_eps=None):
         """Adjoint gradients of J = sum w * FT over the recorded steps.

@@ -367,24 +367,36 @@ def test_backward_without_record_is_state_error():
 def test_backward_overlapped_recompute_equals_one_segment(storage, streaming):
     """psm_backward recomputes the segment before the current one on a second
     stream while the adjoint sweeps the current one (several segments: K = 4,
-    6 or 8 of 24 steps); one segment (K = 24) takes no recompute overlap.
-    The recomputed states equal the recorded ones bit for bit either way, so
-    every gradient agrees bit for bit."""
+    6 or 8 of 24 steps); with PSM_RECORD_SEQUENTIAL, or with one segment
+    (K = 24), it recomputes and sweeps in turn on the solver's stream.  The
+    recomputed states equal the recorded ones bit for bit either way, so every
+    gradient agrees bit for bit."""
     from paper_2502_20049_gb300 import psm
 
     case = W.Case("adj_overlap", 64, 8, 16, Q=19, storage=storage, streaming=streaming, fluid="trt", tau=0.62,
                   u_in=(0.0, 0.0, 0.03), steps=24,
                   bodies=[W.BodyCase(W.ELLIPSOID, (6.0, 2.5, 2.0), 2, (30.0, 4.1, 8.0), omega=(0.0, 0.0, 0.04))])
     out = {}
-    for K in (24, 4, 6, 8):
+    for K, seq in ((24, False), (4, False), (6, False), (8, False), (4, True), (8, True)):
         sol = psm.Solver.from_case(case)
-        sol.record(K, init_from_inflow=True)
+        sol.record(K, init_from_inflow=True, sequential=seq)
         sol.step(case.steps)
-        out[K] = sol.backward()
+        out[K, seq] = sol.backward()
+        if K == 8 and not seq:
+            out["again"] = sol.backward()  # a second pass over the same recording
         sol.close()
-    g0, w0, u0 = out[24]
+    g0, w0, u0 = out[24, False]
     assert np.abs(g0).max() > 0 and np.abs(w0).max() > 0
-    for K in (4, 6, 8):
-        g, w, u = out[K]
-        assert np.array_equal(g, g0), (K, np.abs(g - g0).max())
-        assert np.array_equal(w, w0) and np.array_equal(u, u0), K
+    for key, (g, w, u) in out.items():
+        assert np.array_equal(g, g0), (key, np.abs(g - g0).max())
+        assert np.array_equal(w, w0) and np.array_equal(u, u0), key
+
+
+def test_record_rejects_unknown_flags():
+    from paper_2502_20049_gb300 import psm
+
+    sol = psm.Solver.from_case(small_case())
+    with pytest.raises(psm.PSMError) as ei:
+        psm.check(psm.lib().psm_record(sol._h, 4, 4))
+    assert ei.value.code == -1
+    sol.close()
