@@ -208,13 +208,30 @@ __global__ void __launch_bounds__(PSM_THREADS, sizeof(S) == 8 ? 1 : (PART == 1 ?
       if (GEN) epsf = cell_eps(p.body, nb, x, y, z, owner);
       T e = T(epsf);
       if (p.delta) e += T(p.delta[cell]);
-      if (e == T(0) && !zg.lo && !zg.hi) {
-        // B = 0 and no ghost population (a cell of a general tile outside the
-        // bodies): the fluid-only reverse step, B'(0) for the gradient
+      if (e == T(0)) {
+        // B = 0 (a cell of a general tile outside the bodies): the fluid-only
+        // reverse step, B'(0) for the gradient.  On a ghost plane the
+        // populations entering from it hold the ghost values g_i(u_in) (loaded
+        // so above, mu = 0 for those leaving into it), and their adjoint adds
+        // to dJ/d u_in.
         T lam[Q];
         const T bb = adj_fluid_cell<T, Q>(C, p.solid, inv_tau, f, mu, lam);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) static_cast<T*>(p.lout_slot[i])[cell] = lam[i];
+        for (int i = 0; i < Q; ++i) {
+          static_cast<T*>(p.lout_slot[i])[cell] = lam[i];
+          if (zg.from(lat_cz(i))) {
+            if constexpr (sizeof(T) == 4) {
+              au0 += lam[i] * p.dghostf[i][0];
+              au1 += lam[i] * p.dghostf[i][1];
+              au2 += lam[i] * p.dghostf[i][2];
+            } else {
+              au0 += lam[i] * p.dghost[i][0];
+              au1 += lam[i] * p.dghost[i][1];
+              au2 += lam[i] * p.dghost[i][2];
+            }
+            has_u = true;
+          }
+        }
         grad[cell] = g_old + (double)(bb * Bp0);
       } else {
         T Bw = e, Bp = T(1);
