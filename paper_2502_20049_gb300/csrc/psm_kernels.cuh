@@ -80,6 +80,46 @@ struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ __nv_bfloat16 from_double(double v) { return __double2bfloat16(v); }
 };
 
+// Two 16-bit values of neighbouring cells (x even, x + 1) as one 32-bit word:
+// the lower half is the cell at the lower address (16-bit storage types only).
+template <class S>
+struct Pair16 {
+  template <class T>
+  static __device__ __forceinline__ void unpack(unsigned, T& a, T& b) { a = b = T(0); }
+  template <class T>
+  static __device__ __forceinline__ unsigned pack(T, T) { return 0u; }
+};
+template <>
+struct Pair16<__half> {
+  static __device__ __forceinline__ void unpack(unsigned w, float& a, float& b) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    a = __low2float(h);
+    b = __high2float(h);
+  }
+  static __device__ __forceinline__ unsigned pack(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
+};
+template <>
+struct Pair16<__nv_bfloat16> {
+  static __device__ __forceinline__ void unpack(unsigned w, float& a, float& b) {
+    __nv_bfloat162 h;
+    memcpy(&h, &w, 4);
+    a = __low2float(h);
+    b = __high2float(h);
+  }
+  static __device__ __forceinline__ unsigned pack(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Remap of one body onto one cell (Sec. 3).  The cell centre is taken into the
 // body frame, X = Q_n^T (x_c - R_n); the 2^s sub-cells per axis whose block
@@ -1400,19 +1440,61 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
   }
 
   const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int px = threadIdx.x % (TX / 2), py = threadIdx.x / (TX / 2);
 
   // One staged tile, read from stage s after its full barrier.  Each warp
   // signals empty[s] once it holds its cells' PDFs in registers; warp 0 then
   // waits for all warps' signals before refilling the stage, so warps do not
   // wait for one another otherwise.  A wait that times out sets s_abort and
   // the warp leaves the tile loop.
+  // After the warp holds its cells' PDFs of stage s in registers.
+  auto stage_read = [&](int tile, int k, int s) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    // refill the stage of tile j = k - LAG (read by every warp by now, as a
+    // rule) with tile j + NST; warp j mod NW does it
+    const int j = k - LAG;
+    if (j >= 0 && warp == j % NW) {
+      const int next = tile + (NST - LAG) * gridDim.x;
+      if (next < ntiles) {
+        const int sj = j % NST;
+        // warp-uniform outcome (produce needs the whole warp)
+        if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[sj], (unsigned)((j / NST) & 1)))) {
+          const int4 cur = s_walk[warp];
+          produce(cur, sj);
+          if (lane == 0) s_walk[warp] = tile_advance(p.t, cur, s_wstep);
+        } else {
+          s_abort = 1;
+        }
+      }
+    }
+  };
+
   auto tile_body = [&](auto gen_c, int tile, int k, int s, const int4 hd) {
-    (void)tile;
     constexpr bool GEN = decltype(gen_c)::value;
     const int z = hd.z;
     ZGhost zg;
     zg.init(p.g, z);
     const unsigned char* st = stages + s * L::STAGE;
+    // fluid-only tiles of the AA even step in 16-bit storage: the thread's two
+    // cells are x neighbours (x even, x + 1), so one 32-bit shared load and one
+    // 32-bit store per slot serve both
+    constexpr bool XPAIR = !GEN && CPT == 2 && MODE == MODE_AA_EVEN && sizeof(S) == 2 && FL != 2 && !L::STORE_TMA;
+    if constexpr (XPAIR) {
+      const unsigned* sw = reinterpret_cast<const unsigned*>(st) + (py * TX) / 2 + px;
+      T f0[Q], f1[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) Pair16<S>::unpack(sw[i * (CPT * PSM_THREADS / 2)], f0[i], f1[i]);
+      stage_read(tile, k, s);
+      fluid_collide<T, Q, FL>(p, f0);
+      fluid_collide<T, Q, FL>(p, f1);
+      const int x = hd.x + 2 * px, y = hd.y + py;
+      const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        *reinterpret_cast<unsigned*>(static_cast<S*>(p.dst_slot[lat_opp(i)]) + cell) = Pair16<S>::pack(f0[i], f1[i]);
+      return;
+    }
     // the thread's cells r = 0 .. CPT-1: (lx, ly + r TYB), one after the other
 #pragma unroll
     for (int r = 0; r < CPT; ++r) {
@@ -1429,27 +1511,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
           f[i] = Store<S>::ld(reinterpret_cast<const S*>(st + i * L::ROW + 128) + (lx - lat_cx(i)));
         }
       }
-      if (r == CPT - 1) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-        // refill the stage of tile j = k - LAG (read by every warp by now, as a
-        // rule) with tile j + NST; warp j mod NW does it
-        const int j = k - LAG;
-        if (j >= 0 && warp == j % NW) {
-          const int next = tile + (NST - LAG) * gridDim.x;
-          if (next < ntiles) {
-            const int sj = j % NST;
-            // warp-uniform outcome (produce needs the whole warp)
-            if (__all_sync(0xffffffffu, mbar_wait_bounded(&empty[sj], (unsigned)((j / NST) & 1)))) {
-              const int4 cur = s_walk[warp];
-              produce(cur, sj);
-              if (lane == 0) s_walk[warp] = tile_advance(p.t, cur, s_wstep);
-            } else {
-              s_abort = 1;
-            }
-          }
-        }
-      }
+      if (r == CPT - 1) stage_read(tile, k, s);
       int owner = -1;
       bool solid_cell = false;
       ft_t<T> ft[6] = {0, 0, 0, 0, 0, 0};
