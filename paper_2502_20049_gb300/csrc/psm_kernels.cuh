@@ -1415,7 +1415,9 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
           // cx = +1: cell x0 reads x0 - 1 (the chunk before the row, wrapped in x);
           // cx = -1: cell x0 + 255 reads x0 + 256 (the chunk after it)
           const int xe = cx > 0 ? (x0 == 0 ? p.g.nx - EP : x0 - EP) : (x0 + PSM_THREADS == p.g.nx ? 0 : x0 + PSM_THREADS);
-          const S* src = static_cast<const S*>(p.src_slot[slot]) + ((long long)zs * p.g.ny + ys) * p.g.nx + xe;
+          // slot k starts k ncell values after slot 0 (one uniform base for every lane)
+          const S* src = static_cast<const S*>(p.src_slot[0]) +
+                         (((long long)slot * p.g.nz + zs) * p.g.ny + ys) * p.g.nx + xe;
           mbar_expect_tx(bar, 16u);
           bulk_load_16(cx > 0 ? row - 16 : row + PSM_THREADS * (int)sizeof(S), src, bar);
         }
