@@ -460,6 +460,11 @@ template <class T>
 __device__ __forceinline__ T r_addc(T a, int s, T b) {
   return s > 0 ? r_add(a, b) : r_sub(a, b);
 }
+template <class T>
+__device__ __forceinline__ T r_div(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fdiv_rn(a, b);
+  else return __ddiv_rn(a, b);
+}
 
 // Density deviation, density and velocity of one cell from its shifted PDFs,
 // summed over opposite pairs (i, i + 1): drho = f_0 + sum (f_i + f_i+1),
@@ -509,6 +514,15 @@ __device__ __forceinline__ T c_dot(int i, T ux, T uy, T uz) {
   }
   if (lat_cz(i)) cu = h ? r_addc(cu, lat_cz(i), uz) : (lat_cz(i) > 0 ? uz : -uz);
   return cu;
+}
+
+// feq_shifted with separately rounded operations (the PSM cells of the
+// cumulant step): w_i (drho + rho (3 c.v + 4.5 (c.v)^2 - 1.5 v.v))
+template <int Q, class T>
+__device__ __forceinline__ T feq_shifted_r(int i, T drho, T rho, T vx, T vy, T vz, T vv) {
+  const T cv = c_dot(i, vx, vy, vz);
+  const T q = r_fma(r_mul(T(4.5), cv), cv, r_fma(T(3), cv, r_mul(T(-1.5), vv)));
+  return r_mul(T(lat_w<Q>(i)), r_fma(rho, q, drho));
 }
 
 // Pure fluid cell: f* = f + Omega^F (TRT; BGK is the case omega+ = omega- =
@@ -734,13 +748,15 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
   const T om_a = C.om_a, om_b = C.om_b;
   const T inv_tau = C.inv_tau;
   // ---- remap (Sec. 3) and weighting (Eq. 5/6) ----
+  // Every operation below is separately rounded (r_*): a PSM cell gets the
+  // same bits in every kernel and loop shape that inlines this function.
   const float epsf = cell_eps(bodies, p.nbodies, x, y, z, owner);
   T eps = T(epsf);
-  if (p.delta) eps += T(p.delta[cell]);
+  if (p.delta) eps = r_add(eps, T(p.delta[cell]));
   T Bw = eps;
   if (p.weighting == PSM_B_TAU_WEIGHTED && eps != T(0)) {  // eps = 0 gives B = eps exactly
     const T t = C.tmh;
-    Bw = eps * t / ((T(1) - eps) + t);
+    Bw = r_div(r_mul(eps, t), r_add(r_sub(T(1), eps), t));
   }
   T drho, rho, ux, uy, uz, uu;
   moments<T, Q>(f, C.rho0, drho, rho, ux, uy, uz, uu);
@@ -751,28 +767,30 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
   }
   // ---- PSM cell: f* = f + (1 - B) Omega^F + B Omega^S (Eq. 4) ----
   T usx = 0, usy = 0, usz = 0;
+  T rx = 0, ry = 0, rz = 0;  // lever arm x_c - R (Eq. 11)
   if (owner >= 0) {
     const DevBody& b = bodies[owner];
-    T rx, ry, rz, wx, wy, wz, vx, vy, vz;
+    T wx, wy, wz, vx, vy, vz;
     if constexpr (sizeof(T) == 4) {
-      rx = (T(x) + T(0.5)) - b.Rf[0];
-      ry = (T(y) + T(0.5)) - b.Rf[1];
-      rz = (T(z) + T(0.5)) - b.Rf[2];
+      rx = r_sub(r_add(T(x), T(0.5)), b.Rf[0]);
+      ry = r_sub(r_add(T(y), T(0.5)), b.Rf[1]);
+      rz = r_sub(r_add(T(z), T(0.5)), b.Rf[2]);
       wx = b.omegaf[0], wy = b.omegaf[1], wz = b.omegaf[2];
       vx = b.vf[0], vy = b.vf[1], vz = b.vf[2];
     } else {
-      rx = (double)x + 0.5 - b.R[0];
-      ry = (double)y + 0.5 - b.R[1];
-      rz = (double)z + 0.5 - b.R[2];
+      rx = r_sub(r_add((double)x, 0.5), b.R[0]);
+      ry = r_sub(r_add((double)y, 0.5), b.R[1]);
+      rz = r_sub(r_add((double)z, 0.5), b.R[2]);
       wx = b.omega[0], wy = b.omega[1], wz = b.omega[2];
       vx = b.v[0], vy = b.v[1], vz = b.v[2];
     }
-    usx = wy * rz - wz * ry + vx;
-    usy = wz * rx - wx * rz + vy;
-    usz = wx * ry - wy * rx + vz;
+    // u_s = omega x r + v (Eq. 7-9)
+    usx = r_add(r_sub(r_mul(wy, rz), r_mul(wz, ry)), vx);
+    usy = r_add(r_sub(r_mul(wz, rx), r_mul(wx, rz)), vy);
+    usz = r_add(r_sub(r_mul(wx, ry), r_mul(wy, rx)), vz);
   }
-  const T usus = usx * usx + usy * usy + usz * usz;
-  const T omB = T(1) - Bw;
+  const T usus = r_fma(usz, usz, r_fma(usy, usy, r_mul(usx, usx)));
+  const T omB = r_sub(T(1), Bw);
   // cumulant: Omega^F = C(f) - f from the relaxed copy fc
   T fc[Q];
   if constexpr (FL == 2) {
@@ -780,44 +798,44 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
     for (int i = 0; i < Q; ++i) fc[i] = f[i];
     fluid_relax<T, Q, FL>(C, fc, drho, rho, ux, uy, uz, uu);
   }
-  T gx = 0, gy = 0, gz = 0;
+  T gx = 0, gy = 0, gz = 0;  // sum_i Omega^S_i c_i
   if constexpr (FL == 2) {
     {
-      const T n0 = f[0] - feq_shifted<Q, T>(0, drho, rho, ux, uy, uz, uu);
-      const T m0 = f[0] - feq_shifted<Q, T>(0, drho, rho, usx, usy, usz, usus);
-      const T of = fc[0] - f[0];
+      const T n0 = r_sub(f[0], feq_shifted_r<Q, T>(0, drho, rho, ux, uy, uz, uu));
+      const T m0 = r_sub(f[0], feq_shifted_r<Q, T>(0, drho, rho, usx, usy, usz, usus));
+      const T of = r_sub(fc[0], f[0]);
       T os;
-      if (p.solid == PSM_SC1) os = n0 - m0;
-      else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
+      if (p.solid == PSM_SC1) os = r_sub(n0, m0);
+      else if (p.solid == PSM_SC2) os = r_mul(-m0, inv_tau);
       else os = T(0);
-      f[0] = f[0] + omB * of + Bw * os;
+      f[0] = r_fma(Bw, os, r_fma(omB, of, f[0]));
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
       const int j = i + 1;
-      const T ni = f[i] - feq_shifted<Q, T>(i, drho, rho, ux, uy, uz, uu);
-      const T nj = f[j] - feq_shifted<Q, T>(j, drho, rho, ux, uy, uz, uu);
-      const T mi = f[i] - feq_shifted<Q, T>(i, drho, rho, usx, usy, usz, usus);
-      const T mj = f[j] - feq_shifted<Q, T>(j, drho, rho, usx, usy, usz, usus);
-      const T ofi = fc[i] - f[i], ofj = fc[j] - f[j];
+      const T ni = r_sub(f[i], feq_shifted_r<Q, T>(i, drho, rho, ux, uy, uz, uu));
+      const T nj = r_sub(f[j], feq_shifted_r<Q, T>(j, drho, rho, ux, uy, uz, uu));
+      const T mi = r_sub(f[i], feq_shifted_r<Q, T>(i, drho, rho, usx, usy, usz, usus));
+      const T mj = r_sub(f[j], feq_shifted_r<Q, T>(j, drho, rho, usx, usy, usz, usus));
+      const T ofi = r_sub(fc[i], f[i]), ofj = r_sub(fc[j], f[j]);
       T osi, osj;
       if (p.solid == PSM_SC1) {
-        osi = nj - mi;
-        osj = ni - mj;
+        osi = r_sub(nj, mi);
+        osj = r_sub(ni, mj);
       } else if (p.solid == PSM_SC2) {
-        osi = -mi * inv_tau;
-        osj = -mj * inv_tau;
+        osi = r_mul(-mi, inv_tau);
+        osj = r_mul(-mj, inv_tau);
       } else {
-        osi = mj - mi;
-        osj = mi - mj;
+        osi = r_sub(mj, mi);
+        osj = r_sub(mi, mj);
       }
-      f[i] = f[i] + omB * ofi + Bw * osi;
-      f[j] = f[j] + omB * ofj + Bw * osj;
+      f[i] = r_fma(Bw, osi, r_fma(omB, ofi, f[i]));
+      f[j] = r_fma(Bw, osj, r_fma(omB, ofj, f[j]));
       // c_j = -c_i: sum_i Omega^S_i c_i over the pair
-      const T d = osi - osj;
-      if (lat_cx(i)) gx += T(lat_cx(i)) * d;
-      if (lat_cy(i)) gy += T(lat_cy(i)) * d;
-      if (lat_cz(i)) gz += T(lat_cz(i)) * d;
+      const T d = r_sub(osi, osj);
+      if (lat_cx(i)) gx = r_addc(gx, lat_cx(i), d);
+      if (lat_cy(i)) gy = r_addc(gy, lat_cy(i), d);
+      if (lat_cz(i)) gz = r_addc(gz, lat_cz(i), d);
     }
   } else {
     // BGK / TRT in pair form (c_j = -c_i).  With s = f_i + f_j, d = f_i - f_j
@@ -830,69 +848,59 @@ __device__ __forceinline__ void psm_collide(const StepParams& p, const DevBody* 
     // then f*_i,j = P +- M with P = s/2 + (1 - B) OmF+ + B OmS+ and
     // M = d/2 + (1 - B) OmF- + B OmS-, and the pair adds 2 OmS- c_i to
     // sum_i Omega^S_i c_i.
-    const T wp = om_a + om_b, wm = om_a - om_b;
-    const T bu = drho - T(1.5) * rho * uu, bs = drho - T(1.5) * rho * usus;
+    const T wp = r_add(om_a, om_b), wm = r_sub(om_a, om_b);
+    const T bu = r_fma(T(-1.5), r_mul(rho, uu), drho), bs = r_fma(T(-1.5), r_mul(rho, usus), drho);
     {
       const T w0 = T(lat_w<Q>(0));
-      const T n0 = f[0] - w0 * bu, m0 = f[0] - w0 * bs;
+      const T n0 = r_fma(-w0, bu, f[0]), m0 = r_fma(-w0, bs, f[0]);
       T os;
-      if (p.solid == PSM_SC1) os = n0 - m0;
-      else if (p.solid == PSM_SC2) os = -m0 * inv_tau;
+      if (p.solid == PSM_SC1) os = r_sub(n0, m0);
+      else if (p.solid == PSM_SC2) os = r_mul(-m0, inv_tau);
       else os = T(0);
-      f[0] = f[0] + omB * (-wp * n0) + Bw * os;
+      f[0] = r_fma(Bw, os, r_fma(omB, r_mul(-wp, n0), f[0]));
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
       const int j = i + 1;
       const T w = T(lat_w<Q>(i));
-      const T wr = w * rho;
-      const T cu = cdot(i, ux, uy, uz), cs = cdot(i, usx, usy, usz);
-      const T ev = w * bu + T(4.5) * wr * cu * cu, od = T(3) * wr * cu;
-      const T evs = w * bs + T(4.5) * wr * cs * cs, ods = T(3) * wr * cs;
-      const T hs = T(0.5) * (f[i] + f[j]), hd = T(0.5) * (f[i] - f[j]);
-      const T np = hs - ev, nm = hd - od, mp = hs - evs, mm = hd - ods;
+      const T wr = r_mul(w, rho);
+      const T cu = c_dot(i, ux, uy, uz), cs = c_dot(i, usx, usy, usz);
+      const T k45 = r_mul(T(4.5), wr), k3 = r_mul(T(3), wr);
+      const T ev = r_fma(k45, r_mul(cu, cu), r_mul(w, bu)), od = r_mul(k3, cu);
+      const T evs = r_fma(k45, r_mul(cs, cs), r_mul(w, bs)), ods = r_mul(k3, cs);
+      const T hs = r_mul(T(0.5), r_add(f[i], f[j])), hd = r_mul(T(0.5), r_sub(f[i], f[j]));
+      const T np = r_sub(hs, ev), nm = r_sub(hd, od), mp = r_sub(hs, evs), mm = r_sub(hd, ods);
       T sp, sm;
       if (p.solid == PSM_SC1) {
-        sp = np - mp;
-        sm = -nm - mm;
+        sp = r_sub(np, mp);
+        sm = r_sub(-nm, mm);
       } else if (p.solid == PSM_SC2) {
-        sp = -mp * inv_tau;
-        sm = -mm * inv_tau;
+        sp = r_mul(-mp, inv_tau);
+        sm = r_mul(-mm, inv_tau);
       } else {
         sp = T(0);
-        sm = T(-2) * mm;
+        sm = r_mul(T(-2), mm);
       }
-      const T P = hs + omB * (-wp * np) + Bw * sp;
-      const T M = hd + omB * (-wm * nm) + Bw * sm;
-      f[i] = P + M;
-      f[j] = P - M;
-      const T d = T(2) * sm;
-      if (lat_cx(i)) gx += T(lat_cx(i)) * d;
-      if (lat_cy(i)) gy += T(lat_cy(i)) * d;
-      if (lat_cz(i)) gz += T(lat_cz(i)) * d;
+      const T P = r_fma(Bw, sp, r_fma(omB, r_mul(-wp, np), hs));
+      const T M = r_fma(Bw, sm, r_fma(omB, r_mul(-wm, nm), hd));
+      f[i] = r_add(P, M);
+      f[j] = r_sub(P, M);
+      const T d = r_mul(T(2), sm);
+      if (lat_cx(i)) gx = r_addc(gx, lat_cx(i), d);
+      if (lat_cy(i)) gy = r_addc(gy, lat_cy(i), d);
+      if (lat_cz(i)) gz = r_addc(gz, lat_cz(i), d);
     }
   }
   if (owner >= 0) {
     // Eq. 10 / 11 per cell, in the arithmetic's precision (ft_t); the body
     // receives minus the solid's momentum transfer
-    const T Gx = Bw * gx, Gy = Bw * gy, Gz = Bw * gz;
-    const DevBody& b = bodies[owner];
-    T Rx, Ry, Rz;
-    if constexpr (sizeof(T) == 4) {
-      Rx = (T(x) + T(0.5)) - b.Rf[0];
-      Ry = (T(y) + T(0.5)) - b.Rf[1];
-      Rz = (T(z) + T(0.5)) - b.Rf[2];
-    } else {
-      Rx = (double)x + 0.5 - b.R[0];
-      Ry = (double)y + 0.5 - b.R[1];
-      Rz = (double)z + 0.5 - b.R[2];
-    }
+    const T Gx = r_mul(Bw, gx), Gy = r_mul(Bw, gy), Gz = r_mul(Bw, gz);
     ft[0] = -Gx;
     ft[1] = -Gy;
     ft[2] = -Gz;
-    ft[3] = -(Ry * Gz - Rz * Gy);
-    ft[4] = -(Rz * Gx - Rx * Gz);
-    ft[5] = -(Rx * Gy - Ry * Gx);
+    ft[3] = -r_sub(r_mul(ry, Gz), r_mul(rz, Gy));
+    ft[4] = -r_sub(r_mul(rz, Gx), r_mul(rx, Gz));
+    ft[5] = -r_sub(r_mul(rx, Gy), r_mul(ry, Gx));
   }
 }
 
@@ -1498,8 +1506,7 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
       return;
     }
     // the thread's cells r = 0 .. CPT-1: (lx, ly + r TYB), one after the other
-#pragma unroll
-    for (int r = 0; r < CPT; ++r) {
+    auto one_cell = [&](int r) {
       const int x = hd.x + lx, y = hd.y + ly + r * TYB;
       const unsigned cell = ((unsigned)z * (unsigned)p.g.ny + (unsigned)y) * (unsigned)p.g.nx + (unsigned)x;
       T f[Q];
@@ -1541,6 +1548,15 @@ __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
         psm_store<S, Q, MODE, GEN>(p, sn, zg, cell, f);
       }
       if (GEN) warp_ft(s_ft, nb, solid_cell && owner >= 0, owner, ft);
+    };
+    if constexpr (MODE == MODE_AA_EVEN) {
+      // only general tiles come here (the fluid-only ones took the pairs above):
+      // one copy of the PSM code
+#pragma unroll 1
+      for (int r = 0; r < CPT; ++r) one_cell(r);
+    } else {
+#pragma unroll
+      for (int r = 0; r < CPT; ++r) one_cell(r);
     }
   };
 
