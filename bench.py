@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_BYTES_PER_CELL = {
     # 256x256x240 case of the 1e9-cell rotor workload (one AA odd and one even
     # launch, 15,728,640 cells each): per cell, scaled to the full lattice
-    "c5/aa/fp16/tma": (1.139359e9 + 1.138760e9) / 2 / 15728640,
+    "c5/aa/fp16/tma": (1.140013e9 + 1.137385e9) / 2 / 15728640,
 }
 
 
