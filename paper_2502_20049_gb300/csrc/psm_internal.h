@@ -26,19 +26,20 @@ enum Mode { MODE_TG = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 #define PSM_TMA_STORE 0
 #endif
 // Cells per thread in a tile of the TMA step kernel: PSM_TMA_CPT16 for the
-// D3Q19 two-grid and AA even steps with BGK/TRT in 2-byte storage (FP16,
-// BF16), where the kernel is issue-bound and sharing the per-tile work (stage
-// wait, refill, tile classification, loop) between two cells measured faster
-// (in the AA even step the two cells of a fluid-only tile are x neighbours:
-// one 32-bit shared load and one 32-bit store per slot serve both); one
-// elsewhere (memory-bound 4- and 8-byte storage; D3Q27, the AA odd step and
-// the cumulant, where the larger stages of two-cell tiles cost more pipeline
-// depth than the shared work saves).
+// D3Q19 two-grid step and the D3Q19 and D3Q27 AA even steps with BGK/TRT in
+// 2-byte storage (FP16, BF16), where the kernel is issue-bound and sharing
+// the per-tile work (stage wait, refill, tile classification, loop) between
+// two cells measured faster (in the AA even step the two cells of a
+// fluid-only tile are x neighbours: one 32-bit shared load and one 32-bit
+// store per slot serve both); one elsewhere (memory-bound 4- and 8-byte
+// storage; the D3Q27 two-grid step, the AA odd step and the cumulant, where
+// the larger stages of two-cell tiles cost more pipeline depth than the
+// shared work saves).
 #ifndef PSM_TMA_CPT16
 #define PSM_TMA_CPT16 2
 #endif
 __host__ __device__ constexpr int tma_cells_per_thread(int storage_bytes, int mode, int Q, int fluid) {
-  return (storage_bytes == 2 && (mode == MODE_TG || mode == MODE_AA_EVEN) && Q == 19 && fluid != PSM_CUMULANT)
+  return (storage_bytes == 2 && fluid != PSM_CUMULANT && ((mode == MODE_TG && Q == 19) || mode == MODE_AA_EVEN))
              ? PSM_TMA_CPT16
              : 1;
 }

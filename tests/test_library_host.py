@@ -201,7 +201,8 @@ def test_tma_stage_budget(psm):
     it is sized for (228 KB per SM, 1 KB reserved and 6 KB of static shared
     memory per block; at most 227 KB per block), for every storage, stencil,
     streaming step and fluid operator; two cells per thread exactly for the
-    D3Q19 two-grid and AA even BGK/TRT steps in 2-byte storage.  Host only."""
+    D3Q19 two-grid and the D3Q19/D3Q27 AA even BGK/TRT steps in 2-byte storage.
+    Host only."""
     for storage in ("fp64", "fp32", "fp16", "bf16"):
         for Q in (19, 27):
             for mode in (0, 1, 2):
@@ -216,7 +217,8 @@ def test_tma_stage_budget(psm):
                     assert 2 <= L["stages"] <= 8, key
                     assert L["smem"] <= 227 * 1024, key
                     assert L["blocks_per_sm"] * (L["smem"] + 1024 + 6144) <= 228 * 1024, key
-                    two = storage in ("fp16", "bf16") and Q == 19 and mode in (0, 1) and fluid != "cumulant"
+                    two = (storage in ("fp16", "bf16") and fluid != "cumulant"
+                           and ((mode == 0 and Q == 19) or mode == 1))
                     assert L["cells_per_thread"] == (2 if two else 1), key
     with pytest.raises(psm.PSMError):
         psm.tma_layout("fp32", 15, 0, "bgk")
