@@ -1313,18 +1313,20 @@ struct TmaLayout {
 };
 
 // ---------------------------------------------------------------------------
-// TMA-staged step kernel.  Shapes: tiles of TX x TY = 256 cells of one z
-// plane with nx % TX == 0 and ny % TY == 0 (TX = min(256, nx)), TX * sizeof(S)
-// a multiple of 16 bytes; the AA odd step needs TX = 256.  Persistent blocks
-// stride over tiles.  Warp 0 keeps NST tiles of pre-collision PDFs
-// in flight in shared memory (two-grid and AA even: one cp.async.bulk.tensor
-// box per tile; AA odd: one row per direction plus 16-byte cp.async.bulk edge
-// chunks for x - c_x) while all threads collide the oldest staged tile from
-// shared memory.  The producer classifies each tile (tile_general) and the
-// block takes the fluid-only path or the general one for the whole tile.  The
-// two-grid and AA odd steps store to x + c_i with st.global; in the AA even
-// step every warp writes its 32 cells to shared memory and back with one TMA
-// tensor store.  No block barrier inside the tile loop.
+// TMA-staged step kernel.  Shapes: tiles of TX x TY = 256 CPT cells of one z
+// plane with nx % TX == 0 and ny % TY == 0 (TX = min(256, nx), a power of
+// two), TX * sizeof(S) a multiple of 16 bytes; the AA odd step needs TX = 256.
+// Persistent blocks stride over tiles.  Warp 0 keeps NST tiles of
+// pre-collision PDFs in flight in shared memory (two-grid and AA even: one
+// cp.async.bulk.tensor box per tile; AA odd: one row per direction plus
+// 16-byte cp.async.bulk edge chunks for x - c_x) while all threads collide the
+// oldest staged tile from shared memory.  The producer classifies each tile
+// (tile_general) and the block takes the fluid-only path or the general one
+// for the whole tile.  The two-grid and AA odd steps store to x + c_i with
+// st.global; the AA even step stores to the own cells' swapped slots (with
+// two cells per thread, the fluid-only tiles' x-neighbour pairs with one
+// 32-bit access per slot), or, built with PSM_TMA_STORE, through one TMA
+// tensor store per warp.  No block barrier inside the tile loop.
 // ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int FL>
 __global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
