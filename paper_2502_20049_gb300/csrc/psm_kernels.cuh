@@ -400,9 +400,13 @@ __device__ __forceinline__ void grid_reduce(const double* blk, int ncomp, double
 #ifndef PSM_MIN_BLOCKS_CUM
 #define PSM_MIN_BLOCKS_CUM 2
 #endif
-template <class S, int Q, int FL = 0>
+// The D3Q27 AA odd step in 2-byte storage (one cell per thread) fits 80
+// registers without spills and runs three blocks, where its even step (two
+// cells per thread) needs the 128-register budget of two.
+template <class S, int Q, int FL = 0, int MODE = -1>
 __host__ __device__ constexpr int step_min_blocks() {
   if (FL == 2) return sizeof(S) == 8 ? 1 : PSM_MIN_BLOCKS_CUM;
+  if (Q == 27 && sizeof(S) == 2 && MODE == MODE_AA_ODD) return 3;
   return sizeof(S) == 8 ? (Q == 19 ? PSM_MIN_BLOCKS_Q19 - 1 : PSM_MIN_BLOCKS_Q27 - 1)
                         : (Q == 19 ? PSM_MIN_BLOCKS_Q19 : PSM_MIN_BLOCKS_Q27);
 }
@@ -1298,7 +1302,7 @@ struct TmaLayout {
   static constexpr int WBOX = r128(Q * 32 * (int)sizeof(S));
   static constexpr int OUT = STORE_TMA ? (PSM_THREADS / 32) * WBOX : 0;
   static constexpr int SM_SMEM = 233472;
-  static constexpr int BLOCKS = step_min_blocks<S, Q, FL>();
+  static constexpr int BLOCKS = step_min_blocks<S, Q, FL, MODE>();
   // per block: 1 KB reserved by the hardware and the kernel's static shared
   // memory (about 5 KB: force/torque slots, reduction scratch, the bodies of
   // the step, stage headers), allowed for with 6 KB
@@ -1329,7 +1333,7 @@ struct TmaLayout {
 // tensor store per warp.  No block barrier inside the tile loop.
 // ---------------------------------------------------------------------------
 template <class S, int Q, int MODE, int FL>
-__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL>())
+__global__ void __launch_bounds__(PSM_THREADS, step_min_blocks<S, Q, FL, MODE>())
     k_step_tma(const __grid_constant__ StepParams p, const __grid_constant__ TmaMaps maps) {
   using T = typename Store<S>::T;
   using L = TmaLayout<S, Q, MODE, FL>;
