@@ -264,7 +264,8 @@ def e2e_with_output(sol, args, cells, world, dist, nb, ft_out):
 
     from paper_2502_20049_gb300 import replicas
 
-    k = args.e2e_output_every
+    # at least one export in the timed region (the interval shrinks to the step count)
+    k = min(args.e2e_output_every, args.steps)
     need = 32 * cells
     free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
     if k <= 0:
@@ -503,7 +504,8 @@ def main():
                     help="fluid operator (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-output-every", type=int, default=100,
-                    help="steps between the macroscopic exports of the second end-to-end loop (0: skip it)")
+                    help="steps between the macroscopic exports of the second end-to-end loop, at most --steps "
+                         "(0: skip it)")
     ap.add_argument("--no-extras", action="store_true", help="skip the variant and adjoint measurements")
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint cost measurement")
     ap.add_argument("--scale", type=float, default=1.0,
